@@ -390,3 +390,17 @@ def test_conditioning_floor_mode_is_close_to_fp64():
     b = oracle.image(sysm, fp32=True)
     err = np.abs(a - b).max() / np.abs(a).max()
     assert 0 < err < 1e-4
+
+
+def test_nfw_tnfw_mass_against_40_digit_golden():
+    """tests/golden/nfw_tnfw_mass.txt: mpmath quadrature of the 3-D densities (make_golden.py)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "nfw_tnfw_mass.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    xs = [float(r[0]) for r in rows]
+    nfw = np.array([float(r[1]) for r in rows])
+    tnfw = np.array([float(r[2]) for r in rows])
+    Rs = 0.02
+    # atol: the plain FP64 formulas cancel terms of size ~ tau^2 ln(2/x) at small x
+    np.testing.assert_allclose(_oracle_M("NFW", xs, Rs=Rs), nfw, rtol=2e-9, atol=1e-14)
+    np.testing.assert_allclose(_oracle_M("TNFW", xs, Rs=Rs, rt=5 * Rs), tnfw, rtol=2e-9, atol=1e-14)
