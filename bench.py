@@ -1,0 +1,351 @@
+"""Benchmark: lensed images/s on the substructure workload (200x200 grid, supersampling 3,
+10,000 truncated-NFW subhalos, EPL + shear, elliptical Sersic, 21x21 Moffat PSF).
+
+One step = one lensed image through the C ABI: lens_sim_image (subhalo constants + the
+fused trace/subhalo-sum/Sersic/bin-down kernel) into a device buffer, then
+lens_sim_convolve (PSF).  Inputs are device-resident when timing starts; L2 is flushed
+(256 MiB write) between steps and only the steps are timed, with CUDA events on the
+launching stream.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the baseline arm) on the host cores, each step a
+bounded band of image rows, extrapolated to images/s.
+Under torchrun (N > 1) every rank simulates its own images (weak scaling, no collective on
+the data path); the timed region is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lensed images/s (200², 10k subhalos) vs FP64 oracle; served p50/p99 ms"
+UNIT = "images/s"
+WORKLOAD = ("substructure image: 200x200 grid at 0.04\", supersampling 3 (360,000 traced points), "
+            "EPL + shear, 10,000 truncated-NFW subhalos, elliptical Sersic, 21x21 Moffat PSF, FP32")
+N_SYSTEMS = 8            # distinct seeded systems cycled through the steps
+# Algorithmic work of one point-subhalo pair, frozen from the far-field pair formula
+# (tnfw_pair + tnfw_g_far): 19 FFMA + 17 FMUL + 7 FADD = 62 FP32 flops (FMA = 2), 4 MUFU.
+FLOPS_PER_PAIR = 62
+KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trace_kernel_substructure_200x200.json")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------- clocks
+REASON_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 3:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                bits = int(parts[2], 16) if parts[2].startswith("0x") else int(parts[2])
+            except ValueError:
+                continue
+            for b, name in REASON_BITS.items():
+                if bits & b:
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+def oracle_sample(system, budget_s: float, max_rows: int):
+    """Time the FP64 oracle on bands of rows of one image until budget_s or max_rows."""
+    import oracle
+    oracle.build()
+    nx, ny = system.grid.nx, system.grid.ny
+    rows, t_total = 0, 0.0
+    band = 2
+    r = ny // 3
+    while rows < max_rows and t_total < budget_s:
+        b = min(band, max_rows - rows)
+        r0 = (r + rows) % (ny - b)
+        t0 = time.perf_counter()
+        oracle.image_rows(system, r0, r0 + b)
+        t_total += time.perf_counter() - t0
+        rows += b
+        band = min(band * 2, 32)
+    # the PSF step on the full image is timed once and pro-rated
+    img = np.random.default_rng(0).random((ny, nx))
+    t0 = time.perf_counter()
+    oracle.convolve(img, system.psf)
+    t_conv = time.perf_counter() - t0
+    t_image = t_total * ny / rows + t_conv
+    return 1.0 / t_image, rows, oracle.nthreads()
+
+
+def run_reference(args, rank: int) -> None:
+    if rank != 0:
+        return
+    from paper_2606_01547_gb300 import workloads as W
+    system = W.substructure_system(1000)
+    for _ in range(args.warmup):
+        oracle_sample(system, 0.5, 2)
+    vals, rows_tot, cores = [], 0, 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, rows, cores = oracle_sample(system, args.ref_step_s, 200)
+        vals.append(v)
+        rows_tot += rows
+    elapsed = time.perf_counter() - t0
+    value = statistics.median(vals)
+    sample = (f"{rows_tot} unconvolved rows of 200 over {args.steps} steps (bands of rows of one "
+              f"200x200 s=3 image, 10k subhalos) + one full 21x21 convolution per step; extrapolated")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "arm": "FP64 C++ oracle on host cores"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_01547_gb300 import lenssim
+    from paper_2606_01547_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    sim = lenssim.Simulator(device=local_rank)
+    systems = [W.substructure_system(1000 + rank * N_SYSTEMS + i) for i in range(N_SYSTEMS)]
+    keep = []
+    cs = []
+    for s in systems:
+        sub_d = torch.from_numpy(s.subhalos).to(dev)
+        keep.append(sub_d)
+        c = sim.system_struct(s, keep, subhalos=sub_d, use_psf=False)
+        cs.append(c)
+    psf_id = sim.register_psf(systems[0].psf)
+    nx = ny = systems[0].grid.nx
+    raw = torch.empty((ny, nx), device=dev)
+    out = torch.empty((ny, nx), device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+    stream = torch.cuda.current_stream()
+    sptr = int(stream.cuda_stream)
+    L = lenssim.lib()
+    import ctypes
+    raw_ptrs = (ctypes.c_void_p * 1)(raw.data_ptr())
+
+    def step(i):
+        c = cs[i % N_SYSTEMS]
+        rc = L.lens_sim_image(sim.h, ctypes.byref(c), 1, raw_ptrs, sptr)
+        if rc:
+            raise lenssim.LensSimError(rc, sim.last_error())
+        return c
+
+    def conv():
+        rc = L.lens_sim_convolve(sim.h, raw.data_ptr(), 1, ny, nx, psf_id, out.data_ptr(), sptr)
+        if rc:
+            raise lenssim.LensSimError(rc, sim.last_error())
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        step(i)
+        conv()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(float(i + 1))
+            e0, e1, e2 = ev[i]
+            e0.record(stream)
+            step(i)
+            e1.record(stream)
+            conv()
+            e2.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    step_ms = [e0.elapsed_time(e2) for e0, e1, e2 in ev]
+    trace_ms = [e0.elapsed_time(e1) for e0, e1, e2 in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    images = world * args.steps
+    value = images / (total_ms / 1000.0)
+
+    # dominant kernel: subhalo constants + fused trace kernel (the launch before the PSF)
+    pairs = systems[0].pairs()
+    avg_trace_s = statistics.mean(trace_ms) / 1000.0
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    clocks = clk.summary()
+    max_mhz = clocks["sm_max_mhz"] or 2070.0
+    peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    achieved = pairs * FLOPS_PER_PAIR / avg_trace_s / 1e12
+    traffic = None
+    if os.path.exists(PROFILE_TRAFFIC):
+        prof = json.load(open(PROFILE_TRAFFIC))
+        if prof.get("kernel_hash") == kernel_hash():
+            traffic = prof.get("traffic_bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "kernel": "trace_image_kernel<9,8> (+ tnfw_prep)",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived, FP32 FMA)",
+                "frac_at_median_clock": (achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+                                         if clocks["sm_mhz"] else None),
+                "pairs_per_s": pairs / avg_trace_s, "flops_per_pair": FLOPS_PER_PAIR,
+                "trace_ms": avg_trace_s * 1e3}
+
+    # e2e: the public call with HOST buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        sub_h = [torch.from_numpy(s.subhalos).pin_memory() for s in systems]
+        out_h = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
+        keep2 = []
+        cs_h = []
+        for s, sh in zip(systems, sub_h):
+            c = sim.system_struct(s, keep2, subhalos=sh, use_psf=True)
+            cs_h.append(c)
+        out_ptrs = (ctypes.c_void_p * 1)(out_h.data_ptr())
+
+        def e2e_step(i):
+            rc = L.lens_sim_image(sim.h, ctypes.byref(cs_h[i % N_SYSTEMS]), 1, out_ptrs, sptr)
+            if rc:
+                raise lenssim.LensSimError(rc, sim.last_error())
+
+        for i in range(args.warmup):
+            e2e_step(i)
+        torch.cuda.synchronize()
+        tsum = 0.0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step(i)  # H2D subhalos, kernels, D2H image, stream sync
+            tsum += time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([tsum], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tsum = float(t.item())
+        e2e = {"value": world * args.steps / tsum, "unit": UNIT,
+               "h2d_bytes_per_step": int(systems[0].subhalos.nbytes),
+               "d2h_bytes_per_step": int(ny * nx * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, rows, cores = oracle_sample(systems[0], args.cpu_budget_s, 200)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{rows} unconvolved rows of one 200x200 s=3 image (10k subhalos) + one full "
+                         f"21x21 convolution, extrapolated to whole images"}
+
+    if rank == 0:
+        res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "grid": 200, "supersample": 3, "n_subhalos": 10000,
+                          "psf": 21, "systems_cycled": N_SYSTEMS,
+                          "l2": "flushed between steps (256 MiB write), steps timed individually",
+                          "parallelism": f"replicas x{world}"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+               "gpu_launches": 3 * args.steps,
+               "gpu": props.name}
+        print(json.dumps(res), flush=True)
+    sim.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=8.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * lens_sim.h -- C ABI of the GB300 (sm_103a) lensed-image simulation library.
+ *
+ * The library implements the image-simulation pipeline of JAXtronomy (section
+ * "Improvements over lenstronomy in image simulation"): a coordinate grid in the
+ * observer's angles is ray-traced through the deflectors back to the source plane,
+ * the source surface brightness is evaluated on the traced grid, and the lensed
+ * image is convolved with the PSF.  The deflector and light models are those of
+ * the paper's deflection table (EPL, NIE/SIE, SHEAR, SIS, NFW, TNFW) and light
+ * table (SERSIC, SERSIC_ELLIPSE, SERSIC_ELLIPSE_Q_PHI); the subhalo population is
+ * the "tens of thousands of dark matter substructures" of the statement of need.
+ * The chi^2 log-likelihood and its gradient serve the gradient-based fitting of
+ * section "Improvements over lenstronomy in lens modelling".
+ *
+ * Conventions (apply to every call):
+ *  - Angles in arcsec, position angles in radians measured from +x toward +y.
+ *  - Images are FP32, row-major [ny][nx]; row i is at y = y0 + (i - (ny-1)/2) * pixel_scale,
+ *    column j at x = x0 + (j - (nx-1)/2) * pixel_scale.  With supersampling s, a pixel
+ *    holds pixel_scale^2 times the mean of its s x s sub-pixel samples (flux per pixel).
+ *  - PSF convolution is the zero-padded 'same'-size true convolution with an odd k x k
+ *    kernel: out[i][j] = sum_{a,b} K[a][b] in[i + c - a][j + c - b], c = (k-1)/2.
+ *  - Every call returns a lens_status.  No exception or abort crosses the ABI; on an
+ *    error nothing is launched and lens_sim_last_error() describes it.
+ *  - The caller owns every input and output buffer.  Registered PSFs and subhalo tables
+ *    are copied into library-owned device memory, freed by lens_sim_destroy.
+ *  - `stream` is a cudaStream_t (may be NULL for the legacy default stream).  Work is
+ *    enqueued on it; buffers must stay valid until that work completes.
+ *  - Pointers documented "host or device" are classified with cudaPointerGetAttributes.
+ *  - A handle is not thread-safe: one thread at a time per lens_sim (the server below
+ *    owns its own).
+ */
+#ifndef LENS_SIM_H
+#define LENS_SIM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LENS_OK = 0,
+  LENS_ERR_INVALID_ARG = -1,  /* bad type, size, parameter range or pointer */
+  LENS_ERR_OOM = -2,          /* device memory or memory budget exhausted */
+  LENS_ERR_CUDA = -3,         /* a CUDA runtime call failed; see lens_sim_last_error */
+  LENS_ERR_TIMEOUT = -4,      /* a bounded wait ran out */
+  LENS_ERR_BUSY = -5,         /* admission refused (server) or result still pending (poll) */
+  LENS_ERR_UNSUPPORTED = -6,  /* valid request outside what this build implements */
+  LENS_ERR_CANCELLED = -7     /* the request was cancelled before it ran */
+} lens_status;
+
+#define LENS_MAX_DEFLECTORS 8
+#define LENS_MAX_SUPERSAMPLE 8
+#define LENS_MAX_PSF 135
+#define LENS_N_FREE_PARAMS 15
+
+/* Deflector profile types and their parameter layouts p[] (deflection table rows). */
+typedef enum {
+  LENS_SIS = 0,         /* theta_E, cx, cy                 alpha = theta_E (dx,dy)/r          */
+  LENS_SIE = 1,         /* theta_E, q, phi, cx, cy          Kormann et al. 1994, q in (0,1]   */
+  LENS_EPL = 2,         /* theta_E, gamma, q, phi, cx, cy   Tessore & Metcalf 2015 series      */
+  LENS_SHEAR = 3,       /* gamma1, gamma2                   about the origin                   */
+  LENS_POINT_MASS = 4,  /* theta_E, cx, cy                                                     */
+  LENS_NFW = 5,         /* Rs, alpha_Rs, cx, cy             alpha_Rs = deflection at Rs        */
+  LENS_TNFW = 6,        /* Rs, alpha_Rs, r_t, cx, cy        Baltz, Marshall & Oguri 2009       */
+  LENS_EPL_E1E2 = 7,    /* theta_E, gamma, e1, e2, cx, cy  q = (1-c)/(1+c), c = |e|, phi = arg(e)/2 */
+  LENS_SIE_E1E2 = 8     /* theta_E, e1, e2, cx, cy                                              */
+} lens_profile_type;
+
+/* Source light profile types (light table rows). I = amp exp(-b_n [(R/R_s)^(1/n) - 1]),
+ * R = sqrt(q x'^2 + y'^2/q), b_n = 1.9992 n - 0.3271. */
+typedef enum {
+  LIGHT_SERSIC_ELLIPSE_Q_PHI = 0, /* amp, R_sersic, n, q, phi, cx, cy */
+  LIGHT_SERSIC_ELLIPSE = 1,       /* amp, R_sersic, n, e1, e2, cx, cy */
+  LIGHT_SERSIC = 2                /* amp, R_sersic, n, cx, cy         */
+} light_profile_type;
+
+typedef struct { int type; float p[8]; } lens_profile;
+typedef struct { int type; float p[8]; } light_profile;
+
+/* Grid spec: nx, ny >= 1; supersample in [1, 8]; pixel_scale > 0; (x0, y0) = grid centre. */
+typedef struct { int nx, ny, supersample; float pixel_scale, x0, y0; } lens_grid;
+
+/* One lens system.  `deflectors` is HOST memory (at most LENS_MAX_DEFLECTORS entries).
+ * Subhalos (truncated NFW) are either a structure of arrays `subhalos` = [5][n_subhalos]
+ * (cx, cy, Rs, alpha_Rs, r_t; host or device memory) with subhalo_table = -1, or a
+ * resident table id from lens_sim_register_subhalos (then `subhalos` is ignored).
+ * psf_id = -1 skips the PSF step (the binned, unconvolved image is returned). */
+typedef struct {
+  lens_grid grid;
+  const lens_profile* deflectors;
+  int n_deflectors;
+  const float* subhalos;
+  int n_subhalos;
+  int subhalo_table;
+  light_profile source;
+  int psf_id;
+} lens_system;
+
+typedef struct {
+  int device;               /* CUDA device ordinal                                   */
+  size_t mem_budget_bytes;  /* 0 = no limit; workspace growth beyond it -> LENS_ERR_OOM */
+  int max_batch;            /* largest n_sys / n_points accepted per call (0 = 4096)  */
+  unsigned flags;           /* reserved, must be 0                                   */
+} lens_sim_config;
+
+typedef struct lens_sim lens_sim;
+
+/* Create a handle bound to config->device (NULL config = device 0, no budget).
+ * Allocates nothing on the device until first use. */
+int lens_sim_create(const lens_sim_config* config, lens_sim** out);
+
+/* Synchronise the handle's work and free everything it owns.  NULL is a no-op. */
+void lens_sim_destroy(lens_sim* sim);
+
+/* Text of the last error on this handle; valid until the next call on it. */
+const char* lens_sim_last_error(const lens_sim* sim);
+
+/* Copy an odd k x k FP32 kernel (host memory, row-major, 1 <= k <= LENS_MAX_PSF) into
+ * device memory and return its id.  The kernel is used as given (not re-normalised). */
+int lens_sim_register_psf(lens_sim* sim, const float* kernel, int k, int* psf_id);
+
+/* Copy a subhalo population (SoA [5][n], host or device) into a resident device table
+ * with its per-subhalo constants precomputed, and return its id.  n may be 0. */
+int lens_sim_register_subhalos(lens_sim* sim, const float* soa, int n, int* table_id);
+
+/* Simulate n_sys lensed images (image simulation steps 1-3 plus the supersample
+ * bin-down).  out_images is a HOST array of n_sys pointers, each to ny*nx floats in
+ * host or device memory (host outputs are staged and copied back on `stream`; the call
+ * then synchronises the stream before returning).  Systems may differ in every size. */
+int lens_sim_image(lens_sim* sim, const lens_system* systems, int n_sys, float* const* out_images,
+                   void* stream);
+
+/* Ray-shooting: total deflection of `sys` (deflector list + subhalos) at n points.
+ * x, y, ax, ay are DEVICE arrays of n floats.  The grid, source and PSF are ignored. */
+int lens_sim_deflection(lens_sim* sim, const lens_system* sys, const float* x, const float* y, int n,
+                        float* ax, float* ay, void* stream);
+
+/* PSF step alone: convolve n_img DEVICE images [n_img][ny][nx] with a registered PSF. */
+int lens_sim_convolve(lens_sim* sim, const float* in, int n_img, int ny, int nx, int psf_id, float* out,
+                      void* stream);
+
+/* Chi^2 log-likelihood of n_points parameter vectors against DEVICE data [ny][nx]:
+ *   sigma^2 = sigma_bkg^2 + max(m, 0)/t_exp,   logL = -1/2 sum (d - m)^2 / sigma^2,
+ * with m the PSF-convolved model.  params is DEVICE [n_points][15] in the order
+ * EPL_E1E2 (theta_E, gamma, e1, e2, cx, cy), SHEAR (g1, g2),
+ * SERSIC_ELLIPSE (amp, R, n, e1, e2, cx, cy); `sys` supplies the grid, PSF and the fixed
+ * subhalos (its deflector list and source are ignored).  out_logL: DEVICE [n_points];
+ * out_grad: DEVICE [n_points][15] or NULL for the likelihood only. */
+int lens_sim_grad(lens_sim* sim, const lens_system* sys, const float* data, float sigma_bkg, float t_exp,
+                  const float* params, int n_points, float* out_logL, float* out_grad, void* stream);
+
+/* ---------------------------------------------------------------- serving
+ * A server owns its own lens_sim state, streams and a worker thread that admits requests
+ * by a device-memory budget, batches what is waiting, and overlaps batches on the device.
+ * Requests reference HOST buffers: for kind 0 (image) `out` receives ny*nx floats; for
+ * kind 1 (likelihood + gradient) `data` holds the ny*nx observation, `params` the 15
+ * parameters, `out` the log-likelihood (1 float) and `out_grad` 15 floats.  The buffers
+ * must stay valid until wait/poll returns LENS_OK, LENS_ERR_CANCELLED or an error. */
+typedef struct lens_server lens_server;
+typedef struct {
+  int kind;                 /* 0 image, 1 log-likelihood + gradient */
+  lens_system sys;          /* psf_id refers to the server's lens_sim (see lens_serve_sim) */
+  const float* data;
+  float sigma_bkg, t_exp;
+  const float* params;
+  float* out;
+  float* out_grad;
+} lens_request;
+
+int lens_serve_create(const lens_sim_config* config, int max_inflight, lens_server** out);
+/* The server's own handle, for lens_sim_register_psf / lens_sim_register_subhalos before
+ * submitting requests that use them (do not call them while requests are in flight). */
+lens_sim* lens_serve_sim(lens_server* srv);
+/* Enqueue a request; LENS_ERR_BUSY when max_inflight requests are already queued or running. */
+int lens_serve_submit(lens_server* srv, const lens_request* req, unsigned long long* ticket);
+/* Wait up to timeout_ms (>= 0) for a ticket: LENS_OK, LENS_ERR_TIMEOUT, LENS_ERR_CANCELLED,
+ * or the request's own error.  Never blocks longer than timeout_ms plus one poll period. */
+int lens_serve_wait(lens_server* srv, unsigned long long ticket, int timeout_ms);
+/* LENS_OK when done, LENS_ERR_BUSY while pending, or the request's error. */
+int lens_serve_poll(lens_server* srv, unsigned long long ticket);
+/* Cancel a request that has not started; LENS_ERR_BUSY if it is already running. */
+int lens_serve_cancel(lens_server* srv, unsigned long long ticket);
+/* Latency percentiles (submit -> completion) and throughput over completed requests. */
+int lens_serve_stats(lens_server* srv, double* p50_ms, double* p99_ms, double* requests_per_s);
+void lens_serve_destroy(lens_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LENS_SIM_H */

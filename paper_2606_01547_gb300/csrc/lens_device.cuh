@@ -1,0 +1,353 @@
+// Device-side FP32 lensing arithmetic for sm_103a: deflection profiles, the truncated-NFW
+// subhalo pair term, and the elliptical Sersic source.  Every accumulation is FP32; no FP64
+// is used on the device.
+//
+// Profiles follow their published definitions (the paper names them in its deflection and
+// light tables but prints no formula):
+//   SIE   Kormann, Schneider & Bartelmann (1994): kappa = theta_E / (2 sqrt(q x'^2 + y'^2/q)).
+//   EPL   Tessore & Metcalf (2015): hypergeometric series in e^{2 i phi}, b = theta_E sqrt(q).
+//   NFW   Bartelmann (1996), Wright & Brainerd (2000); alpha_Rs = deflection at r = Rs.
+//   TNFW  Baltz, Marshall & Oguri (2009), n = 1 truncation, tau = r_t / Rs.
+//   Sersic I = amp exp(-b_n [(R/R_s)^(1/n) - 1]), R = sqrt(q x'^2 + y'^2/q), b_n = 1.9992 n - 0.3271.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lens_sim.h"
+
+namespace ls {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kHalfPi = 1.57079632679489661923f;
+constexpr float kLn2 = 0.69314718055994530942f;
+constexpr float kOneMinusLn2 = 0.30685281944005469058f;
+
+struct DevProfile {
+  int type;
+  float p[8];
+};
+
+// One lens system as the kernels see it.  `sub` is the precomputed subhalo table (two
+// float4 per subhalo, see tnfw_prep); `out` receives the binned, unconvolved image.
+struct DevSystem {
+  int nx, ny, s, n_defl;
+  float dpix, x0, y0;
+  int src_type;
+  float src[8];
+  DevProfile defl[LENS_MAX_DEFLECTORS];
+  int n_sub;
+  int pad_;
+  const float4* sub;
+  float* out;
+};
+
+// ---------------------------------------------------------------------------- helpers
+__device__ __forceinline__ void e1e2_to_qphi(float e1, float e2, float& q, float& phi) {
+  phi = 0.5f * atan2f(e2, e1);
+  float c = sqrtf(e1 * e1 + e2 * e2);
+  q = (1.f - c) / (1.f + c);
+}
+
+__device__ __forceinline__ void to_frame(float dx, float dy, float cp, float sp, float& xp, float& yp) {
+  xp = cp * dx + sp * dy;
+  yp = -sp * dx + cp * dy;
+}
+
+// ---------------------------------------------------------------------------- main deflectors
+__device__ __forceinline__ void alpha_sis(float x, float y, float thetaE, float cx, float cy,
+                                          float& ax, float& ay) {
+  float dx = x - cx, dy = y - cy;
+  float r2 = dx * dx + dy * dy;
+  if (r2 < 1e-24f) { ax = 0.f; ay = 0.f; return; }
+  float ir = rsqrtf(r2);
+  ax = thetaE * dx * ir;
+  ay = thetaE * dy * ir;
+}
+
+__device__ __forceinline__ void alpha_point_mass(float x, float y, float thetaE, float cx, float cy,
+                                                 float& ax, float& ay) {
+  float dx = x - cx, dy = y - cy;
+  float r2 = dx * dx + dy * dy;
+  if (r2 < 1e-24f) { ax = 0.f; ay = 0.f; return; }
+  float k = thetaE * thetaE / r2;
+  ax = k * dx;
+  ay = k * dy;
+}
+
+static __device__ __noinline__ void alpha_sie(float x, float y, float thetaE, float q, float phi, float cx,
+                                       float cy, float& ax, float& ay) {
+  float sp, cp;
+  sincosf(phi, &sp, &cp);
+  float dx = x - cx, dy = y - cy, xp, yp;
+  to_frame(dx, dy, cp, sp, xp, yp);
+  float r2 = dx * dx + dy * dy;
+  if (r2 < 1e-24f) { ax = 0.f; ay = 0.f; return; }
+  float apx, apy;
+  if (fabsf(1.f - q) < 1e-6f) {
+    float ir = rsqrtf(r2);
+    apx = thetaE * xp * ir;
+    apy = thetaE * yp * ir;
+  } else {
+    float b = thetaE * sqrtf(q);
+    float psi = sqrtf(q * q * xp * xp + yp * yp);
+    float e = sqrtf((1.f - q) * (1.f + q));
+    float be = b / e;
+    apx = be * atanf(e * xp / psi);
+    apy = be * atanhf(e * yp / psi);
+  }
+  ax = cp * apx - sp * apy;
+  ay = sp * apx + cp * apy;
+}
+
+// Number of EPL series terms for FP32: |Omega_n| <= f^n, stop once f^n < 2^-26.
+__device__ __forceinline__ int epl_terms(float f) {
+  if (f < 1e-20f) return 0;
+  int n = (int)ceilf(-18.0218f / logf(f)) + 1;
+  return n < 1 ? 1 : (n > 200 ? 200 : n);
+}
+
+static __device__ __noinline__ void alpha_epl(float x, float y, float thetaE, float gamma, float q, float phi,
+                                       float cx, float cy, float& ax, float& ay) {
+  float sp, cp;
+  sincosf(phi, &sp, &cp);
+  float dx = x - cx, dy = y - cy, xp, yp;
+  to_frame(dx, dy, cp, sp, xp, yp);
+  float R = sqrtf(q * q * xp * xp + yp * yp);
+  if (R < 1e-12f) { ax = 0.f; ay = 0.f; return; }
+  float t = gamma - 1.f;
+  float b = thetaE * sqrtf(q);
+  float iR = 1.f / R;
+  float er = q * xp * iR, ei = yp * iR;
+  float f = (1.f - q) / (1.f + q);
+  float zr = -f * (er * er - ei * ei), zi = -f * (2.f * er * ei);
+  float omr = er, omi = ei, sr = er, si = ei;
+  const int nt = epl_terms(f);
+  for (int n = 1; n <= nt; ++n) {
+    float coef = (2.f * n - 2.f + t) / (2.f * n + 2.f - t);
+    float nr = coef * (omr * zr - omi * zi);
+    float ni = coef * (omr * zi + omi * zr);
+    omr = nr; omi = ni;
+    sr += omr; si += omi;
+  }
+  float pref = 2.f * b / (1.f + q) * exp2f((t - 1.f) * log2f(b * iR));
+  float apx = pref * sr, apy = pref * si;
+  ax = cp * apx - sp * apy;
+  ay = sp * apx + cp * apy;
+}
+
+// ---------------------------------------------------------------------------- NFW / TNFW
+// Both are written as alpha = K * g(x^2) * (dx, dy) with x = r/Rs and g = M(x)/x^2 up to a
+// constant; the functions below return that g for FP32 without catastrophic cancellation.
+
+// F(x) near x = 1 as sum_k (-v)^k/(2k+1), v = x^2 - 1 (|v| < 0.1: 9 terms reach 1e-10).
+__device__ __forceinline__ float nfw_F_series(float v) {
+  float s = 0.f, t = 1.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) { s += t / (2.f * k + 1.f); t *= -v; }
+  return s;
+}
+
+__device__ __forceinline__ float nfw_F(float x2) {
+  float v = x2 - 1.f;
+  if (fabsf(v) < 0.1f) return nfw_F_series(v);
+  if (v > 0.f) { float u = sqrtf(v); return atanf(u) / u; }
+  float x = sqrtf(x2);
+  float u = sqrtf((1.f - x) * (1.f + x));
+  return logf((1.f + u) / x) / u;
+}
+
+// NFW: h(x)/x^2 with h = ln(x/2) + F(x).  For x < 1, with u = sqrt(1-x^2), w = 1-u = x^2/(1+u):
+// h = [log1p(-w/2) + w ln(2/x)] / u, whose two terms are both O(x^2).
+static __device__ __noinline__ float nfw_h_over_x2(float x2) {
+  if (x2 < 0.81f) {
+    float x = sqrtf(x2);
+    float u = sqrtf((1.f - x) * (1.f + x));
+    float wx = 1.f / (1.f + u);       // w / x^2
+    float w = x2 * wx;
+    float z = -0.5f * w;
+    float l1 = (log1pf(z) / z) * (-0.5f * wx);  // log1p(-w/2) / x^2
+    return (l1 + (kLn2 - logf(x)) * wx) / u;
+  }
+  float x = sqrtf(x2);
+  return (logf(0.5f * x) + nfw_F(x2)) / x2;
+}
+
+// Taylor coefficients of asin(y)/y = sum_k c_k y^(2k), c_k = (2k)! / (4^k (k!)^2 (2k+1));
+// asinh(z)/z is the same series with alternating signs.
+__device__ __forceinline__ float asin_over_y(float y2) {
+  float p = 0.017352764f;                 // 231/13312
+  p = fmaf(p, y2, 0.022372159f);          // 63/2816
+  p = fmaf(p, y2, 0.030381944f);          // 35/1152
+  p = fmaf(p, y2, 0.044642857f);          // 5/112
+  p = fmaf(p, y2, 0.075f);                // 3/40
+  p = fmaf(p, y2, 0.16666667f);           // 1/6
+  return fmaf(p, y2, 1.f);
+}
+
+__device__ __forceinline__ float asinh_over_z(float z2) {
+  float p = 0.017352764f;
+  p = fmaf(p, -z2, 0.022372159f);
+  p = fmaf(p, -z2, 0.030381944f);
+  p = fmaf(p, -z2, 0.044642857f);
+  p = fmaf(p, -z2, 0.075f);
+  p = fmaf(p, -z2, 0.16666667f);
+  return fmaf(p, -z2, 1.f);
+}
+
+// Truncated NFW bracket G(x) of M(x) = tau^2/(tau^2+1)^2 G(x):
+//   G = (tau^2 + 1 + 2(x^2-1)) F(x) + tau pi + (tau^2-1) ln tau + S (-pi + L (tau^2-1)/tau),
+//   S = sqrt(tau^2 + x^2),  L = ln(x / (S + tau)) = -asinh(tau/x).
+// Returned: G/x^2.  Constants: t2 = tau^2, t2m1 = tau^2 - 1, C = tau pi + (tau^2-1) ln tau.
+//
+// Three evaluation regimes, each free of catastrophic cancellation in FP32:
+//  x < 0.9  : G = (tau^2-1) D + 2 x^2 F + pi (tau - S), D = F + ln tau + (S/tau) L, with D and
+//             tau - S rewritten as sums of O(x^2) terms (log1p forms);
+//  x < 4    : the defining formula (cancellation is mild there);
+//  x >= 4   : in y = 1/x, z = tau y, r1 = (1-y^2)^(-1/2), Sx = sqrt(1+z^2), P = asin(y)/y:
+//             G = r1 [(tau^2-1)(pi/2 y - y^2 P) - 2P] + C + pi y (tau^2 y^2 - (tau^2-1)) r1^2/(r1+Sx)
+//                 - (tau^2-1) Sx asinh(z)/z,
+//             which removes the +-pi x cancellation and the ln of a ratio near 1.
+static __device__ __noinline__ float tnfw_g_near(float x2, float tau, float t2, float t2m1, float C) {
+  float S = sqrtf(t2 + x2);
+  if (x2 < 0.81f) {
+    float x = sqrtf(x2);
+    float u = sqrtf((1.f - x) * (1.f + x));
+    float wx = 1.f / (1.f + u);
+    float w = x2 * wx;
+    float lnx = logf(x);
+    float F = logf((1.f + u) / x) / u;
+    float L = -asinhf(tau / x);
+    float z = -0.5f * w;
+    float l1 = (log1pf(z) / z) * (-0.5f * wx);
+    float l2 = log1pf(x2 / (2.f * tau * (S + tau))) / x2;
+    float Dx2 = (l1 + (kLn2 - lnx) * wx) / u - l2 + L / (tau * (S + tau));
+    return t2m1 * Dx2 + 2.f * F - kPi / (tau + S);
+  }
+  float F = nfw_F(x2);
+  float x = sqrtf(x2);
+  float L = -asinhf(tau / x);
+  float G = (t2m1 + 2.f * x2) * F + C + S * (-kPi + L * t2m1 / tau);
+  return G / x2;
+}
+
+__device__ __forceinline__ float tnfw_g_far(float x2, float tau, float t2, float t2m1, float C) {
+  float y = rsqrtf(x2);
+  float y2 = y * y;
+  float r1 = rsqrtf(1.f - y2);
+  float z = tau * y;
+  float z2 = z * z;
+  float sq = 1.f + z2;
+  float Sx = sq * rsqrtf(sq);
+  float P = asin_over_y(y2);
+  float ash = (z2 < 0.0625f) ? asinh_over_z(z2) : __fdividef(logf(z + Sx), z);
+  float head = r1 * fmaf(t2m1, fmaf(kHalfPi, y, -y2 * P), -2.f * P);
+  float mid = __fdividef(kPi * y * fmaf(t2, y2, -t2m1) * r1 * r1, r1 + Sx);
+  float G = head + C + mid - t2m1 * Sx * ash;
+  return G * y2;
+}
+
+__device__ __forceinline__ float tnfw_g(float x2, float tau, float t2, float t2m1, float C) {
+  return (x2 >= 16.f) ? tnfw_g_far(x2, tau, t2, t2m1, C) : tnfw_g_near(x2, tau, t2, t2m1, C);
+}
+
+// Per-subhalo constants, two float4: (cx, cy, 1/Rs^2, tau), (tau^2, tau^2-1, C, A) with
+// A = alpha_Rs tau^2 / ((1 - ln 2) Rs (tau^2+1)^2), so that alpha = A g(x^2) (dx, dy).
+__device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, float alphaRs, float rt,
+                                               float4& a, float4& b) {
+  float tau = rt / Rs;
+  float t2 = tau * tau;
+  float t2p1 = t2 + 1.f;
+  a = make_float4(cx, cy, 1.f / (Rs * Rs), tau);
+  b = make_float4(t2, t2 - 1.f, tau * kPi + (t2 - 1.f) * logf(tau),
+                  alphaRs * t2 / (kOneMinusLn2 * Rs * t2p1 * t2p1));
+}
+
+// One point-subhalo pair, accumulated into (ax, ay).  The x floor of 1e-6 (x^2 >= 1e-12)
+// makes alpha vanish continuously at the subhalo centre.
+__device__ __forceinline__ void tnfw_pair(float px, float py, const float4 a, const float4 b,
+                                          float& ax, float& ay) {
+  float dx = px - a.x, dy = py - a.y;
+  float r2 = fmaf(dx, dx, dy * dy);
+  float x2 = fmaxf(r2 * a.z, 1e-12f);
+  float k = b.w * tnfw_g(x2, a.w, b.x, b.y, b.z);
+  ax = fmaf(k, dx, ax);
+  ay = fmaf(k, dy, ay);
+}
+
+__device__ __forceinline__ void alpha_nfw(float x, float y, float Rs, float alphaRs, float cx, float cy,
+                                          float& ax, float& ay) {
+  float dx = x - cx, dy = y - cy;
+  float x2 = fmaxf((dx * dx + dy * dy) / (Rs * Rs), 1e-12f);
+  float k = alphaRs / (kOneMinusLn2 * Rs) * nfw_h_over_x2(x2);
+  ax = k * dx;
+  ay = k * dy;
+}
+
+__device__ __forceinline__ void alpha_tnfw(float x, float y, float Rs, float alphaRs, float rt, float cx,
+                                           float cy, float& ax, float& ay) {
+  float4 a, b;
+  tnfw_constants(cx, cy, Rs, alphaRs, rt, a, b);
+  ax = 0.f; ay = 0.f;
+  tnfw_pair(x, y, a, b, ax, ay);
+}
+
+// Deflection of one deflector-list profile at (x, y); returns (ax, ay).
+static __device__ __noinline__ void alpha_profile(const DevProfile& P, float x, float y, float& ax, float& ay) {
+  const float* p = P.p;
+  switch (P.type) {
+    case LENS_SIS: alpha_sis(x, y, p[0], p[1], p[2], ax, ay); return;
+    case LENS_SIE: alpha_sie(x, y, p[0], p[1], p[2], p[3], p[4], ax, ay); return;
+    case LENS_EPL: alpha_epl(x, y, p[0], p[1], p[2], p[3], p[4], p[5], ax, ay); return;
+    case LENS_SHEAR: ax = p[0] * x + p[1] * y; ay = p[1] * x - p[0] * y; return;
+    case LENS_POINT_MASS: alpha_point_mass(x, y, p[0], p[1], p[2], ax, ay); return;
+    case LENS_NFW: alpha_nfw(x, y, p[0], p[1], p[2], p[3], ax, ay); return;
+    case LENS_TNFW: alpha_tnfw(x, y, p[0], p[1], p[2], p[3], p[4], ax, ay); return;
+    case LENS_EPL_E1E2: {
+      float q, phi;
+      e1e2_to_qphi(p[2], p[3], q, phi);
+      alpha_epl(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay);
+      return;
+    }
+    case LENS_SIE_E1E2: {
+      float q, phi;
+      e1e2_to_qphi(p[1], p[2], q, phi);
+      alpha_sie(x, y, p[0], q, phi, p[3], p[4], ax, ay);
+      return;
+    }
+    default: ax = 0.f; ay = 0.f; return;
+  }
+}
+
+// ---------------------------------------------------------------------------- Sersic source
+__device__ __forceinline__ float sersic(float x, float y, float amp, float Rs, float n, float q, float phi,
+                                        float cx, float cy) {
+  float sp, cp;
+  sincosf(phi, &sp, &cp);
+  float xp, yp;
+  to_frame(x - cx, y - cy, cp, sp, xp, yp);
+  float R = sqrtf(q * xp * xp + yp * yp / q);
+  float bn = 1.9992f * n - 0.3271f;
+  float pw = exp2f(log2f(R / Rs) / n);
+  return amp * expf(-bn * (pw - 1.f));
+}
+
+static __device__ __noinline__ float source_light(int type, const float* p, float x, float y) {
+  switch (type) {
+    case LIGHT_SERSIC_ELLIPSE_Q_PHI: return sersic(x, y, p[0], p[1], p[2], p[3], p[4], p[5], p[6]);
+    case LIGHT_SERSIC_ELLIPSE: {
+      float q, phi;
+      e1e2_to_qphi(p[3], p[4], q, phi);
+      return sersic(x, y, p[0], p[1], p[2], q, phi, p[5], p[6]);
+    }
+    case LIGHT_SERSIC: return sersic(x, y, p[0], p[1], p[2], 1.f, 0.f, p[3], p[4]);
+    default: return 0.f;
+  }
+}
+
+// Grid coordinate of column j (or row i), sub-sample b of s: centre-relative offsets in pixels.
+__device__ __forceinline__ float grid_coord(float c0, int j, int n, int b, int s, float dpix) {
+  return c0 + ((float)j - 0.5f * (float)(n - 1) + ((float)b + 0.5f) / (float)s - 0.5f) * dpix;
+}
+
+}  // namespace ls

@@ -1,0 +1,397 @@
+// Host implementation of the C ABI in include/lens_sim.h: argument validation, device
+// workspace management, resident PSF/subhalo state, and the per-system launch sequence
+//   subhalo constants -> fused trace/source/bin-down kernel -> PSF convolution.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "lens_sim.h"
+#include "sim_internal.h"
+
+using namespace ls;
+
+namespace ls {
+
+int fail(lens_sim* s, int code, const char* fmt, ...) {
+  if (s) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    s->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(lens_sim* s, cudaError_t e, const char* what) {
+  return fail(s, LENS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ensure(lens_sim* s, DevBuffer& b, size_t bytes) {
+  if (bytes <= b.cap) return LENS_OK;
+  size_t want = bytes + bytes / 4;  // geometric growth
+  if (s->budget && s->allocated - b.cap + want > s->budget) {
+    want = bytes;
+    if (s->allocated - b.cap + want > s->budget)
+      return fail(s, LENS_ERR_OOM, "workspace of %zu bytes exceeds the memory budget (%zu of %zu used)",
+                  bytes, s->allocated, s->budget);
+  }
+  if (b.p) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaDeviceSynchronize");
+    cudaFree(b.p);
+    s->allocated -= b.cap;
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(s, LENS_ERR_OOM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e));
+  }
+  b.cap = want;
+  s->allocated += want;
+  return LENS_OK;
+}
+
+void release(lens_sim* s, DevBuffer& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    s->allocated -= b.cap;
+  }
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+static bool finite(float v) { return v == v && v < 3.0e38f && v > -3.0e38f; }
+
+int validate_profile(lens_sim* s, const lens_profile& p) {
+  for (int k = 0; k < 8; ++k)
+    if (!finite(p.p[k])) return fail(s, LENS_ERR_INVALID_ARG, "deflector parameter %d is not finite", k);
+  switch (p.type) {
+    case LENS_SIS: case LENS_SHEAR: case LENS_POINT_MASS: return LENS_OK;
+    case LENS_SIE:
+      if (!(p.p[1] > 0.f && p.p[1] <= 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "SIE q=%g not in (0,1]", p.p[1]);
+      return LENS_OK;
+    case LENS_EPL:
+      if (!(p.p[2] > 0.f && p.p[2] <= 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL q=%g not in (0,1]", p.p[2]);
+      if (!(p.p[1] > 1.f && p.p[1] < 3.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL gamma=%g not in (1,3)", p.p[1]);
+      return LENS_OK;
+    case LENS_EPL_E1E2:
+      if (!(p.p[1] > 1.f && p.p[1] < 3.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL gamma=%g not in (1,3)", p.p[1]);
+      if (!(p.p[2] * p.p[2] + p.p[3] * p.p[3] < 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL |e| >= 1");
+      return LENS_OK;
+    case LENS_SIE_E1E2:
+      if (!(p.p[1] * p.p[1] + p.p[2] * p.p[2] < 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "SIE |e| >= 1");
+      return LENS_OK;
+    case LENS_NFW:
+      if (!(p.p[0] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "NFW Rs must be > 0");
+      return LENS_OK;
+    case LENS_TNFW:
+      if (!(p.p[0] > 0.f && p.p[2] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "TNFW Rs and r_t must be > 0");
+      return LENS_OK;
+    default: return fail(s, LENS_ERR_INVALID_ARG, "unknown deflector type %d", p.type);
+  }
+}
+
+int validate_light(lens_sim* s, const light_profile& p) {
+  for (int k = 0; k < 8; ++k)
+    if (!finite(p.p[k])) return fail(s, LENS_ERR_INVALID_ARG, "source parameter %d is not finite", k);
+  if (!(p.p[1] > 0.f) || !(p.p[2] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "Sersic R and n must be > 0");
+  switch (p.type) {
+    case LIGHT_SERSIC: return LENS_OK;
+    case LIGHT_SERSIC_ELLIPSE_Q_PHI:
+      if (!(p.p[3] > 0.f && p.p[3] <= 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "Sersic q=%g not in (0,1]", p.p[3]);
+      return LENS_OK;
+    case LIGHT_SERSIC_ELLIPSE:
+      if (!(p.p[3] * p.p[3] + p.p[4] * p.p[4] < 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "Sersic |e| >= 1");
+      return LENS_OK;
+    default: return fail(s, LENS_ERR_INVALID_ARG, "unknown light type %d", p.type);
+  }
+}
+
+int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
+  if (need_grid) {
+    const lens_grid& g = y.grid;
+    if (g.nx < 1 || g.ny < 1 || g.nx > 16384 || g.ny > 16384)
+      return fail(s, LENS_ERR_INVALID_ARG, "grid %dx%d out of range [1, 16384]", g.nx, g.ny);
+    if (g.supersample < 1 || g.supersample > LENS_MAX_SUPERSAMPLE)
+      return fail(s, LENS_ERR_INVALID_ARG, "supersample %d not in [1, %d]", g.supersample, LENS_MAX_SUPERSAMPLE);
+    if (!(g.pixel_scale > 0.f) || !finite(g.pixel_scale) || !finite(g.x0) || !finite(g.y0))
+      return fail(s, LENS_ERR_INVALID_ARG, "bad pixel scale or grid centre");
+    int rc = validate_light(s, y.source);
+    if (rc) return rc;
+    if (y.psf_id < -1 || y.psf_id >= (int)s->psfs.size() || (y.psf_id >= 0 && !s->psfs[y.psf_id].d))
+      return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", y.psf_id);
+  }
+  if (y.n_deflectors < 0 || y.n_deflectors > LENS_MAX_DEFLECTORS)
+    return fail(s, LENS_ERR_INVALID_ARG, "n_deflectors %d not in [0, %d]", y.n_deflectors, LENS_MAX_DEFLECTORS);
+  if (y.n_deflectors > 0 && !y.deflectors) return fail(s, LENS_ERR_INVALID_ARG, "deflectors is NULL");
+  for (int d = 0; d < y.n_deflectors; ++d) {
+    int rc = validate_profile(s, y.deflectors[d]);
+    if (rc) return rc;
+  }
+  if (y.subhalo_table >= 0) {
+    if (y.subhalo_table >= (int)s->tables.size() || (!s->tables[y.subhalo_table].d && s->tables[y.subhalo_table].n))
+      return fail(s, LENS_ERR_INVALID_ARG, "unknown subhalo_table %d", y.subhalo_table);
+  } else {
+    if (y.subhalo_table != -1) return fail(s, LENS_ERR_INVALID_ARG, "subhalo_table must be -1 or a table id");
+    if (y.n_subhalos < 0) return fail(s, LENS_ERR_INVALID_ARG, "n_subhalos < 0");
+    if (y.n_subhalos > 0 && !y.subhalos) return fail(s, LENS_ERR_INVALID_ARG, "subhalos is NULL");
+  }
+  return LENS_OK;
+}
+
+int sub_count(lens_sim* s, const lens_system& y) {
+  return y.subhalo_table >= 0 ? s->tables[y.subhalo_table].n : y.n_subhalos;
+}
+
+// Resolve the subhalo table of a system into device constants (2 float4 per subhalo).
+// `tab_buf` must hold 32 * n bytes when the system carries raw subhalos.
+int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* raw_buf,
+                     const float4** out_tab, int* out_n, cudaStream_t st) {
+  if (y.subhalo_table >= 0) {
+    *out_tab = s->tables[y.subhalo_table].d;
+    *out_n = s->tables[y.subhalo_table].n;
+    return LENS_OK;
+  }
+  const int n = y.n_subhalos;
+  *out_n = n;
+  *out_tab = tab_buf;
+  if (n == 0) return LENS_OK;
+  const float* src = y.subhalos;
+  if (!is_device_ptr(src)) {
+    cudaError_t e = cudaMemcpyAsync(raw_buf, src, sizeof(float) * 5 * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "copy subhalos to device");
+    src = raw_buf;
+  }
+  cudaError_t e = launch_tnfw_prep(src, n, n, tab_buf, st);
+  if (e != cudaSuccess) return cuda_fail(s, e, "tnfw_prep launch");
+  return LENS_OK;
+}
+
+void fill_dev_system(const lens_system& y, DevSystem& d) {
+  std::memset(&d, 0, sizeof(d));
+  d.nx = y.grid.nx;
+  d.ny = y.grid.ny;
+  d.s = y.grid.supersample;
+  d.dpix = y.grid.pixel_scale;
+  d.x0 = y.grid.x0;
+  d.y0 = y.grid.y0;
+  d.n_defl = y.n_deflectors;
+  for (int k = 0; k < y.n_deflectors; ++k) {
+    d.defl[k].type = y.deflectors[k].type;
+    for (int q = 0; q < 8; ++q) d.defl[k].p[q] = y.deflectors[k].p[q];
+  }
+  d.src_type = y.source.type;
+  for (int q = 0; q < 8; ++q) d.src[q] = y.source.p[q];
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+  cudaGetDevice(&prev_);
+  if (prev_ != dev) cudaSetDevice(dev);
+  dev_ = dev;
+}
+DeviceGuard::~DeviceGuard() {
+  if (prev_ != dev_) cudaSetDevice(prev_);
+}
+
+}  // namespace ls
+
+// ============================================================================ C ABI
+extern "C" {
+
+int lens_sim_create(const lens_sim_config* cfg, lens_sim** out) {
+  if (!out) return LENS_ERR_INVALID_ARG;
+  *out = nullptr;
+  lens_sim_config c{0, 0, 0, 0};
+  if (cfg) c = *cfg;
+  if (c.flags != 0 || c.max_batch < 0) return LENS_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return LENS_ERR_CUDA;
+  }
+  if (c.device < 0 || c.device >= ndev) return LENS_ERR_INVALID_ARG;
+  lens_sim* s = new (std::nothrow) lens_sim();
+  if (!s) return LENS_ERR_OOM;
+  s->device = c.device;
+  s->budget = c.mem_budget_bytes;
+  s->max_batch = c.max_batch ? c.max_batch : 4096;
+  DeviceGuard g(s->device);
+  cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+  *out = s;
+  return LENS_OK;
+}
+
+void lens_sim_destroy(lens_sim* s) {
+  if (!s) return;
+  {
+    DeviceGuard g(s->device);
+    cudaDeviceSynchronize();
+    for (auto& p : s->psfs) if (p.d) cudaFree(p.d);
+    for (auto& t : s->tables) if (t.d) cudaFree(t.d);
+    release(s, s->raw_sub);
+    release(s, s->tab);
+    release(s, s->img);
+    release(s, s->stage);
+    release(s, s->grad_ws);
+  }
+  delete s;
+}
+
+const char* lens_sim_last_error(const lens_sim* s) { return s ? s->err.c_str() : "null handle"; }
+
+int lens_sim_register_psf(lens_sim* s, const float* kernel, int k, int* psf_id) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (!kernel || !psf_id) return fail(s, LENS_ERR_INVALID_ARG, "NULL kernel or psf_id");
+  if (k < 1 || k > LENS_MAX_PSF || (k % 2) == 0) return fail(s, LENS_ERR_INVALID_ARG, "PSF size %d must be odd in [1, %d]", k, LENS_MAX_PSF);
+  DeviceGuard g(s->device);
+  size_t bytes = sizeof(float) * (size_t)k * k;
+  if (s->budget && s->allocated + bytes > s->budget) return fail(s, LENS_ERR_OOM, "PSF exceeds the memory budget");
+  float* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, bytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(s, LENS_ERR_OOM, "cudaMalloc PSF: %s", cudaGetErrorString(e)); }
+  e = cudaMemcpy(d, kernel, bytes, is_device_ptr(kernel) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(d); return cuda_fail(s, e, "copy PSF"); }
+  s->allocated += bytes;
+  s->psfs.push_back({d, k});
+  *psf_id = (int)s->psfs.size() - 1;
+  return LENS_OK;
+}
+
+int lens_sim_register_subhalos(lens_sim* s, const float* soa, int n, int* table_id) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (!table_id || n < 0 || (n > 0 && !soa)) return fail(s, LENS_ERR_INVALID_ARG, "bad subhalo table arguments");
+  DeviceGuard g(s->device);
+  SubTable t{nullptr, n};
+  if (n > 0) {
+    size_t bytes = 2 * sizeof(float4) * (size_t)n;
+    if (s->budget && s->allocated + bytes > s->budget) return fail(s, LENS_ERR_OOM, "subhalo table exceeds the memory budget");
+    cudaError_t e = cudaMalloc(&t.d, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(s, LENS_ERR_OOM, "cudaMalloc subhalo table: %s", cudaGetErrorString(e)); }
+    const float* src = soa;
+    float* tmp = nullptr;
+    if (!is_device_ptr(soa)) {
+      e = cudaMalloc(&tmp, sizeof(float) * 5 * (size_t)n);
+      if (e == cudaSuccess) e = cudaMemcpy(tmp, soa, sizeof(float) * 5 * (size_t)n, cudaMemcpyHostToDevice);
+      src = tmp;
+    }
+    if (e == cudaSuccess) e = launch_tnfw_prep(src, n, n, t.d, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) { cudaFree(t.d); return cuda_fail(s, e, "subhalo table"); }
+    s->allocated += bytes;
+  }
+  s->tables.push_back(t);
+  *table_id = (int)s->tables.size() - 1;
+  return LENS_OK;
+}
+
+int lens_sim_image(lens_sim* s, const lens_system* systems, int n_sys, float* const* out_images, void* stream) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (n_sys < 0 || n_sys > s->max_batch) return fail(s, LENS_ERR_INVALID_ARG, "n_sys %d not in [0, %d]", n_sys, s->max_batch);
+  if (n_sys == 0) return LENS_OK;
+  if (!systems || !out_images) return fail(s, LENS_ERR_INVALID_ARG, "NULL systems or out_images");
+  DeviceGuard g(s->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t max_pix = 0, max_sub = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    int rc = validate_system(s, systems[i], true);
+    if (rc) return fail(s, rc, "system %d: %s", i, s->err.c_str());
+    if (!out_images[i]) return fail(s, LENS_ERR_INVALID_ARG, "system %d: NULL output", i);
+    max_pix = std::max(max_pix, (size_t)systems[i].grid.nx * systems[i].grid.ny);
+    if (systems[i].subhalo_table < 0) max_sub = std::max(max_sub, (size_t)systems[i].n_subhalos);
+  }
+  int rc;
+  if ((rc = ensure(s, s->img, sizeof(float) * max_pix))) return rc;
+  if ((rc = ensure(s, s->stage, sizeof(float) * max_pix))) return rc;
+  if (max_sub) {
+    if ((rc = ensure(s, s->tab, 2 * sizeof(float4) * max_sub))) return rc;
+    if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * max_sub))) return rc;
+  }
+  bool host_out = false;
+  for (int i = 0; i < n_sys; ++i) {
+    const lens_system& y = systems[i];
+    DevSystem d;
+    fill_dev_system(y, d);
+    if ((rc = prepare_subhalos(s, y, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
+    const bool dev_out = is_device_ptr(out_images[i]);
+    float* final_dst = dev_out ? out_images[i] : (float*)s->stage.p;
+    d.out = (y.psf_id >= 0) ? (float*)s->img.p : final_dst;
+    TraceShape sh = choose_trace_shape(d.nx, d.ny, d.s, d.n_sub, s->sm_count);
+    cudaError_t e = launch_trace(d, sh, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "trace kernel launch");
+    if (y.psf_id >= 0) {
+      const PsfEntry& p = s->psfs[y.psf_id];
+      e = launch_conv((float*)s->img.p, final_dst, 1, d.ny, d.nx, p.d, p.k, 1, st);
+      if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
+    }
+    if (!dev_out) {
+      e = cudaMemcpyAsync(out_images[i], final_dst, sizeof(float) * d.nx * d.ny, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return cuda_fail(s, e, "copy image to host");
+      host_out = true;
+    }
+  }
+  if (host_out) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  }
+  return LENS_OK;
+}
+
+int lens_sim_deflection(lens_sim* s, const lens_system* sys, const float* x, const float* y, int n, float* ax,
+                        float* ay, void* stream) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (!sys || n < 0) return fail(s, LENS_ERR_INVALID_ARG, "bad arguments");
+  if (n == 0) return LENS_OK;
+  if (!x || !y || !ax || !ay) return fail(s, LENS_ERR_INVALID_ARG, "NULL point arrays");
+  DeviceGuard g(s->device);
+  int rc = validate_system(s, *sys, false);
+  if (rc) return rc;
+  if (!is_device_ptr(x) || !is_device_ptr(y) || !is_device_ptr(ax) || !is_device_ptr(ay))
+    return fail(s, LENS_ERR_INVALID_ARG, "point arrays must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (sys->subhalo_table < 0 && sys->n_subhalos > 0) {
+    if ((rc = ensure(s, s->tab, 2 * sizeof(float4) * sys->n_subhalos))) return rc;
+    if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * sys->n_subhalos))) return rc;
+  }
+  DevSystem d;
+  lens_system tmp = *sys;
+  tmp.grid = lens_grid{1, 1, 1, 1.f, 0.f, 0.f};
+  fill_dev_system(tmp, d);
+  if ((rc = prepare_subhalos(s, *sys, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
+  cudaError_t e = launch_deflection(d, x, y, n, ax, ay, st);
+  if (e != cudaSuccess) return cuda_fail(s, e, "deflection kernel launch");
+  return LENS_OK;
+}
+
+int lens_sim_convolve(lens_sim* s, const float* in, int n_img, int ny, int nx, int psf_id, float* out, void* stream) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (n_img < 0 || ny < 1 || nx < 1 || ny > 16384 || nx > 16384) return fail(s, LENS_ERR_INVALID_ARG, "bad image sizes");
+  if (psf_id < 0 || psf_id >= (int)s->psfs.size()) return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", psf_id);
+  if (n_img == 0) return LENS_OK;
+  if (!in || !out || in == out) return fail(s, LENS_ERR_INVALID_ARG, "NULL or aliased buffers");
+  DeviceGuard g(s->device);
+  if (!is_device_ptr(in) || !is_device_ptr(out)) return fail(s, LENS_ERR_INVALID_ARG, "images must be device memory");
+  const PsfEntry& p = s->psfs[psf_id];
+  cudaError_t e = launch_conv(in, out, n_img, ny, nx, p.d, p.k, 1, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
+  return LENS_OK;
+}
+
+}  // extern "C"

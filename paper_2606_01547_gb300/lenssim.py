@@ -1,0 +1,297 @@
+"""Thin ctypes binding of liblenssim.so (include/lens_sim.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA library.
+PyTorch supplies device memory and the current CUDA stream.  If the library has not
+been built, every entry point raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import workloads as W
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblenssim.so")
+
+LENS_OK, LENS_ERR_INVALID_ARG, LENS_ERR_OOM, LENS_ERR_CUDA = 0, -1, -2, -3
+LENS_ERR_TIMEOUT, LENS_ERR_BUSY, LENS_ERR_UNSUPPORTED, LENS_ERR_CANCELLED = -4, -5, -6, -7
+STATUS_NAMES = {0: "LENS_OK", -1: "LENS_ERR_INVALID_ARG", -2: "LENS_ERR_OOM", -3: "LENS_ERR_CUDA",
+                -4: "LENS_ERR_TIMEOUT", -5: "LENS_ERR_BUSY", -6: "LENS_ERR_UNSUPPORTED",
+                -7: "LENS_ERR_CANCELLED"}
+
+LENS_TYPES = {"SIS": 0, "SIE": 1, "EPL": 2, "SHEAR": 3, "POINT_MASS": 4, "NFW": 5, "TNFW": 6,
+              "EPL_E1E2": 7, "SIE_E1E2": 8}
+LIGHT_TYPES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2}
+MAX_DEFLECTORS = 8
+
+EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
+            "lens_sim_register_subhalos", "lens_sim_image", "lens_sim_deflection", "lens_sim_convolve",
+            "lens_sim_grad", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
+            "lens_serve_poll", "lens_serve_cancel", "lens_serve_stats", "lens_serve_destroy")
+
+
+class LensProfile(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("p", ctypes.c_float * 8)]
+
+
+class LightProfile(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("p", ctypes.c_float * 8)]
+
+
+class LensGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("supersample", ctypes.c_int),
+                ("pixel_scale", ctypes.c_float), ("x0", ctypes.c_float), ("y0", ctypes.c_float)]
+
+
+class LensSystemC(ctypes.Structure):
+    _fields_ = [("grid", LensGrid),
+                ("deflectors", ctypes.POINTER(LensProfile)),
+                ("n_deflectors", ctypes.c_int),
+                ("subhalos", ctypes.c_void_p),
+                ("n_subhalos", ctypes.c_int),
+                ("subhalo_table", ctypes.c_int),
+                ("source", LightProfile),
+                ("psf_id", ctypes.c_int)]
+
+
+class SimConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
+                ("max_batch", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+class LensRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sys", LensSystemC), ("data", ctypes.c_void_p),
+                ("sigma_bkg", ctypes.c_float), ("t_exp", ctypes.c_float), ("params", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("out_grad", ctypes.c_void_p)]
+
+
+class LensSimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load liblenssim.so; raise if it has not been built (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f"CUDA library {_LIB_PATH} is missing: run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'` first")
+            L = ctypes.CDLL(_LIB_PATH)
+            vp, ip, fp = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+            L.lens_sim_create.argtypes = [ctypes.POINTER(SimConfig), ctypes.POINTER(vp)]
+            L.lens_sim_destroy.argtypes = [vp]
+            L.lens_sim_destroy.restype = None
+            L.lens_sim_last_error.argtypes = [vp]
+            L.lens_sim_last_error.restype = ctypes.c_char_p
+            L.lens_sim_register_psf.argtypes = [vp, vp, ip, ctypes.POINTER(ip)]
+            L.lens_sim_register_subhalos.argtypes = [vp, vp, ip, ctypes.POINTER(ip)]
+            L.lens_sim_image.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(vp), vp]
+            L.lens_sim_deflection.argtypes = [vp, ctypes.POINTER(LensSystemC), vp, vp, ip, vp, vp, vp]
+            L.lens_sim_convolve.argtypes = [vp, vp, ip, ip, ip, ip, vp, vp]
+            L.lens_sim_grad.argtypes = [vp, ctypes.POINTER(LensSystemC), vp, fp, fp, vp, ip, vp, vp, vp]
+            L.lens_serve_create.argtypes = [ctypes.POINTER(SimConfig), ip, ctypes.POINTER(vp)]
+            L.lens_serve_sim.argtypes = [vp]
+            L.lens_serve_sim.restype = vp
+            L.lens_serve_submit.argtypes = [vp, ctypes.POINTER(LensRequest), ctypes.POINTER(ctypes.c_ulonglong)]
+            L.lens_serve_wait.argtypes = [vp, ctypes.c_ulonglong, ip]
+            L.lens_serve_poll.argtypes = [vp, ctypes.c_ulonglong]
+            L.lens_serve_cancel.argtypes = [vp, ctypes.c_ulonglong]
+            L.lens_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]
+            L.lens_serve_destroy.argtypes = [vp]
+            L.lens_serve_destroy.restype = None
+            _lib = L
+    return _lib
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return int(t.data_ptr())
+    return int(t.ctypes.data)
+
+
+def profile_struct(name: str, params: Sequence[float], table=LENS_TYPES, cls=LensProfile):
+    p = cls()
+    p.type = table[name]
+    for i, v in enumerate(params):
+        p.p[i] = float(v)
+    return p
+
+
+class Simulator:
+    """A lens_sim handle: resident PSFs and subhalo tables plus a device workspace."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 0, max_batch: int = 0):
+        self._L = lib()
+        cfg = SimConfig(device, mem_budget, max_batch, 0)
+        h = ctypes.c_void_p()
+        rc = self._L.lens_sim_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != 0:
+            raise LensSimError(rc, "lens_sim_create failed")
+        self.h = h
+        self.device = device
+        self._psf_ids: Dict[Tuple[int, bytes], int] = {}
+
+    @classmethod
+    def wrap(cls, handle: int, device: int = 0) -> "Simulator":
+        """A non-owning view of an existing handle (e.g. a server's)."""
+        obj = cls.__new__(cls)
+        obj._L = lib()
+        obj.h = ctypes.c_void_p(handle)
+        obj.device = device
+        obj._psf_ids = {}
+        obj._borrowed = True
+        return obj
+
+    def close(self):
+        if getattr(self, "h", None) is not None and not getattr(self, "_borrowed", False):
+            self._L.lens_sim_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise LensSimError(rc, self._L.lens_sim_last_error(self.h).decode())
+
+    def last_error(self) -> str:
+        return self._L.lens_sim_last_error(self.h).decode()
+
+    # ------------------------------------------------------------------ resident state
+    def register_psf(self, kernel: np.ndarray) -> int:
+        k = np.ascontiguousarray(kernel, dtype=np.float32)
+        key = (k.shape[0], k.tobytes())
+        if key in self._psf_ids:
+            return self._psf_ids[key]
+        pid = ctypes.c_int()
+        self._check(self._L.lens_sim_register_psf(self.h, k.ctypes.data, int(k.shape[0]), ctypes.byref(pid)))
+        self._psf_ids[key] = pid.value
+        return pid.value
+
+    def register_subhalos(self, soa) -> int:
+        if isinstance(soa, torch.Tensor):
+            t = soa.contiguous()
+            n = int(t.shape[1]) if t.dim() == 2 else 0
+            ptr = t.data_ptr() if n else None
+        else:
+            t = np.ascontiguousarray(soa, dtype=np.float32).reshape(5, -1)
+            n = int(t.shape[1])
+            ptr = t.ctypes.data if n else None
+        tid = ctypes.c_int()
+        self._check(self._L.lens_sim_register_subhalos(self.h, ptr, n, ctypes.byref(tid)))
+        return tid.value
+
+    # ------------------------------------------------------------------ marshalling
+    def system_struct(self, system: W.LensSystem, keep: list, subhalos=None, subhalo_table: int = -1,
+                      use_psf: bool = True) -> LensSystemC:
+        g = system.grid
+        c = LensSystemC()
+        c.grid = LensGrid(int(g.nx), int(g.ny), int(g.s), float(g.dpix), float(g.x0), float(g.y0))
+        nd = len(system.deflectors)
+        if nd > MAX_DEFLECTORS:
+            raise ValueError("too many deflectors")
+        arr = (LensProfile * max(nd, 1))()
+        for i, (name, vals) in enumerate(system.deflectors):
+            arr[i] = profile_struct(name, vals)
+        keep.append(arr)
+        c.deflectors = ctypes.cast(arr, ctypes.POINTER(LensProfile))
+        c.n_deflectors = nd
+        if subhalo_table >= 0:
+            c.subhalos = None
+            c.n_subhalos = 0
+            c.subhalo_table = subhalo_table
+        else:
+            src = subhalos if subhalos is not None else system.subhalos
+            if isinstance(src, torch.Tensor):
+                src = src.contiguous()
+            else:
+                src = np.ascontiguousarray(src, dtype=np.float32).reshape(5, -1)
+            keep.append(src)
+            n = int(src.shape[1])
+            c.subhalos = _ptr(src) if n else None
+            c.n_subhalos = n
+            c.subhalo_table = -1
+        c.source = profile_struct(system.source[0], system.source[1], LIGHT_TYPES, LightProfile)
+        c.psf_id = self.register_psf(system.psf) if (use_psf and system.psf is not None) else -1
+        return c
+
+    # ------------------------------------------------------------------ compute
+    def image(self, systems, out: Optional[List] = None, stream=None, subhalos=None, subhalo_tables=None,
+              use_psf: bool = True) -> List[torch.Tensor]:
+        """Simulate images.  `out` may hold CUDA tensors or NumPy arrays (host outputs)."""
+        if isinstance(systems, W.LensSystem):
+            systems = [systems]
+        n = len(systems)
+        keep: list = []
+        arr = (LensSystemC * n)()
+        for i, s in enumerate(systems):
+            arr[i] = self.system_struct(s, keep, None if subhalos is None else subhalos[i],
+                                        -1 if subhalo_tables is None else subhalo_tables[i], use_psf)
+        if out is None:
+            out = [torch.empty((s.grid.ny, s.grid.nx), dtype=torch.float32, device=f"cuda:{self.device}")
+                   for s in systems]
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in out])
+        self._check(self._L.lens_sim_image(self.h, arr, n, ptrs, _stream_ptr(stream)))
+        return out
+
+    def deflection(self, system: W.LensSystem, x: torch.Tensor, y: torch.Tensor, stream=None):
+        keep: list = []
+        c = self.system_struct(system, keep, use_psf=False)
+        x = x.contiguous().float()
+        y = y.contiguous().float()
+        ax = torch.empty_like(x)
+        ay = torch.empty_like(y)
+        self._check(self._L.lens_sim_deflection(self.h, ctypes.byref(c), x.data_ptr(), y.data_ptr(), x.numel(),
+                                                ax.data_ptr(), ay.data_ptr(), _stream_ptr(stream)))
+        return ax, ay
+
+    def convolve(self, images: torch.Tensor, psf, out: Optional[torch.Tensor] = None, stream=None):
+        pid = psf if isinstance(psf, int) else self.register_psf(psf)
+        imgs = images.contiguous()
+        if imgs.dim() == 2:
+            imgs = imgs[None]
+        if out is None:
+            out = torch.empty_like(imgs)
+        self._check(self._L.lens_sim_convolve(self.h, imgs.data_ptr(), imgs.shape[0], imgs.shape[1],
+                                              imgs.shape[2], pid, out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def grad(self, system: W.LensSystem, data: torch.Tensor, sigma_bkg: float, t_exp: float,
+             params: torch.Tensor, want_grad: bool = True, stream=None, subhalo_table: int = -1):
+        keep: list = []
+        c = self.system_struct(system, keep, subhalo_table=subhalo_table)
+        P = params.contiguous().float()
+        n = P.shape[0]
+        L = torch.empty(n, dtype=torch.float32, device=P.device)
+        G = torch.empty((n, 15), dtype=torch.float32, device=P.device) if want_grad else None
+        self._check(self._L.lens_sim_grad(self.h, ctypes.byref(c), data.contiguous().data_ptr(), float(sigma_bkg),
+                                          float(t_exp), P.data_ptr(), n, L.data_ptr(),
+                                          None if G is None else G.data_ptr(), _stream_ptr(stream)))
+        return (L, G) if want_grad else L

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on seeded inputs.
+
+Image tolerance: max|gpu - oracle| / max|oracle| <= max(1e-5, 2 * floor), where floor is
+the same relative error of the oracle's conditioning-floor mode (FP64 arithmetic with the
+grid, every deflection term and the traced position rounded to FP32).  That floor is the
+error any FP32 evaluation must make; it only exceeds 1e-5 where a steep Sersic cusp meets
+FP32 rounding of the traced coordinates.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_01547_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_01547_gb300 import lenssim
+    s = lenssim.Simulator(device=0)
+    yield s
+    s.close()
+
+
+def rel_linf(got, ref):
+    return float(np.abs(np.asarray(got, np.float64) - ref).max() / np.abs(ref).max())
+
+
+def image_tol(system, ref):
+    floor = rel_linf(oracle.image(system, fp32=True), ref)
+    return max(1e-5, 2.0 * floor), floor
+
+
+def gpu_image(sim, system, **kw):
+    out = sim.image(system, **kw)[0]
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+# ----------------------------------------------------------------------------- whole images
+def test_plain_60x60_image_matches_oracle(sim):
+    system = W.plain_system()
+    ref = oracle.image(system)
+    err = rel_linf(gpu_image(sim, system), ref)
+    assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("seed,nx,s,nsub,k", [(0, 36, 3, 300, 7), (1, 29, 2, 77, 5), (2, 20, 1, 513, 1),
+                                              (3, 17, 4, 40, 3), (4, 11, 5, 130, 9)])
+def test_substructure_small_images_match_oracle(sim, seed, nx, s, nsub, k):
+    # several 8x4 tiles with ragged edges; s = 4, 5 exercise the multi-pass sample path
+    system = W.substructure_system(seed, n_sub=nsub, nx=nx, s=s, k=k)
+    ref = oracle.image(system)
+    tol, floor = image_tol(system, ref)
+    err = rel_linf(gpu_image(sim, system), ref)
+    assert err <= tol, (err, floor)
+
+
+def test_unconvolved_image_and_no_subhalos(sim):
+    system = W.substructure_system(5, n_sub=0, nx=40, s=2, k=0)
+    ref = oracle.image(system)
+    tol, _ = image_tol(system, ref)
+    assert rel_linf(gpu_image(sim, system), ref) <= tol
+
+
+def test_substructure_full_size_sampled_rows(sim):
+    # 200x200, s = 3, 10,000 subhalos, 21x21 Moffat: the launch configuration the benchmark times.
+    # The oracle computes the 21 unconvolved rows the kernel spans around one output row.
+    system = W.substructure_system(11)
+    got_conv = gpu_image(sim, system)
+    got_raw = gpu_image(sim, system, use_psf=False)
+    k = system.psf.shape[0]
+    c = (k - 1) // 2
+    row = 142
+    r0, r1 = row - c, row + c + 1
+    raw = oracle.image_rows(system, r0, r1)
+    raw_fp32 = oracle.image_rows(system, row - 1, row + 2, fp32=True)
+    scale = np.abs(raw).max()
+    floor = np.abs(raw_fp32 - raw[c - 1:c + 2]).max() / scale
+    tol = max(1e-5, 2 * floor)
+    err = np.abs(got_raw[r0:r1] - raw).max() / scale
+    assert err <= tol, (err, floor)
+    conv_row = np.zeros(system.grid.nx)
+    K = system.psf.astype(np.float64)
+    pad = np.pad(raw, ((0, 0), (c, c)))
+    for a in range(k):
+        for b in range(k):
+            conv_row += K[a, b] * pad[k - 1 - a, (k - 1 - b):(k - 1 - b) + system.grid.nx]
+    err_c = np.abs(got_conv[row] - conv_row).max() / np.abs(got_conv).max()
+    assert err_c <= tol, (err_c, floor)
+    # one more unconvolved row elsewhere, with its own floor
+    row2 = 57
+    raw2 = oracle.image_rows(system, row2, row2 + 1)
+    fl2 = np.abs(oracle.image_rows(system, row2, row2 + 1, fp32=True) - raw2).max() / np.abs(raw2).max()
+    assert np.abs(got_raw[row2] - raw2[0]).max() / np.abs(raw2).max() <= max(1e-5, 2 * fl2)
+
+
+# ----------------------------------------------------------------------------- deflections
+def _points(n, seed, lo=-3.0, hi=3.0):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, n).astype(np.float32), rng.uniform(lo, hi, n).astype(np.float32)
+
+
+PROFILES = [("SIS", [1.1, 0.05, -0.02]), ("SIE", [1.0, 0.8, 0.3, 0.0, 0.0]),
+            ("SIE", [1.2, 0.45, 2.1, 0.1, -0.1]), ("EPL", [1.2, 1.85, 0.65, 1.0, 0.02, 0.01]),
+            ("EPL", [0.9, 2.17, 0.9, 2.5, -0.05, 0.0]), ("EPL", [1.0, 2.0, 0.7, 0.3, 0.0, 0.0]),
+            ("SHEAR", [0.04, -0.03]), ("POINT_MASS", [0.3, 0.1, 0.2]), ("NFW", [0.4, 0.2, 0.05, 0.1]),
+            ("TNFW", [0.3, 0.15, 1.5, -0.1, 0.0]), ("EPL_E1E2", [1.1, 2.05, 0.08, -0.05, 0.0, 0.03]),
+            ("SIE_E1E2", [1.0, -0.1, 0.06, 0.0, 0.0])]
+
+
+@pytest.mark.parametrize("name,params", PROFILES)
+def test_profile_deflection_matches_oracle(sim, name, params):
+    x, y = _points(5000, 7)
+    system = W.LensSystem(W.Grid(1, 1, 1, 1.0), [(name, [W.f32(v) for v in params])],
+                          np.zeros((5, 0), np.float32), ("SERSIC", [1.0, 0.1, 1.0, 0.0, 0.0]))
+    ax, ay = sim.deflection(system, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    rx, ry = oracle.alpha(name, system.deflectors[0][1], x, y)
+    scale = max(np.abs(rx).max(), np.abs(ry).max())
+    err = max(np.abs(ax.cpu().numpy() - rx).max(), np.abs(ay.cpu().numpy() - ry).max()) / scale
+    assert err < 2e-6, err
+
+
+@pytest.mark.parametrize("tau", [5.0, 2.0, 20.0])
+def test_tnfw_pair_term_across_all_regimes(sim, tau):
+    # points at x = r/Rs from 1e-5 to 3e3 cross the small, near-1 and far-field forms
+    Rs, ars = 0.02, 5e-3
+    xs = np.concatenate([np.logspace(-5, 3.5, 3000), np.linspace(0.85, 1.2, 500), np.linspace(3.9, 4.1, 200)])
+    ang = np.random.default_rng(3).uniform(0, 2 * np.pi, xs.size)
+    x = (0.3 + xs * Rs * np.cos(ang)).astype(np.float32)
+    y = (-0.2 + xs * Rs * np.sin(ang)).astype(np.float32)
+    p = [W.f32(v) for v in (Rs, ars, tau * Rs, 0.3, -0.2)]
+    system = W.LensSystem(W.Grid(1, 1, 1, 1.0), [("TNFW", p)], np.zeros((5, 0), np.float32),
+                          ("SERSIC", [1.0, 0.1, 1.0, 0.0, 0.0]))
+    ax, ay = sim.deflection(system, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    rx, ry = oracle.alpha("TNFW", p, x, y)
+    mag = np.hypot(rx, ry)
+    d = np.hypot(ax.cpu().numpy() - rx, ay.cpu().numpy() - ry)
+    # per-pair: relative 1e-5 of the deflection, or an absolute floor well below FP32 position rounding
+    assert np.all(d <= 1e-5 * mag + 1e-10), float((d / (mag + 1e-30)).max())
+
+
+def test_subhalo_sum_deflection_matches_oracle(sim):
+    system = W.substructure_system(21, n_sub=2500, nx=8, s=1, k=0)
+    x, y = _points(4096, 8, -4.0, 4.0)
+    ax, ay = sim.deflection(system, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    rx, ry = oracle.alpha_system(system, x, y)
+    scale = np.abs(np.concatenate([rx, ry])).max()
+    err = max(np.abs(ax.cpu().numpy() - rx).max(), np.abs(ay.cpu().numpy() - ry).max()) / scale
+    assert err < 2e-6, err
+
+
+# ----------------------------------------------------------------------------- PSF
+@pytest.mark.parametrize("k,ny,nx,n", [(1, 9, 13, 1), (5, 37, 53, 3), (21, 64, 64, 2), (31, 40, 71, 1),
+                                       (3, 1, 1, 2), (45, 50, 50, 1)])
+def test_convolution_matches_oracle(sim, k, ny, nx, n):
+    rng = np.random.default_rng(k)
+    imgs = rng.random((n, ny, nx)).astype(np.float32)
+    K = rng.random((k, k)).astype(np.float32)
+    out = sim.convolve(torch.from_numpy(imgs).cuda(), K).cpu().numpy()
+    for i in range(n):
+        ref = oracle.convolve(imgs[i], K)
+        assert rel_linf(out[i], ref) < 2e-6
+
+
+def test_delta_psf_is_identity_on_gpu(sim):
+    img = np.random.default_rng(1).random((33, 47)).astype(np.float32)
+    K = np.zeros((7, 7), np.float32)
+    K[3, 3] = 1.0
+    out = sim.convolve(torch.from_numpy(img).cuda(), K).cpu().numpy()[0]
+    np.testing.assert_array_equal(out, img)
+
+
+# ----------------------------------------------------------------------------- API behaviour
+def test_host_and_device_buffers_and_tables_agree_bitwise(sim):
+    system = W.substructure_system(31, n_sub=700, nx=24, s=2, k=5)
+    a = gpu_image(sim, system)
+    host_out = np.zeros((24, 24), np.float32)
+    sim.image(system, out=[host_out])
+    dev_sub = torch.from_numpy(system.subhalos).cuda()
+    b = gpu_image(sim, system, subhalos=[dev_sub])
+    tid = sim.register_subhalos(system.subhalos)
+    c = gpu_image(sim, system, subhalo_tables=[tid])
+    np.testing.assert_array_equal(a, host_out)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+    np.testing.assert_array_equal(a, gpu_image(sim, system))  # deterministic
+
+
+def test_batch_of_uneven_systems_matches_single_calls(sim):
+    systems = W.batched_systems(5, count=6, max_sub=400, grids=(16, 24, 40))
+    outs = sim.image(systems)
+    torch.cuda.synchronize()
+    for s_, o in zip(systems, outs):
+        np.testing.assert_array_equal(o.cpu().numpy(), gpu_image(sim, s_))
+
+
+def test_invalid_arguments_are_rejected(sim):
+    from paper_2606_01547_gb300 import lenssim
+    base = W.plain_system()
+    bad = [W.LensSystem(W.Grid(60, 60, 9, 0.05), base.deflectors, base.subhalos, base.source, base.psf),
+           W.LensSystem(W.Grid(0, 60, 1, 0.05), base.deflectors, base.subhalos, base.source, base.psf),
+           W.LensSystem(base.grid, [("SIE", [1.0, 1.3, 0.0, 0.0, 0.0])], base.subhalos, base.source, base.psf),
+           W.LensSystem(base.grid, base.deflectors, base.subhalos, base.source, np.ones((4, 4), np.float32))]
+    for b in bad:
+        with pytest.raises(lenssim.LensSimError) as ei:
+            sim.image(b)
+        assert ei.value.code == lenssim.LENS_ERR_INVALID_ARG
+    # a valid call still works afterwards
+    assert rel_linf(gpu_image(sim, base), oracle.image(base)) <= 1e-5
