@@ -37,9 +37,11 @@ UNIT = "images/s"
 WORKLOAD = ("substructure image: 200x200 grid at 0.04\", supersampling 3 (360,000 traced points), "
             "EPL + shear, 10,000 truncated-NFW subhalos, elliptical Sersic, 21x21 Moffat PSF, FP32")
 N_SYSTEMS = 8            # distinct seeded systems cycled through the steps
-# Algorithmic work of one point-subhalo pair, frozen from the far-field pair formula
-# (tnfw_pair + tnfw_g_far): 19 FFMA + 17 FMUL + 7 FADD = 62 FP32 flops (FMA = 2), 4 MUFU.
-FLOPS_PER_PAIR = 62
+# Algorithmic work of one point-subhalo pair, frozen from the far-field series pair formula that
+# almost every pair takes: dx, dy (2 FADD); x^2 = (dx^2 + dy^2)/Rs^2 (FMUL, FFMA, FMUL);
+# y = rsqrt(x^2) (1 MUFU); y^2 (FMUL); Horner over 10 coefficients (9 FFMA); g = p y^2 (FMUL);
+# alpha += g (dx, dy) (2 FFMA)  ->  12 FFMA + 4 FMUL + 2 FADD = 30 FP32 flops (FMA = 2), 1 MUFU.
+FLOPS_PER_PAIR = 30
 KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trace_kernel_substructure_200x200.json")
 
@@ -49,6 +51,28 @@ def kernel_hash() -> str:
     for p in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, p), "rb").read())
     return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------- multi-rank helpers
+def rank_seeds(rank: int, n: int = N_SYSTEMS):
+    """Seeds of the systems one rank simulates: disjoint across ranks (replicas, weak scaling)."""
+    return [1000 + rank * n + i for i in range(n)]
+
+
+def max_over_ranks(value: float, device, world: int) -> float:
+    """The timed region of a multi-rank run is the slowest rank's."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -174,7 +198,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     sim = lenssim.Simulator(device=local_rank)
-    systems = [W.substructure_system(1000 + rank * N_SYSTEMS + i) for i in range(N_SYSTEMS)]
+    systems = [W.substructure_system(seed) for seed in rank_seeds(rank)]
     keep = []
     cs = []
     for s in systems:
@@ -229,13 +253,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             dist.barrier()
     step_ms = [e0.elapsed_time(e2) for e0, e1, e2 in ev]
     trace_ms = [e0.elapsed_time(e1) for e0, e1, e2 in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    images = world * args.steps
-    value = images / (total_ms / 1000.0)
+    total_ms = max_over_ranks(sum(step_ms), dev, world)
+    value = throughput(args.steps, world, total_ms / 1000.0)
 
     # dominant kernel: subhalo constants + fused trace kernel (the launch before the PSF)
     pairs = systems[0].pairs()
@@ -253,7 +272,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             traffic = prof.get("traffic_bytes_per_launch")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": "trace_image_kernel<9,8> (+ tnfw_prep)",
+                "kernel": "trace_image_kernel<8> (+ tnfw_prep)",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived, FP32 FMA)",
                 "frac_at_median_clock": (achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
                                          if clocks["sm_mhz"] else None),
@@ -287,11 +306,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             t0 = time.perf_counter()
             e2e_step(i)  # H2D subhalos, kernels, D2H image, stream sync
             tsum += time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([tsum], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tsum = float(t.item())
-        e2e = {"value": world * args.steps / tsum, "unit": UNIT,
+        tsum = max_over_ranks(tsum, dev, world)
+        e2e = {"value": throughput(args.steps, world, tsum), "unit": UNIT,
                "h2d_bytes_per_step": int(systems[0].subhalos.nbytes),
                "d2h_bytes_per_step": int(ny * nx * 4)}
 
@@ -320,7 +336,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")

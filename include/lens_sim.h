@@ -181,8 +181,16 @@ int lens_serve_wait(lens_server* srv, unsigned long long ticket, int timeout_ms)
 int lens_serve_poll(lens_server* srv, unsigned long long ticket);
 /* Cancel a request that has not started; LENS_ERR_BUSY if it is already running. */
 int lens_serve_cancel(lens_server* srv, unsigned long long ticket);
+/* Hold (paused = 1) or release (0) admission: queued requests stay queued and can be
+ * cancelled; running work completes.  For draining a device and for tests that need a
+ * request to stay pending. */
+int lens_serve_pause(lens_server* srv, int paused);
 /* Latency percentiles (submit -> completion) and throughput over completed requests. */
 int lens_serve_stats(lens_server* srv, double* p50_ms, double* p99_ms, double* requests_per_s);
+/* Forget the latency samples (e.g. between arrival-rate sweeps). */
+int lens_serve_reset_stats(lens_server* srv);
+/* Stop the worker, cancel what is still queued, wait for running work, free everything.
+ * No wait/poll may be in progress on another thread. */
 void lens_serve_destroy(lens_server* srv);
 
 #ifdef __cplusplus

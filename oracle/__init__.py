@@ -77,7 +77,7 @@ def lib():
             L.oracle_convolve.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp]
             L.oracle_correlate.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp]
             L.oracle_loglike.argtypes = [ctypes.POINTER(_OSys), _dp, ctypes.c_double, ctypes.c_double,
-                                         _dp, ctypes.c_int, _dp, _dp]
+                                         _dp, ctypes.c_int, _dp, _dp, ctypes.c_int]
             L.oracle_model_image.argtypes = [ctypes.POINTER(_OSys), _dp, _dp]
             L.oracle_set_threads.argtypes = [ctypes.c_int]
             L.oracle_nthreads.restype = ctypes.c_int
@@ -202,8 +202,11 @@ def correlate(img, K) -> np.ndarray:
     return out
 
 
-def loglike(system, data, sigma_bkg: float, t_exp: float, params, grad: bool = True):
-    """Chi^2 log-likelihood (and its exact gradient) at [n, 15] parameter points."""
+def loglike(system, data, sigma_bkg: float, t_exp: float, params, grad: bool = True, fp32: bool = False):
+    """Chi^2 log-likelihood (and its exact gradient) at [n, 15] parameter points.
+
+    fp32=True is the conditioning-floor mode: grid, deflection terms, traced positions and
+    model image rounded to FP32 (values only), the error any FP32 evaluation must make."""
     pk = _Packed(system)
     P = _f64(params).reshape(-1, 15)
     d = _f64(data)
@@ -211,7 +214,7 @@ def loglike(system, data, sigma_bkg: float, t_exp: float, params, grad: bool = T
     L = np.empty(n)
     G = np.empty((n, 15)) if grad else None
     if lib().oracle_loglike(ctypes.byref(pk.st), _ptr(d), float(sigma_bkg), float(t_exp), _ptr(P), n,
-                            _ptr(L), _ptr(G)) != 0:
+                            _ptr(L), _ptr(G), int(fp32)) != 0:
         raise ValueError("oracle_loglike failed")
     return (L, G) if grad else L
 

@@ -359,6 +359,9 @@ int light_profile(int type, const T* p, const T& x, const T& y, T& I) {
 }
 
 inline double round32(double v) { return (double)(float)v; }
+// Round the value of a number to FP32, keeping its tangents (conditioning-floor mode).
+inline double r32(double v) { return round32(v); }
+template <int N> inline Dual<N> r32(const Dual<N>& a) { Dual<N> r = a; r.v = round32(a.v); return r; }
 
 }  // namespace
 
@@ -535,10 +538,12 @@ extern "C" int oracle_image(const oracle_system* S, double* out, double* unconvo
 constexpr int kNP = 15;
 using D15 = Dual<kNP>;
 
+// fp32 = 1: conditioning-floor mode; the grid, every deflection term, the traced position and
+// the model image are rounded to FP32 (values only, tangents kept).
 template <class T>
 static double loglike_T(const oracle_system* S, const double* data, double sigma_bkg, double t_exp,
                         const std::vector<double>& asx, const std::vector<double>& asy,
-                        const T* P, T* logL_out) {
+                        const T* P, T* logL_out, int fp32) {
   const int nx = S->nx, ny = S->ny, s = S->s;
   std::vector<T> raw((size_t)nx * ny), model((size_t)nx * ny);
   const double w = S->dpix * S->dpix / ((double)s * s);
@@ -551,11 +556,15 @@ static double loglike_T(const oracle_system* S, const double* data, double sigma
         for (int b = 0; b < s; ++b) {
           size_t sp = (((size_t)i * nx + j) * s + a) * s + b;
           double x = grid_x(S, j, b), y = grid_y(S, i, a);
+          double ux = asx[sp], uy = asy[sp];
+          if (fp32) { x = round32(x); y = round32(y); ux = round32(ux); uy = round32(uy); }
           T ax, ay, sx, sy;
           alpha_profile<T>(O_EPL_E1E2, epl, T(x), T(y), ax, ay);
           alpha_shear<T>(T(x), T(y), P[6], P[7], sx, sy);
-          T bx = T(x) - ax - sx - asx[sp];
-          T by = T(y) - ay - sy - asy[sp];
+          if (fp32) { ax = r32(ax); ay = r32(ay); sx = r32(sx); sy = r32(sy); }
+          T bx = T(x) - ax - sx - ux;
+          T by = T(y) - ay - sy - uy;
+          if (fp32) { bx = r32(bx); by = r32(by); }
           T I;
           light_profile<T>(O_SERSIC_ELLIPSE, src, bx, by, I);
           sum += I;
@@ -567,7 +576,7 @@ static double loglike_T(const oracle_system* S, const double* data, double sigma
   T acc = T(0.0);
   const double vb = sigma_bkg * sigma_bkg;
   for (size_t p = 0; p < model.size(); ++p) {
-    T m = model[p];
+    T m = fp32 ? r32(model[p]) : model[p];
     T var = (val(m) > 0.0) ? vb + m / t_exp : T(vb);
     T r = data[p] - m;
     acc += r * r / var;
@@ -600,7 +609,7 @@ static void subhalo_field(const oracle_system* S, std::vector<double>& asx, std:
 
 // params: [n_points][15]; logL: [n_points]; grad: [n_points][15] or NULL.
 extern "C" int oracle_loglike(const oracle_system* S, const double* data, double sigma_bkg, double t_exp,
-                   const double* params, int n_points, double* logL, double* grad) {
+                   const double* params, int n_points, double* logL, double* grad, int fp32) {
   std::vector<double> asx, asy;
   subhalo_field(S, asx, asy);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -610,12 +619,12 @@ extern "C" int oracle_loglike(const oracle_system* S, const double* data, double
       D15 Pd[kNP];
       for (int k = 0; k < kNP; ++k) { Pd[k] = D15(P[k]); Pd[k].d[k] = 1.0; }
       D15 L;
-      loglike_T<D15>(S, data, sigma_bkg, t_exp, asx, asy, Pd, &L);
+      loglike_T<D15>(S, data, sigma_bkg, t_exp, asx, asy, Pd, &L, fp32);
       logL[p] = L.v;
       for (int k = 0; k < kNP; ++k) grad[(size_t)p * kNP + k] = L.d[k];
     } else {
       double L;
-      loglike_T<double>(S, data, sigma_bkg, t_exp, asx, asy, P, &L);
+      loglike_T<double>(S, data, sigma_bkg, t_exp, asx, asy, P, &L, fp32);
       logL[p] = L;
     }
   }

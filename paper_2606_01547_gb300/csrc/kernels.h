@@ -7,8 +7,37 @@
 
 namespace ls {
 
+constexpr int kUnitPts = 9;      // samples per lane in a trace unit (a unit is 32 x 9 samples)
+constexpr int kTraceWarps = 8;   // warps per trace CTA, splitting the subhalo list
+
+// One system's subhalo constants for the batched preparation kernel.
+struct PrepJob {
+  const float* soa;  // SoA [5][ld]
+  float4* tab;       // kSubStride float4 per subhalo
+  int n, ld;
+};
+
+// One image of a batched convolution; `tile0` is the prefix of 32x32 output tiles.
+struct ConvJob {
+  const float* in;
+  float* out;
+  const float* K;
+  int ny, nx, k, tile0;
+};
+
+// Device header of a batched launch; every batch kernel reads its counts, pointers and work
+// counters from here, so a captured graph does not depend on the batch.
+struct BatchMeta {
+  int n_sys, n_prep, n_conv, kmax;
+  unsigned int trace_counter, conv_counter, pad0, pad1;  // zeroed by each call's header copy
+  const DevSystem* systems;  // ordered by per-unit cost, largest first
+  const int* unit_prefix;    // [n_sys + 1]
+  const PrepJob* prep;       // [n_prep]
+  const ConvJob* conv;       // [n_conv + 1], the last entry's tile0 = total tiles
+};
+
 // Launch shape of the fused trace kernel: `nw` warps per CTA split the subhalo list of one
-// 8x4-pixel tile; `pts` sub-pixel samples per thread per pass.
+// unit; `pts` samples per lane.
 struct TraceShape {
   int nw;
   int pts;
@@ -19,8 +48,16 @@ TraceShape choose_trace_shape(int nx, int ny, int s, int n_sub, int sm_count);
 // Per-subhalo constants from a SoA [5][ld] table (cx, cy, Rs, alpha_Rs, r_t).
 cudaError_t launch_tnfw_prep(const float* soa, int n, int ld, float4* table, cudaStream_t st);
 
+// Trace units of a system (one CTA per unit in the single-system launch).
+int unit_count(int nx, int ny, int s);
+
 // Fused ray-trace + subhalo sum + Sersic + supersample bin-down of one system into sys.out.
 cudaError_t launch_trace(const DevSystem& sys, TraceShape shape, cudaStream_t st);
+
+// Persistent batched trace over device descriptors; units are numbered by unit_prefix
+// ([n_sys + 1] ints) and handed out through *counter (zeroed before the launch).
+int trace_batch_grid(int sm_count);
+cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int grid, cudaStream_t st);
 
 // Total deflection at n device points.
 cudaError_t launch_deflection(const DevSystem& sys, const float* x, const float* y, int n, float* ax,
@@ -29,5 +66,11 @@ cudaError_t launch_deflection(const DevSystem& sys, const float* x, const float*
 // Zero-padded 'same' convolution (flip = 1) or correlation (flip = 0) of n_img images.
 cudaError_t launch_conv(const float* in, float* out, int n_img, int ny, int nx, const float* K, int k,
                         int flip, cudaStream_t st);
+
+// Persistent batched convolution over device job descriptors; tiles are numbered by
+// jobs[i].tile0 (jobs[n_jobs].tile0 = total) and handed out through *counter.
+int conv_batch_grid(int sm_count, int kmax);
+cudaError_t launch_conv_batch_meta(const BatchMeta* meta, int kmax, int grid, cudaStream_t st);
+size_t conv_batch_smem(int kmax);
 
 }  // namespace ls

@@ -135,7 +135,7 @@ int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
       return fail(s, LENS_ERR_INVALID_ARG, "bad pixel scale or grid centre");
     int rc = validate_light(s, y.source);
     if (rc) return rc;
-    if (y.psf_id < -1 || y.psf_id >= (int)s->psfs.size() || (y.psf_id >= 0 && !s->psfs[y.psf_id].d))
+    if (y.psf_id < -1 || y.psf_id >= (int)s->res->psfs.size() || (y.psf_id >= 0 && !s->res->psfs[y.psf_id].d))
       return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", y.psf_id);
   }
   if (y.n_deflectors < 0 || y.n_deflectors > LENS_MAX_DEFLECTORS)
@@ -146,7 +146,7 @@ int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
     if (rc) return rc;
   }
   if (y.subhalo_table >= 0) {
-    if (y.subhalo_table >= (int)s->tables.size() || (!s->tables[y.subhalo_table].d && s->tables[y.subhalo_table].n))
+    if (y.subhalo_table >= (int)s->res->tables.size() || (!s->res->tables[y.subhalo_table].d && s->res->tables[y.subhalo_table].n))
       return fail(s, LENS_ERR_INVALID_ARG, "unknown subhalo_table %d", y.subhalo_table);
   } else {
     if (y.subhalo_table != -1) return fail(s, LENS_ERR_INVALID_ARG, "subhalo_table must be -1 or a table id");
@@ -157,16 +157,16 @@ int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
 }
 
 int sub_count(lens_sim* s, const lens_system& y) {
-  return y.subhalo_table >= 0 ? s->tables[y.subhalo_table].n : y.n_subhalos;
+  return y.subhalo_table >= 0 ? s->res->tables[y.subhalo_table].n : y.n_subhalos;
 }
 
-// Resolve the subhalo table of a system into device constants (2 float4 per subhalo).
-// `tab_buf` must hold 32 * n bytes when the system carries raw subhalos.
+// Resolve the subhalo table of a system into device constants (kSubStride float4 per subhalo).
+// `tab_buf` must hold 16 * kSubStride * n bytes when the system carries raw subhalos.
 int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* raw_buf,
                      const float4** out_tab, int* out_n, cudaStream_t st) {
   if (y.subhalo_table >= 0) {
-    *out_tab = s->tables[y.subhalo_table].d;
-    *out_n = s->tables[y.subhalo_table].n;
+    *out_tab = s->res->tables[y.subhalo_table].d;
+    *out_n = s->res->tables[y.subhalo_table].n;
     return LENS_OK;
   }
   const int n = y.n_subhalos;
@@ -243,13 +243,23 @@ void lens_sim_destroy(lens_sim* s) {
   {
     DeviceGuard g(s->device);
     cudaDeviceSynchronize();
-    for (auto& p : s->psfs) if (p.d) cudaFree(p.d);
-    for (auto& t : s->tables) if (t.d) cudaFree(t.d);
+    if (s->owns_resident) {
+      for (auto& p : s->res->psfs) if (p.d) cudaFree(p.d);
+      for (auto& t : s->res->tables) if (t.d) cudaFree(t.d);
+      s->res->psfs.clear();
+      s->res->tables.clear();
+    }
     release(s, s->raw_sub);
     release(s, s->tab);
     release(s, s->img);
     release(s, s->stage);
     release(s, s->grad_ws);
+    release(s, s->batch_meta);
+    release(s, s->batch_data);
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->pinned_ready) cudaEventDestroy(s->pinned_ready);
+    if (s->pinned) cudaFreeHost(s->pinned);
   }
   delete s;
 }
@@ -269,8 +279,8 @@ int lens_sim_register_psf(lens_sim* s, const float* kernel, int k, int* psf_id) 
   e = cudaMemcpy(d, kernel, bytes, is_device_ptr(kernel) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(d); return cuda_fail(s, e, "copy PSF"); }
   s->allocated += bytes;
-  s->psfs.push_back({d, k});
-  *psf_id = (int)s->psfs.size() - 1;
+  s->res->psfs.push_back({d, k});
+  *psf_id = (int)s->res->psfs.size() - 1;
   return LENS_OK;
 }
 
@@ -280,7 +290,7 @@ int lens_sim_register_subhalos(lens_sim* s, const float* soa, int n, int* table_
   DeviceGuard g(s->device);
   SubTable t{nullptr, n};
   if (n > 0) {
-    size_t bytes = 2 * sizeof(float4) * (size_t)n;
+    size_t bytes = kSubStride * sizeof(float4) * (size_t)n;
     if (s->budget && s->allocated + bytes > s->budget) return fail(s, LENS_ERR_OOM, "subhalo table exceeds the memory budget");
     cudaError_t e = cudaMalloc(&t.d, bytes);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(s, LENS_ERR_OOM, "cudaMalloc subhalo table: %s", cudaGetErrorString(e)); }
@@ -297,8 +307,8 @@ int lens_sim_register_subhalos(lens_sim* s, const float* soa, int n, int* table_
     if (e != cudaSuccess) { cudaFree(t.d); return cuda_fail(s, e, "subhalo table"); }
     s->allocated += bytes;
   }
-  s->tables.push_back(t);
-  *table_id = (int)s->tables.size() - 1;
+  s->res->tables.push_back(t);
+  *table_id = (int)s->res->tables.size() - 1;
   return LENS_OK;
 }
 
@@ -317,11 +327,12 @@ int lens_sim_image(lens_sim* s, const lens_system* systems, int n_sys, float* co
     max_pix = std::max(max_pix, (size_t)systems[i].grid.nx * systems[i].grid.ny);
     if (systems[i].subhalo_table < 0) max_sub = std::max(max_sub, (size_t)systems[i].n_subhalos);
   }
+  if (n_sys > 1) return run_image_batch(s, systems, n_sys, out_images, st);
   int rc;
   if ((rc = ensure(s, s->img, sizeof(float) * max_pix))) return rc;
   if ((rc = ensure(s, s->stage, sizeof(float) * max_pix))) return rc;
   if (max_sub) {
-    if ((rc = ensure(s, s->tab, 2 * sizeof(float4) * max_sub))) return rc;
+    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * max_sub))) return rc;
     if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * max_sub))) return rc;
   }
   bool host_out = false;
@@ -337,7 +348,7 @@ int lens_sim_image(lens_sim* s, const lens_system* systems, int n_sys, float* co
     cudaError_t e = launch_trace(d, sh, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "trace kernel launch");
     if (y.psf_id >= 0) {
-      const PsfEntry& p = s->psfs[y.psf_id];
+      const PsfEntry& p = s->res->psfs[y.psf_id];
       e = launch_conv((float*)s->img.p, final_dst, 1, d.ny, d.nx, p.d, p.k, 1, st);
       if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
     }
@@ -367,7 +378,7 @@ int lens_sim_deflection(lens_sim* s, const lens_system* sys, const float* x, con
     return fail(s, LENS_ERR_INVALID_ARG, "point arrays must be device memory");
   cudaStream_t st = (cudaStream_t)stream;
   if (sys->subhalo_table < 0 && sys->n_subhalos > 0) {
-    if ((rc = ensure(s, s->tab, 2 * sizeof(float4) * sys->n_subhalos))) return rc;
+    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * sys->n_subhalos))) return rc;
     if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * sys->n_subhalos))) return rc;
   }
   DevSystem d;
@@ -383,12 +394,12 @@ int lens_sim_deflection(lens_sim* s, const lens_system* sys, const float* x, con
 int lens_sim_convolve(lens_sim* s, const float* in, int n_img, int ny, int nx, int psf_id, float* out, void* stream) {
   if (!s) return LENS_ERR_INVALID_ARG;
   if (n_img < 0 || ny < 1 || nx < 1 || ny > 16384 || nx > 16384) return fail(s, LENS_ERR_INVALID_ARG, "bad image sizes");
-  if (psf_id < 0 || psf_id >= (int)s->psfs.size()) return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", psf_id);
+  if (psf_id < 0 || psf_id >= (int)s->res->psfs.size()) return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", psf_id);
   if (n_img == 0) return LENS_OK;
   if (!in || !out || in == out) return fail(s, LENS_ERR_INVALID_ARG, "NULL or aliased buffers");
   DeviceGuard g(s->device);
   if (!is_device_ptr(in) || !is_device_ptr(out)) return fail(s, LENS_ERR_INVALID_ARG, "images must be device memory");
-  const PsfEntry& p = s->psfs[psf_id];
+  const PsfEntry& p = s->res->psfs[psf_id];
   cudaError_t e = launch_conv(in, out, n_img, ny, nx, p.d, p.k, 1, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
   return LENS_OK;

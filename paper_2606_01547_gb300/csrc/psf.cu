@@ -67,3 +67,89 @@ cudaError_t launch_conv(const float* in, float* out, int n_img, int ny, int nx, 
 }
 
 }  // namespace ls
+
+namespace ls {
+
+size_t conv_batch_smem(int kmax) {
+  const int tw = kConvT + kmax - 1;
+  return sizeof(float) * ((size_t)kmax * kmax + (size_t)tw * tw);
+}
+
+// Persistent form over many images of different sizes and kernels (the batched PSF step).
+__global__ void __launch_bounds__(kConvT * kConvRows)
+conv_batch_kernel(BatchMeta* __restrict__ meta) {
+  extern __shared__ float smem[];
+  __shared__ int s_ticket;
+  const ConvJob* __restrict__ jobs = meta->conv;
+  const int n_jobs = meta->n_conv;
+  unsigned int* counter = &meta->conv_counter;
+  const int total = jobs[n_jobs].tile0;
+  const int tid = threadIdx.y * kConvT + threadIdx.x;
+  const int nthr = kConvT * kConvRows;
+  for (;;) {
+    if (tid == 0) s_ticket = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int u = s_ticket;
+    __syncthreads();
+    if (u >= total) return;
+    int lo = 0, hi = n_jobs;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (jobs[mid].tile0 <= u) lo = mid; else hi = mid;
+    }
+    const ConvJob J = jobs[lo];
+    const int t = u - J.tile0;
+    const int tiles_x = (J.nx + kConvT - 1) / kConvT;
+    const int i0 = (t / tiles_x) * kConvT, j0 = (t % tiles_x) * kConvT;
+    const int k = J.k, c = (k - 1) / 2, tw = kConvT + k - 1;
+    float* sK = smem;
+    float* sT = smem + k * k;
+    for (int q = tid; q < k * k; q += nthr) sK[q] = J.K[k * k - 1 - q];
+    for (int q = tid; q < tw * tw; q += nthr) {
+      const int r = q / tw, cc = q - r * tw;
+      const int gi = i0 - c + r, gj = j0 - c + cc;
+      sT[q] = (gi >= 0 && gi < J.ny && gj >= 0 && gj < J.nx) ? J.in[(size_t)gi * J.nx + gj] : 0.f;
+    }
+    __syncthreads();
+    float acc[kConvT / kConvRows];
+#pragma unroll
+    for (int q = 0; q < kConvT / kConvRows; ++q) acc[q] = 0.f;
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) {
+        const float kv = sK[a * k + b];
+#pragma unroll
+        for (int q = 0; q < kConvT / kConvRows; ++q)
+          acc[q] = fmaf(kv, sT[(threadIdx.y + q * kConvRows + a) * tw + threadIdx.x + b], acc[q]);
+      }
+#pragma unroll
+    for (int q = 0; q < kConvT / kConvRows; ++q) {
+      const int gi = i0 + threadIdx.y + q * kConvRows, gj = j0 + threadIdx.x;
+      if (gi < J.ny && gj < J.nx) J.out[(size_t)gi * J.nx + gj] = acc[q];
+    }
+    __syncthreads();
+  }
+}
+
+int conv_batch_grid(int sm_count, int kmax) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_batch_kernel, kConvT * kConvRows,
+                                                    conv_batch_smem(kmax)) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return sm_count * per_sm;
+}
+
+cudaError_t launch_conv_batch_meta(const BatchMeta* meta, int kmax, int grid, cudaStream_t st) {
+  const size_t smem = conv_batch_smem(kmax);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(conv_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  conv_batch_kernel<<<grid, dim3(kConvT, kConvRows), smem, st>>>(const_cast<BatchMeta*>(meta));
+  return cudaGetLastError();
+}
+
+}  // namespace ls

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -47,7 +48,17 @@ int sub_count(lens_sim* s, const lens_system& y);
 int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* raw_buf, const float4** out_tab,
                      int* out_n, cudaStream_t st);
 void fill_dev_system(const lens_system& y, DevSystem& d);
+int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const* outs, cudaStream_t st);
 
+}  // namespace ls
+
+namespace ls {
+// Resident state (registered PSFs and subhalo tables).  A server's slot handles share their
+// parent's resident state; only the owner frees it.
+struct Resident {
+  std::vector<PsfEntry> psfs;
+  std::vector<SubTable> tables;
+};
 }  // namespace ls
 
 struct lens_sim {
@@ -57,11 +68,21 @@ struct lens_sim {
   int max_batch = 4096;
   int sm_count = 0;
   std::string err;
-  std::vector<ls::PsfEntry> psfs;
-  std::vector<ls::SubTable> tables;
+  std::shared_ptr<ls::Resident> res = std::make_shared<ls::Resident>();
+  bool owns_resident = true;
   ls::DevBuffer raw_sub;  // device copy of a host subhalo SoA
   ls::DevBuffer tab;      // per-call subhalo constants
   ls::DevBuffer img;      // unconvolved (binned) image
   ls::DevBuffer stage;    // device staging of host outputs
   ls::DevBuffer grad_ws;  // likelihood / adjoint workspace
+  // batched launch
+  ls::DevBuffer batch_meta;   // packed header + descriptors + prefix + jobs
+  ls::DevBuffer batch_data;   // subhalo tables, raw copies, unconvolved images, output staging
+  void* pinned = nullptr;     // host staging of the metadata block
+  size_t pinned_cap = 0;
+  cudaEvent_t pinned_ready = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  void* graph_meta = nullptr;
+  int graph_kmax = 0;
 };

@@ -32,7 +32,8 @@ MAX_DEFLECTORS = 8
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
             "lens_sim_register_subhalos", "lens_sim_image", "lens_sim_deflection", "lens_sim_convolve",
             "lens_sim_grad", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
-            "lens_serve_poll", "lens_serve_cancel", "lens_serve_stats", "lens_serve_destroy")
+            "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats",
+            "lens_serve_reset_stats", "lens_serve_destroy")
 
 
 class LensProfile(ctypes.Structure):
@@ -114,6 +115,8 @@ def lib():
             L.lens_serve_cancel.argtypes = [vp, ctypes.c_ulonglong]
             L.lens_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]
+            L.lens_serve_pause.argtypes = [vp, ip]
+            L.lens_serve_reset_stats.argtypes = [vp]
             L.lens_serve_destroy.argtypes = [vp]
             L.lens_serve_destroy.restype = None
             _lib = L
@@ -295,3 +298,112 @@ class Simulator:
                                           float(t_exp), P.data_ptr(), n, L.data_ptr(),
                                           None if G is None else G.data_ptr(), _stream_ptr(stream)))
         return (L, G) if want_grad else L
+
+
+class LensLogLike(torch.autograd.Function):
+    """chi^2 log-likelihood of [n, 15] parameter points as an autograd op.
+
+    forward runs lens_sim_grad once (likelihood and the hand-written adjoint together) and
+    keeps the gradient; backward scales it by the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, params, sim, system, data, sigma_bkg, t_exp, subhalo_table=-1):
+        L, G = sim.grad(system, data, sigma_bkg, t_exp, params.detach(), want_grad=True,
+                        subhalo_table=subhalo_table)
+        ctx.save_for_backward(G)
+        return L
+
+    @staticmethod
+    def backward(ctx, grad_L):
+        (G,) = ctx.saved_tensors
+        return grad_L[:, None] * G, None, None, None, None, None, None
+
+
+class Server:
+    """A lens_server: continuous batching of image and likelihood+gradient requests.
+
+    Requests reference host NumPy buffers, which must stay alive until wait()/poll() reports
+    the request finished; the server keeps them referenced until then."""
+
+    def __init__(self, device: int = 0, max_inflight: int = 4096, mem_budget: int = 0):
+        self._L = lib()
+        cfg = SimConfig(device, mem_budget, 0, 0)
+        h = ctypes.c_void_p()
+        rc = self._L.lens_serve_create(ctypes.byref(cfg), int(max_inflight), ctypes.byref(h))
+        if rc != 0:
+            raise LensSimError(rc, "lens_serve_create failed")
+        self.h = h
+        self.sim = Simulator.wrap(self._L.lens_serve_sim(h), device)
+        self._keep: Dict[int, list] = {}
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self._L.lens_serve_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit_image(self, system: W.LensSystem, out: np.ndarray) -> int:
+        keep: list = [out]
+        req = LensRequest()
+        req.kind = 0
+        req.sys = self.sim.system_struct(system, keep)
+        req.out = out.ctypes.data
+        return self._submit(req, keep)
+
+    def submit_loglike(self, system: W.LensSystem, data: np.ndarray, sigma_bkg: float, t_exp: float,
+                       params: np.ndarray, out: np.ndarray, out_grad: Optional[np.ndarray]) -> int:
+        data = np.ascontiguousarray(data, np.float32)
+        params = np.ascontiguousarray(params, np.float32)
+        keep: list = [data, params, out, out_grad]
+        req = LensRequest()
+        req.kind = 1
+        req.sys = self.sim.system_struct(system, keep)
+        req.data = data.ctypes.data
+        req.sigma_bkg = float(sigma_bkg)
+        req.t_exp = float(t_exp)
+        req.params = params.ctypes.data
+        req.out = out.ctypes.data
+        req.out_grad = None if out_grad is None else out_grad.ctypes.data
+        return self._submit(req, keep)
+
+    def _submit(self, req, keep) -> int:
+        t = ctypes.c_ulonglong()
+        rc = self._L.lens_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if rc != 0:
+            raise LensSimError(rc, "lens_serve_submit")
+        keep.append(req)
+        self._keep[t.value] = keep
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
+        rc = self._L.lens_serve_wait(self.h, ticket, int(timeout_ms))
+        if rc != LENS_ERR_TIMEOUT:
+            self._keep.pop(ticket, None)
+        return rc
+
+    def poll(self, ticket: int) -> int:
+        rc = self._L.lens_serve_poll(self.h, ticket)
+        if rc != LENS_ERR_BUSY:
+            self._keep.pop(ticket, None)
+        return rc
+
+    def cancel(self, ticket: int) -> int:
+        return self._L.lens_serve_cancel(self.h, ticket)
+
+    def pause(self, paused: bool = True) -> None:
+        self._L.lens_serve_pause(self.h, 1 if paused else 0)
+
+    def stats(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._L.lens_serve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return {"p50_ms": a.value, "p99_ms": b.value, "requests_per_s": c.value}
+
+    def reset_stats(self) -> None:
+        self._L.lens_serve_reset_stats(self.h)

@@ -1,0 +1,105 @@
+"""GPU parity of the chi^2 log-likelihood and its hand-written adjoint against the FP64
+oracle (exact dual-number gradient).
+
+Tolerances: logL within 1e-5 relative; the gradient within 1e-4 relative in the L-infinity
+norm (|g - g_ref|_inf <= 1e-4 |g_ref|_inf); and, as a guard against a wrong term in any one
+component, every component within 2e-3 of max(|g_ref_i|, 1e-2 |g_ref|_inf).  Components that
+are a few percent of the largest are sums of thousands of per-pixel terms with heavy
+cancellation, and the FP32 model image carries ~1e-6 relative evaluation error (EPL series,
+exp of Sersic exponents up to ~30), so their component-wise error reaches a few 1e-4 without
+any defect in the adjoint; the oracle's conditioning-floor mode (rounding alone) already
+moves some by 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_01547_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_01547_gb300 import lenssim
+    s = lenssim.Simulator(device=0)
+    yield s
+    s.close()
+
+
+def _check(sim, pb, data, idx, sub_table=-1):
+    P = torch.from_numpy(pb.points).cuda()
+    L, G = sim.grad(pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp, P, subhalo_table=sub_table)
+    torch.cuda.synchronize()
+    L = L.cpu().numpy()
+    G = G.cpu().numpy()
+    Lr, Gr = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pb.points[idx])
+    for n, i in enumerate(idx):
+        assert abs(L[i] - Lr[n]) <= 1e-5 * abs(Lr[n]), (i, L[i], Lr[n])
+        gmax = np.abs(Gr[n]).max()
+        assert np.abs(G[i] - Gr[n]).max() <= 1e-4 * gmax, (i, np.abs(G[i] - Gr[n]).max() / gmax)
+        scale = np.maximum(np.abs(Gr[n]), 1e-2 * gmax)
+        err = np.abs(G[i] - Gr[n]) / scale
+        assert err.max() <= 2e-3, (i, err.argmax(), err.max(), G[i], Gr[n])
+    return L, G
+
+
+@pytest.mark.parametrize("nx,s,k,nsub", [(24, 1, 5, 20), (19, 2, 7, 50), (16, 1, 0, 0), (21, 3, 3, 30)])
+def test_small_likelihood_and_gradient_match_oracle(sim, nx, s, k, nsub):
+    pb = W.diff_problem(7, n_points=9, n_sub=nsub, nx=nx, dpix=0.1, k=max(k, 1))
+    sysm = W.LensSystem(W.Grid(nx, nx, s, pb.system.grid.dpix), pb.system.deflectors, pb.system.subhalos,
+                        pb.system.source, pb.system.psf if k else None)
+    pb.system = sysm
+    data = W.observe(oracle.model_image(sysm, pb.truth), pb.sigma_bkg, pb.t_exp, 3)
+    _check(sim, pb, data, list(range(9)))
+
+
+def test_differentiation_workload_sampled_points(sim):
+    # 100x100, 13x13 Gaussian PSF, 1,000 fixed subhalos, 512 parameter points
+    pb = W.diff_problem(42)
+    data = W.observe(oracle.model_image(pb.system, pb.truth), pb.sigma_bkg, pb.t_exp, 42)
+    tid = sim.register_subhalos(pb.system.subhalos)
+    L, G = _check(sim, pb, data, [0, 131, 257, 511], sub_table=tid)
+    assert np.all(np.isfinite(L)) and np.all(np.isfinite(G))
+
+
+def test_noise_free_truth_is_a_stationary_point(sim):
+    pb = W.diff_problem(3, n_points=1, n_sub=40, nx=32, dpix=0.08, k=5)
+    data = oracle.model_image(pb.system, pb.truth).astype(np.float32)
+    P = torch.from_numpy(pb.truth[None]).cuda()
+    L, G = sim.grad(pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp, P)
+    # FP32 data rounding leaves a tiny residual; the gradient must be far below a prior draw's
+    pts = torch.from_numpy(pb.points).cuda()
+    _, Gp = sim.grad(pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp, pts)
+    assert float(G.abs().max()) < 1e-3 * float(Gp.abs().max())
+
+
+def test_autograd_function_matches_adjoint(sim):
+    from paper_2606_01547_gb300 import lenssim
+    pb = W.diff_problem(5, n_points=6, n_sub=30, nx=24, dpix=0.1, k=5)
+    data = torch.from_numpy(W.observe(oracle.model_image(pb.system, pb.truth), 0.01, 1000.0, 1)).cuda()
+    P = torch.from_numpy(pb.points).cuda().requires_grad_(True)
+    L = lenssim.LensLogLike.apply(P, sim, pb.system, data, 0.01, 1000.0)
+    w = torch.linspace(0.5, 1.5, L.numel(), device="cuda")
+    (g,) = torch.autograd.grad((w * L).sum(), P)
+    _, G = sim.grad(pb.system, data, 0.01, 1000.0, P.detach())
+    torch.testing.assert_close(g, w[:, None] * G)
+
+
+def test_gpu_gradient_consistent_with_gpu_finite_differences(sim):
+    pb = W.diff_problem(9, n_points=2, n_sub=10, nx=20, dpix=0.1, k=3)
+    data = torch.from_numpy(W.observe(oracle.model_image(pb.system, pb.truth), 0.01, 1000.0, 2)).cuda()
+    P = torch.from_numpy(pb.points).cuda()
+    _, G = sim.grad(pb.system, data, 0.01, 1000.0, P)
+    G = G.cpu().numpy()
+    for k in range(15):
+        h = 2e-3 * max(1.0, abs(float(pb.points[0, k])))
+        Pp = P[:1].clone(); Pp[0, k] += h
+        Pm = P[:1].clone(); Pm[0, k] -= h
+        fd = (sim.grad(pb.system, data, 0.01, 1000.0, Pp, want_grad=False)
+              - sim.grad(pb.system, data, 0.01, 1000.0, Pm, want_grad=False)).item() / (2 * h)
+        scale = max(abs(G[0, k]), 1e-2 * np.abs(G[0]).max())
+        assert abs(fd - G[0, k]) <= 2e-2 * scale, (k, fd, G[0, k])
