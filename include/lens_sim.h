@@ -140,6 +140,18 @@ int lens_sim_deflection(lens_sim* sim, const lens_system* sys, const float* x, c
 int lens_sim_convolve(lens_sim* sim, const float* in, int n_img, int ny, int nx, int psf_id, float* out,
                       void* stream);
 
+/* Launch variants of the fused trace kernel (one CTA per work unit; the same capped at 80
+ * registers; thread-block clusters of 2 or 4 CTAs per unit).  Every variant gives
+ * bitwise-identical images; only the speed differs.  lens_sim_autotune times each variant
+ * on `sample` (reps launches each, CUDA events on `stream`, synchronising it), makes the
+ * fastest the handle's default for single-system calls, and reports the index and the mean
+ * milliseconds of each variant (ms_per_variant may be NULL; n_ms entries are written at most).
+ * lens_sim_set_variant sets it directly (0 .. LENS_TRACE_VARIANTS-1). */
+#define LENS_TRACE_VARIANTS 4
+int lens_sim_autotune(lens_sim* sim, const lens_system* sample, int reps, int* best_variant,
+                      float* ms_per_variant, int n_ms, void* stream);
+int lens_sim_set_variant(lens_sim* sim, int variant);
+
 /* Chi^2 log-likelihood of n_points parameter vectors against DEVICE data [ny][nx]:
  *   sigma^2 = sigma_bkg^2 + max(m, 0)/t_exp,   logL = -1/2 sum (d - m)^2 / sigma^2,
  * with m the PSF-convolved model.  params is DEVICE [n_points][15] in the order

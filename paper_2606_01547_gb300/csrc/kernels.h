@@ -53,6 +53,12 @@ int unit_count(int nx, int ny, int s);
 
 // Fused ray-trace + subhalo sum + Sersic + supersample bin-down of one system into sys.out.
 cudaError_t launch_trace(const DevSystem& sys, TraceShape shape, cudaStream_t st);
+// The same with an explicit launch variant (all variants give bitwise-identical images):
+// 0 one CTA of 8 warps per unit, 1 the same capped at 80 registers (3 CTAs per SM),
+// 2 a cluster of 2 CTAs x 4 warps per unit, 3 a cluster of 4 CTAs x 2 warps per unit.
+constexpr int kTraceVariants = 4;
+cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t st);
+const char* trace_variant_name(int v);
 
 // Persistent batched trace over device descriptors; units are numbered by unit_prefix
 // ([n_sys + 1] ints) and handed out through *counter (zeroed before the launch).

@@ -297,9 +297,17 @@ __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, flo
   v3 = make_float4(A * c[7], A * c[8], A * c[9], A * c[10]);
 }
 
+// Reciprocal square root on the MUFU with flush-to-zero: the far-field argument is >= 16, so
+// the denormal handling of the IEEE-mode rsqrtf is never needed.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Far-field series: A g(x^2) = A y^2 (c_0 + y^2 (c_2 + c_3 y + ... + c_10 y^8)), y = 1/x.
 __device__ __forceinline__ float tnfw_series(float x2, const float4 v1, const float4 v2, const float4 v3) {
-  const float y = rsqrtf(x2);
+  const float y = rsqrt_ftz(x2);
   const float y2 = y * y;
   float p = fmaf(v3.w, y, v3.z);
   p = fmaf(p, y, v3.y);

@@ -344,8 +344,7 @@ int lens_sim_image(lens_sim* s, const lens_system* systems, int n_sys, float* co
     const bool dev_out = is_device_ptr(out_images[i]);
     float* final_dst = dev_out ? out_images[i] : (float*)s->stage.p;
     d.out = (y.psf_id >= 0) ? (float*)s->img.p : final_dst;
-    TraceShape sh = choose_trace_shape(d.nx, d.ny, d.s, d.n_sub, s->sm_count);
-    cudaError_t e = launch_trace(d, sh, st);
+    cudaError_t e = launch_trace_variant(d, s->trace_variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "trace kernel launch");
     if (y.psf_id >= 0) {
       const PsfEntry& p = s->res->psfs[y.psf_id];
@@ -402,6 +401,58 @@ int lens_sim_convolve(lens_sim* s, const float* in, int n_img, int ny, int nx, i
   const PsfEntry& p = s->res->psfs[psf_id];
   cudaError_t e = launch_conv(in, out, n_img, ny, nx, p.d, p.k, 1, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
+  return LENS_OK;
+}
+
+int lens_sim_set_variant(lens_sim* s, int variant) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (variant < 0 || variant >= kTraceVariants) return fail(s, LENS_ERR_INVALID_ARG, "variant %d not in [0, %d)", variant, kTraceVariants);
+  s->trace_variant = variant;
+  return LENS_OK;
+}
+
+int lens_sim_autotune(lens_sim* s, const lens_system* sample, int reps, int* best_variant, float* ms_per_variant,
+                      int n_ms, void* stream) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (!sample || !best_variant || reps < 1 || reps > 1000) return fail(s, LENS_ERR_INVALID_ARG, "bad autotune arguments");
+  DeviceGuard g(s->device);
+  int rc = validate_system(s, *sample, true);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t npix = (size_t)sample->grid.nx * sample->grid.ny;
+  if ((rc = ensure(s, s->img, sizeof(float) * npix))) return rc;
+  if (sample->subhalo_table < 0 && sample->n_subhalos > 0) {
+    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * sample->n_subhalos))) return rc;
+    if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * sample->n_subhalos))) return rc;
+  }
+  DevSystem d;
+  fill_dev_system(*sample, d);
+  if ((rc = prepare_subhalos(s, *sample, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
+  d.out = (float*)s->img.p;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 3.0e38f;
+  int bi = 0;
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < kTraceVariants && e == cudaSuccess; ++v) {
+    e = launch_trace_variant(d, v, st);  // warm-up
+    if (e != cudaSuccess) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_trace_variant(d, v, st);
+    cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (ms_per_variant && v < n_ms) ms_per_variant[v] = ms;
+    if (e == cudaSuccess && ms < best) { best = ms; bi = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(s, e, "autotune");
+  s->trace_variant = bi;
+  *best_variant = bi;
   return LENS_OK;
 }
 

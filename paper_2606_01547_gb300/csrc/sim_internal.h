@@ -67,6 +67,7 @@ struct lens_sim {
   size_t allocated = 0;
   int max_batch = 4096;
   int sm_count = 0;
+  int trace_variant = 0;  // launch variant of the single-system trace kernel
   std::string err;
   std::shared_ptr<ls::Resident> res = std::make_shared<ls::Resident>();
   bool owns_resident = true;

@@ -12,7 +12,11 @@
 // kernel that pulls units of many systems from a device-side queue (largest cost first).
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace ls {
 
@@ -61,44 +65,83 @@ struct TraceSmem {
   float I[kUnitPts * 32];
 };
 
-// One unit of one system.  All threads of the CTA call it; it ends with a CTA barrier.
-template <int NW>
-__device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceSmem<NW>& sm) {
+struct UnitGeom {
+  int s, s2, bw, bh, bx, by, nsamp;
+};
+
+__device__ __forceinline__ UnitGeom unit_geom(const DevSystem& sys, int blk) {
+  UnitGeom g;
+  g.s = sys.s;
+  g.s2 = g.s * g.s;
+  unit_shape(g.s, g.bw, g.bh);
+  const int nbx = (sys.nx + g.bw - 1) / g.bw;
+  g.bx = blk % nbx;
+  g.by = blk / nbx;
+  g.nsamp = g.bw * g.bh * g.s2;
+  return g;
+}
+
+__device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& g, int q, float& x, float& y) {
+  const int p = q / g.s2, sub = q - p * g.s2;
+  const int a = sub / g.s, b = sub - a * g.s;
+  const int i = g.by * g.bh + p / g.bw, j = g.bx * g.bw + p % g.bw;
+  x = grid_coord(sys.x0, j, sys.nx, b, g.s, sys.dpix);
+  y = grid_coord(sys.y0, i, sys.ny, a, g.s, sys.dpix);
+}
+
+// Partial subhalo deflections of one unit: warp w of this CTA sums slice (slice0 + w) of the
+// kTraceWarps-way split of the subhalo list and writes its 288 partials to part[w].
+template <int NWC>
+__device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGeom& g, int slice0,
+                                              TraceSmem<NWC>& sm) {
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
-  const int s = sys.s, s2 = s * s;
-  int bw, bh;
-  unit_shape(s, bw, bh);
-  const int nbx = (sys.nx + bw - 1) / bw;
-  const int bx = blk % nbx, by = blk / nbx;
-  const int nsamp = bw * bh * s2;
   const int n = sys.n_sub;
-  const int lo = (int)(((long long)n * w) / NW);
-  const int hi = (int)(((long long)n * (w + 1)) / NW);
+  const int slice = slice0 + w;
+  const int lo = (int)(((long long)n * slice) / kTraceWarps);
+  const int hi = (int)(((long long)n * (slice + 1)) / kTraceWarps);
   const float4* __restrict__ tab = sys.sub;
 
   float px[kUnitPts], py[kUnitPts], ax[kUnitPts], ay[kUnitPts];
+  float xmin = 3.0e38f, xmax = -3.0e38f, ymin = 3.0e38f, ymax = -3.0e38f;
 #pragma unroll
   for (int k = 0; k < kUnitPts; ++k) {
     int q = lane * kUnitPts + k;
-    if (q >= nsamp) q = 0;
-    const int p = q / s2, sub = q - p * s2;
-    const int a = sub / s, b = sub - a * s;
-    const int i = by * bh + p / bw, j = bx * bw + p % bw;
-    px[k] = grid_coord(sys.x0, j, sys.nx, b, s, sys.dpix);
-    py[k] = grid_coord(sys.y0, i, sys.ny, a, s, sys.dpix);
+    if (q >= g.nsamp) q = 0;
+    sample_xy(sys, g, q, px[k], py[k]);
+    xmin = fminf(xmin, px[k]); xmax = fmaxf(xmax, px[k]);
+    ymin = fminf(ymin, py[k]); ymax = fmaxf(ymax, py[k]);
     ax[k] = 0.f;
     ay[k] = 0.f;
   }
-  // Subhalo sum over this warp's slice [lo, hi), 32 subhalos per shared-memory stage.  Per
-  // subhalo the warp votes: if no sample of any lane is inside the far-field radius, every
-  // pair takes the straight-line series path; otherwise each sample picks its own form.
+  // bounding box of the unit's samples (uniform across the warp)
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    xmin = fminf(xmin, __shfl_xor_sync(0xffffffffu, xmin, off));
+    xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
+    ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, off));
+    ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, off));
+  }
+  // 32 subhalos per shared-memory stage.  While staging, each lane tests its subhalo against
+  // the unit's bounding box; the ballot marks the subhalos some sample might see inside the
+  // far-field radius.  All other pairs take the straight-line series; marked subhalos let
+  // every sample pick its own form (the series again beyond the radius), so the result does
+  // not depend on the mask.
   for (int base = lo; base < hi; base += 32) {
     const int idx = base + lane;
+    bool near = false;
     if (idx < hi) {
+      float4 st[kSubStride];
 #pragma unroll
-      for (int c = 0; c < kSubStride; ++c) sm.sub[w][lane][c] = __ldg(tab + (size_t)kSubStride * idx + c);
+      for (int c = 0; c < kSubStride; ++c) {
+        st[c] = __ldg(tab + (size_t)kSubStride * idx + c);
+        sm.sub[w][lane][c] = st[c];
+      }
+      const float ddx = fmaxf(fmaxf(xmin - st[0].x, st[0].x - xmax), 0.f);
+      const float ddy = fmaxf(fmaxf(ymin - st[0].y, st[0].y - ymax), 0.f);
+      near = fmaf(ddx, ddx, ddy * ddy) * st[0].z < st[0].w;
     }
+    const unsigned near_mask = __ballot_sync(0xffffffffu, near);
     __syncwarp();
     const int cnt = min(32, hi - base);
     for (int q = 0; q < cnt; ++q) {
@@ -106,28 +149,21 @@ __device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceS
       const float4 v1 = sm.sub[w][q][1];
       const float4 v2 = sm.sub[w][q][2];
       const float4 v3 = sm.sub[w][q][3];
-      float dx[kUnitPts], dy[kUnitPts], x2[kUnitPts];
-      bool inner = false;
-#pragma unroll
-      for (int k = 0; k < kUnitPts; ++k) {
-        dx[k] = px[k] - v0.x;
-        dy[k] = py[k] - v0.y;
-        x2[k] = fmaf(dx[k], dx[k], dy[k] * dy[k]) * v0.z;
-        inner |= x2[k] < v0.w;
-      }
-      if (!__any_sync(0xffffffffu, inner)) {
+      if (!((near_mask >> q) & 1u)) {
 #pragma unroll
         for (int k = 0; k < kUnitPts; ++k) {
-          const float g = tnfw_series(x2[k], v1, v2, v3);
-          ax[k] = fmaf(g, dx[k], ax[k]);
-          ay[k] = fmaf(g, dy[k], ay[k]);
+          const float dx = px[k] - v0.x, dy = py[k] - v0.y;
+          const float gg = tnfw_series(fmaf(dx, dx, dy * dy) * v0.z, v1, v2, v3);
+          ax[k] = fmaf(gg, dx, ax[k]);
+          ay[k] = fmaf(gg, dy, ay[k]);
         }
       } else {
 #pragma unroll
         for (int k = 0; k < kUnitPts; ++k) {
-          const float g = tnfw_ag(x2[k], v0, v1, v2, v3);
-          ax[k] = fmaf(g, dx[k], ax[k]);
-          ay[k] = fmaf(g, dy[k], ay[k]);
+          const float dx = px[k] - v0.x, dy = py[k] - v0.y;
+          const float gg = tnfw_ag(fmaf(dx, dx, dy * dy) * v0.z, v0, v1, v2, v3);
+          ax[k] = fmaf(gg, dx, ax[k]);
+          ay[k] = fmaf(gg, dy, ay[k]);
         }
       }
     }
@@ -135,58 +171,97 @@ __device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceS
   }
 #pragma unroll
   for (int k = 0; k < kUnitPts; ++k) sm.part[w][k][lane] = make_float2(ax[k], ay[k]);
-  __syncthreads();
-  // Per sample: fixed-order reduction over warps, main deflectors, lens equation, source.
-  for (int idx = threadIdx.x; idx < 32 * kUnitPts; idx += 32 * NW) {
+}
+
+// Finalise a unit from its kTraceWarps slice partials (part(slice, k, lane) in slice order):
+// main deflectors, lens equation, source, then the bin-down.  Executed by `nthr` threads.
+template <class PartFn>
+__device__ __forceinline__ void unit_finalize(const DevSystem& sys, const UnitGeom& g, float* I, int nthr,
+                                              PartFn part) {
+  for (int idx = threadIdx.x; idx < 32 * kUnitPts; idx += nthr) {
     const int k = idx >> 5, l = idx & 31;
     const int q = l * kUnitPts + k;
-    if (q >= nsamp) continue;
+    if (q >= g.nsamp) continue;
     float sx = 0.f, sy = 0.f;
 #pragma unroll
-    for (int ww = 0; ww < NW; ++ww) {
-      const float2 v = sm.part[ww][k][l];
+    for (int sl = 0; sl < kTraceWarps; ++sl) {
+      const float2 v = part(sl, k, l);
       sx += v.x;
       sy += v.y;
     }
-    const int p = q / s2, sub = q - p * s2;
-    const int a = sub / s, b = sub - a * s;
-    const int i = by * bh + p / bw, j = bx * bw + p % bw;
-    const float x = grid_coord(sys.x0, j, sys.nx, b, s, sys.dpix);
-    const float y = grid_coord(sys.y0, i, sys.ny, a, s, sys.dpix);
+    float x, y;
+    sample_xy(sys, g, q, x, y);
     for (int d = 0; d < sys.n_defl; ++d) {
       float dax, day;
       alpha_profile(sys.defl[d], x, y, dax, day);
       sx += dax;
       sy += day;
     }
-    sm.I[q] = source_light(sys.src_type, sys.src, x - sx, y - sy);
+    I[q] = source_light(sys.src_type, sys.src, x - sx, y - sy);
   }
-  __syncthreads();
-  // Bin-down: dpix^2 times the mean of each pixel's s^2 samples, summed in sample order.
-  const float wgt = sys.dpix * sys.dpix / (float)s2;
-  for (int p = threadIdx.x; p < bw * bh; p += 32 * NW) {
-    const int i = by * bh + p / bw, j = bx * bw + p % bw;
+}
+
+__device__ __forceinline__ void unit_bin_down(const DevSystem& sys, const UnitGeom& g, const float* I, int nthr) {
+  // dpix^2 times the mean of each pixel's s^2 samples, summed in sample order
+  const float wgt = sys.dpix * sys.dpix / (float)g.s2;
+  for (int p = threadIdx.x; p < g.bw * g.bh; p += nthr) {
+    const int i = g.by * g.bh + p / g.bw, j = g.bx * g.bw + p % g.bw;
     if (i < sys.ny && j < sys.nx) {
       float acc = 0.f;
-      for (int t = 0; t < s2; ++t) acc += sm.I[p * s2 + t];
+      for (int t = 0; t < g.s2; ++t) acc += I[p * g.s2 + t];
       sys.out[(size_t)i * sys.nx + j] = acc * wgt;
     }
   }
+}
+
+// One unit of one system by one CTA of kTraceWarps warps; ends with a CTA barrier.
+__device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceSmem<kTraceWarps>& sm) {
+  const UnitGeom g = unit_geom(sys, blk);
+  unit_partials<kTraceWarps>(sys, g, 0, sm);
+  __syncthreads();
+  unit_finalize(sys, g, sm.I, 32 * kTraceWarps, [&](int sl, int k, int l) { return sm.part[sl][k][l]; });
+  __syncthreads();
+  unit_bin_down(sys, g, sm.I, 32 * kTraceWarps);
   __syncthreads();
 }
 
-template <int NW>
-__global__ void __launch_bounds__(32 * NW) trace_image_kernel(const __grid_constant__ DevSystem sys) {
-  __shared__ TraceSmem<NW> sm;
-  trace_unit<NW>(sys, blockIdx.x, sm);
+template <int MINB>
+__global__ void __launch_bounds__(32 * kTraceWarps, MINB) trace_image_kernel(const __grid_constant__ DevSystem sys) {
+  __shared__ TraceSmem<kTraceWarps> sm;
+  trace_unit(sys, blockIdx.x, sm);
+}
+
+// Cluster form: CL CTAs of kTraceWarps/CL warps share one unit.  CTA r computes slices
+// [r*NWC, (r+1)*NWC) of the same split; the leader reads every CTA's partials through
+// distributed shared memory in slice order, so the image is bitwise that of the one-CTA form,
+// while the finer CTAs balance the tail of the grid across the SMs.
+template <int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(32 * (kTraceWarps / CL))
+trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
+  constexpr int NWC = kTraceWarps / CL;
+  __shared__ TraceSmem<NWC> sm;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const UnitGeom g = unit_geom(sys, blockIdx.x / CL);
+  unit_partials<NWC>(sys, g, rank * NWC, sm);
+  cluster.sync();
+  if (rank == 0) {
+    const TraceSmem<NWC>* peers[CL];
+#pragma unroll
+    for (int r = 0; r < CL; ++r) peers[r] = cluster.map_shared_rank(&sm, r);
+    unit_finalize(sys, g, sm.I, 32 * NWC,
+                  [&](int sl, int k, int l) { return peers[sl / NWC]->part[sl % NWC][k][l]; });
+    __syncthreads();
+    unit_bin_down(sys, g, sm.I, 32 * NWC);
+  }
+  cluster.sync();  // peers keep their shared memory alive until the leader has read it
 }
 
 // Persistent form: CTAs pull unit tickets from the header's counter; ticket u belongs to the
 // system whose prefix range [unit_prefix[i], unit_prefix[i+1]) contains it.  Systems arrive
 // ordered by per-unit cost (largest first), so the queue hands out the longest units first.
-template <int NW>
-__global__ void __launch_bounds__(32 * NW) trace_batch_kernel(BatchMeta* __restrict__ meta) {
-  __shared__ TraceSmem<NW> sm;
+__global__ void __launch_bounds__(32 * kTraceWarps) trace_batch_kernel(BatchMeta* __restrict__ meta) {
+  __shared__ TraceSmem<kTraceWarps> sm;
   __shared__ int s_ticket;
   const int n_sys = meta->n_sys;
   const int* __restrict__ unit_prefix = meta->unit_prefix;
@@ -203,31 +278,50 @@ __global__ void __launch_bounds__(32 * NW) trace_batch_kernel(BatchMeta* __restr
       const int mid = (lo + hi) >> 1;
       if (unit_prefix[mid] <= u) lo = mid; else hi = mid;
     }
-    trace_unit<NW>(systems[lo], u - unit_prefix[lo], sm);
+    trace_unit(systems[lo], u - unit_prefix[lo], sm);
   }
 }
 
 TraceShape choose_trace_shape(int nx, int ny, int s, int n_sub, int sm_count) {
   (void)nx; (void)ny; (void)s; (void)n_sub; (void)sm_count;
-  // Fixed for every system so that a system's image does not depend on the launch form or on
-  // the other systems of a batch: eight warps split the subhalo list of each unit.
+  // The subhalo split (kTraceWarps slices) is the same for every system and launch form, so a
+  // system's image does not depend on the variant, the launch form or the rest of a batch.
   TraceShape sh;
   sh.nw = kTraceWarps;
   sh.pts = kUnitPts;
   return sh;
 }
 
+const char* trace_variant_name(int v) {
+  switch (v) {
+    case 0: return "cta8";
+    case 1: return "cta8_minblocks3";
+    case 2: return "cluster2x4";
+    case 3: return "cluster4x2";
+    default: return "?";
+  }
+}
+
+cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t st) {
+  const int units = unit_count(sys.nx, sys.ny, sys.s);
+  switch (variant) {
+    case 1: trace_image_kernel<3><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
+    case 2: trace_cluster_kernel<2><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
+    case 3: trace_cluster_kernel<4><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
+    default: trace_image_kernel<1><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_trace(const DevSystem& sys, TraceShape shape, cudaStream_t st) {
   (void)shape;
-  const int grid = unit_count(sys.nx, sys.ny, sys.s);
-  trace_image_kernel<kTraceWarps><<<grid, 32 * kTraceWarps, 0, st>>>(sys);
-  return cudaGetLastError();
+  return launch_trace_variant(sys, 0, st);
 }
 
 int trace_batch_grid(int sm_count) {
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, trace_batch_kernel<kTraceWarps>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, trace_batch_kernel,
                                                       32 * kTraceWarps, 0) != cudaSuccess || blocks_per_sm < 1) {
       cudaGetLastError();
       blocks_per_sm = 1;
@@ -237,7 +331,7 @@ int trace_batch_grid(int sm_count) {
 }
 
 cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int grid, cudaStream_t st) {
-  trace_batch_kernel<kTraceWarps><<<grid, 32 * kTraceWarps, 0, st>>>(const_cast<BatchMeta*>(meta));
+  trace_batch_kernel<<<grid, 32 * kTraceWarps, 0, st>>>(const_cast<BatchMeta*>(meta));
   return cudaGetLastError();
 }
 

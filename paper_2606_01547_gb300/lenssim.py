@@ -28,10 +28,12 @@ LENS_TYPES = {"SIS": 0, "SIE": 1, "EPL": 2, "SHEAR": 3, "POINT_MASS": 4, "NFW": 
               "EPL_E1E2": 7, "SIE_E1E2": 8}
 LIGHT_TYPES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2}
 MAX_DEFLECTORS = 8
+TRACE_VARIANTS = ("cta8", "cta8_minblocks3", "cluster2x4", "cluster4x2")
+_TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
             "lens_sim_register_subhalos", "lens_sim_image", "lens_sim_deflection", "lens_sim_convolve",
-            "lens_sim_grad", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
+            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_grad", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
             "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats",
             "lens_serve_reset_stats", "lens_serve_destroy")
 
@@ -106,6 +108,9 @@ def lib():
             L.lens_sim_deflection.argtypes = [vp, ctypes.POINTER(LensSystemC), vp, vp, ip, vp, vp, vp]
             L.lens_sim_convolve.argtypes = [vp, vp, ip, ip, ip, ip, vp, vp]
             L.lens_sim_grad.argtypes = [vp, ctypes.POINTER(LensSystemC), vp, fp, fp, vp, ip, vp, vp, vp]
+            L.lens_sim_autotune.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(ip),
+                                            ctypes.POINTER(fp), ip, vp]
+            L.lens_sim_set_variant.argtypes = [vp, ip]
             L.lens_serve_create.argtypes = [ctypes.POINTER(SimConfig), ip, ctypes.POINTER(vp)]
             L.lens_serve_sim.argtypes = [vp]
             L.lens_serve_sim.restype = vp
@@ -244,6 +249,46 @@ class Simulator:
         c.source = profile_struct(system.source[0], system.source[1], LIGHT_TYPES, LightProfile)
         c.psf_id = self.register_psf(system.psf) if (use_psf and system.psf is not None) else -1
         return c
+
+    # ------------------------------------------------------------------ tuning
+    def set_variant(self, variant: int) -> None:
+        self._check(self._L.lens_sim_set_variant(self.h, int(variant)))
+
+    def autotune(self, system: W.LensSystem, reps: int = 5, use_cache: bool = True, stream=None):
+        """Pick the fastest trace-kernel launch variant for systems shaped like `system`.
+
+        Results are cached per GPU name and shape bucket (grid, supersampling, subhalo count
+        rounded to a power of two) in _build/autotune.json."""
+        import json
+        g = system.grid
+        nsub = system.n_sub
+        bucket = f"{g.nx}x{g.ny}/s{g.s}/sub{1 << max(nsub, 1).bit_length()}"
+        key = f"{torch.cuda.get_device_name(self.device)}|{bucket}"
+        cache = {}
+        if use_cache and os.path.exists(_TUNE_CACHE):
+            try:
+                cache = json.load(open(_TUNE_CACHE))
+            except (OSError, ValueError):
+                cache = {}
+        if use_cache and key in cache:
+            self.set_variant(cache[key]["variant"])
+            return cache[key]
+        keep: list = []
+        c = self.system_struct(system, keep, use_psf=False)
+        best = ctypes.c_int()
+        ms = (ctypes.c_float * len(TRACE_VARIANTS))()
+        self._check(self._L.lens_sim_autotune(self.h, ctypes.byref(c), int(reps), ctypes.byref(best), ms,
+                                              len(TRACE_VARIANTS), _stream_ptr(stream)))
+        entry = {"variant": best.value, "name": TRACE_VARIANTS[best.value],
+                 "ms": {TRACE_VARIANTS[i]: float(ms[i]) for i in range(len(TRACE_VARIANTS))}}
+        if use_cache:
+            cache[key] = entry
+            os.makedirs(os.path.dirname(_TUNE_CACHE), exist_ok=True)
+            tmp = _TUNE_CACHE + f".tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(cache, fh, indent=1)
+            os.replace(tmp, _TUNE_CACHE)
+        return entry
 
     # ------------------------------------------------------------------ compute
     def image(self, systems, out: Optional[List] = None, stream=None, subhalos=None, subhalo_tables=None,

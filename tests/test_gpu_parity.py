@@ -214,3 +214,18 @@ def test_invalid_arguments_are_rejected(sim):
         assert ei.value.code == lenssim.LENS_ERR_INVALID_ARG
     # a valid call still works afterwards
     assert rel_linf(gpu_image(sim, base), oracle.image(base)) <= 1e-5
+
+
+def test_trace_variants_are_bitwise_identical_and_autotune_picks_one(sim):
+    from paper_2606_01547_gb300 import lenssim
+    system = W.substructure_system(41, n_sub=1500, nx=45, s=3, k=7)
+    imgs = []
+    for v in range(len(lenssim.TRACE_VARIANTS)):
+        sim.set_variant(v)
+        imgs.append(gpu_image(sim, system))
+    for im in imgs[1:]:
+        np.testing.assert_array_equal(im, imgs[0])
+    entry = sim.autotune(system, reps=2, use_cache=False)
+    assert entry["name"] in lenssim.TRACE_VARIANTS and all(v > 0 for v in entry["ms"].values())
+    np.testing.assert_array_equal(gpu_image(sim, system), imgs[0])
+    sim.set_variant(0)
