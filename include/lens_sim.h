@@ -162,6 +162,33 @@ int lens_sim_set_variant(lens_sim* sim, int variant);
 int lens_sim_grad(lens_sim* sim, const lens_system* sys, const float* data, float sigma_bkg, float t_exp,
                   const float* params, int n_points, float* out_logL, float* out_grad, void* stream);
 
+/* ---------------------------------------------------------------- allocation-free form
+ * The paper has no counterpart to this entry point; it is a deployment convenience.
+ * lens_sim_image_noalloc simulates one system with the same kernels as lens_sim_image, for
+ * callers that cannot allocate device memory: applications whose device memory is reserved
+ * up front by their own pool allocator, and latency-critical loops that forbid
+ * cudaMalloc/cudaFree after start-up because those calls can synchronise the whole device.
+ * It takes no handle and calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch (per-subhalo constants and the unconvolved image) is one fixed array of
+ * LENS_NOALLOC_SCRATCH_BYTES of device memory that every GPU loading the library holds until
+ * the process exits.
+ *  - sys: grid, HOST deflector list, source; subhalos in DEVICE memory (SoA [5][n]);
+ *    subhalo_table must be -1; psf_id is ignored.
+ *  - psf: DEVICE pointer to an odd k x k kernel (1 <= k <= LENS_MAX_PSF), or NULL (or k = 0)
+ *    to skip the PSF step.  out_image: caller-owned DEVICE buffer of ny*nx floats.
+ *  - n_subhalos > LENS_NOALLOC_MAX_SUBHALOS or nx*ny > LENS_NOALLOC_MAX_PIXELS returns
+ *    LENS_ERR_OOM with nothing launched; bad arguments return LENS_ERR_INVALID_ARG and a
+ *    failed CUDA call LENS_ERR_CUDA (there is no handle, hence no error text).
+ *  - The first call on each device, made with that device current, looks up the array's
+ *    device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array, which keeps the last call's contents; each call writes
+ *    everything it reads.  Calls that overlap on the GPU (different streams, or several host
+ *    threads) race on the array: serialise them on one stream. */
+#define LENS_NOALLOC_MAX_SUBHALOS 20000
+#define LENS_NOALLOC_MAX_PIXELS (512 * 512)
+#define LENS_NOALLOC_SCRATCH_BYTES (LENS_NOALLOC_MAX_SUBHALOS * 64 + LENS_NOALLOC_MAX_PIXELS * 4)
+int lens_sim_image_noalloc(const lens_system* sys, const float* psf, int k, float* out_image, void* stream);
+
 /* ---------------------------------------------------------------- serving
  * A server owns its own lens_sim state, streams and a worker thread that admits requests
  * by a device-memory budget, batches what is waiting, and overlaps batches on the device.

@@ -33,7 +33,7 @@ _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
 
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
             "lens_sim_register_subhalos", "lens_sim_image", "lens_sim_deflection", "lens_sim_convolve",
-            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_grad", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
+            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_grad", "lens_sim_image_noalloc", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
             "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats",
             "lens_serve_reset_stats", "lens_serve_destroy")
 
@@ -111,6 +111,7 @@ def lib():
             L.lens_sim_autotune.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(ip),
                                             ctypes.POINTER(fp), ip, vp]
             L.lens_sim_set_variant.argtypes = [vp, ip]
+            L.lens_sim_image_noalloc.argtypes = [ctypes.POINTER(LensSystemC), vp, ip, vp, vp]
             L.lens_serve_create.argtypes = [ctypes.POINTER(SimConfig), ip, ctypes.POINTER(vp)]
             L.lens_serve_sim.argtypes = [vp]
             L.lens_serve_sim.restype = vp
