@@ -314,6 +314,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
+        extras["psf_conv"] = conv_extra(sim, W, dev)
         extras["batched"] = batched_extra(sim, lenssim, W, dev, args.batch_systems)
         extras["differentiation"] = grad_extra(sim, W, dev)
         extras["serving"] = serving_extra(lenssim, W, args.serve_rates, args.serve_seconds)
@@ -388,6 +389,39 @@ def batched_extra(sim, lenssim, W, dev, n_sys: int):
                         "PSF 5..31, one graph launch vs per-image calls with a sync each"}
 
 
+def conv_extra(sim, W, dev, n_img: int = 4096, size: int = 256):
+    """PSF step alone on a batch larger than L2: n_img x size^2 FP32 images through
+    lens_sim_convolve.  k = 5 is HBM-bound (algorithmic 8 B per pixel: one read, one write);
+    k = 21 is FP32-bound (2 k^2 flops per pixel)."""
+    import torch
+    x = torch.rand((n_img, size, size), device=dev)
+    y = torch.empty_like(x)
+    st = torch.cuda.current_stream()
+    res = {}
+    for k in (5, 21):
+        K = W.gaussian_psf(0.1, 0.04, k) if k == 5 else W.moffat_psf(3.0, 0.12, 0.04, k)
+        pid = sim.register_psf(K)
+        sim.convolve(x, pid, out=y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(st)
+        for _ in range(reps):
+            sim.convolve(x, pid, out=y)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0 / reps
+        px = n_img * size * size
+        res[f"k{k}"] = {"ms": t * 1e3, "gbs_algorithmic": 8.0 * px / t / 1e9,
+                        "tflops": 2.0 * k * k * px / t / 1e12}
+    res["hbm_peak_gbs_measured"] = 6780.0
+    res["k5_frac_of_measured_hbm"] = res["k5"]["gbs_algorithmic"] / 6780.0
+    res["workload"] = f"{n_img} x {size}^2 FP32 images, lens_sim_convolve, inputs larger than L2"
+    del x, y
+    torch.cuda.empty_cache()
+    return res
+
+
 def grad_extra(sim, W, dev):
     """Differentiation workload: chi^2 logL + 15-parameter adjoint at 512 points (100x100, 13x13
     PSF, 1,000 fixed subhalos); the observation is this GPU path's own truth image plus noise."""
@@ -415,11 +449,17 @@ def grad_extra(sim, W, dev):
 
 def serving_extra(lenssim, W, rates, seconds: float):
     """Open-loop Poisson arrivals (70% image / 30% likelihood+gradient, grids 64..256, subhalos
-    0..20,000, PSF 5..31) at each rate; p50/p99 latency and completed requests/s."""
+    0..20,000, PSF 5..31) at each rate: p50/p99 latency (submit to result in host memory) and
+    completed requests/s.  The image requests of the first rate are also run one by one through
+    lens_sim_image with a synchronisation each: the plain per-image path on the same GPU."""
+    import collections
     import numpy as np
+    import torch
     out = []
+    plain = None
     for rate in rates:
-        reqs = W.serving_stream(7, rate=rate, duration=seconds)
+        dur = min(seconds, 6000.0 / rate)  # bounded number of requests (host buffers)
+        reqs = W.serving_stream(7, rate=rate, duration=dur)
         srv = lenssim.Server(device=0)
         bufs = []
         tickets = []
@@ -440,12 +480,26 @@ def serving_extra(lenssim, W, rates, seconds: float):
                 o, gr = np.empty(1, np.float32), np.empty(15, np.float32)
                 bufs += [d, p, o, gr]
                 tickets.append(srv.submit_loglike(rq.system, d, 0.01, 1000.0, p, o, gr))
-        ok = sum(1 for t in tickets if srv.wait(t, 600000) == 0)
+        codes = collections.Counter(srv.wait(t, 600000) for t in tickets)
         st = srv.stats()
-        out.append({"rate_req_per_s": rate, "requests": len(reqs), "completed_ok": ok,
+        n_img = sum(1 for rq in reqs if rq.kind == 0)
+        out.append({"rate_req_per_s": rate, "seconds": dur, "requests": len(reqs), "images": n_img,
+                    "completed_ok": codes.get(0, 0), "failed": {str(k): v for k, v in codes.items() if k != 0},
                     "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "served_req_per_s": st["requests_per_s"]})
         srv.close()
-    return out
+        if plain is None:
+            sim = lenssim.Simulator(device=0)
+            imgs = [rq.system for rq in reqs if rq.kind == 0]
+            dev_out = [torch.empty((s_.grid.ny, s_.grid.nx), device="cuda") for s_ in imgs]
+            sim.image(imgs[0], out=[dev_out[0]])
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for s_, o in zip(imgs, dev_out):
+                sim.image(s_, out=[o])
+                torch.cuda.synchronize()
+            plain = len(imgs) / (time.perf_counter() - t1)
+            sim.close()
+    return {"rates": out, "plain_images_per_s": plain}
 
 
 def main():
@@ -460,7 +514,7 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, gradient and serving lines")
     ap.add_argument("--batch-systems", type=int, default=4096)
-    ap.add_argument("--serve-rates", type=float, nargs="*", default=[300.0, 3000.0])
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[300.0, 3000.0, 12000.0])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     args = ap.parse_args()
     if args.warmup < 3:

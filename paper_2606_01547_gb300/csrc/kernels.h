@@ -73,6 +73,12 @@ cudaError_t launch_deflection(const DevSystem& sys, const float* x, const float*
 cudaError_t launch_conv(const float* in, float* out, int n_img, int ny, int nx, const float* K, int k,
                         int flip, cudaStream_t st);
 
+// TMA form of the convolution for batches of equal-size images (odd k <= 31, nx % 4 == 0,
+// 16-byte aligned buffers).  `err` is a host-mapped flag raised if a bounded wait expires.
+bool conv_tma_supported(const float* in, const float* out, int ny, int nx, int k);
+cudaError_t launch_conv_tma(const float* in, float* out, int n_img, int ny, int nx, const float* K, int k, int* err,
+                            int sm_count, cudaStream_t st);
+
 // Persistent batched convolution over device job descriptors; tiles are numbered by
 // jobs[i].tile0 (jobs[n_jobs].tile0 = total) and handed out through *counter.
 int conv_batch_grid(int sm_count, int kmax);

@@ -262,9 +262,10 @@ constexpr int kFarTerms = 10;
 constexpr int kSubStride = 4;  // float4 per subhalo in the table
 
 // Four float4 per subhalo:
-//   v0 = (cx, cy, 1/Rs^2, x_far^2 = 16 max(tau,1)^2), v1 = (tau, A, A c_0, A c_2),
-//   v2 = A (c_3, c_4, c_5, c_6), v3 = A (c_7, c_8, c_9, c_10),
-// with A = alpha_Rs tau^2 / ((1 - ln 2) Rs (tau^2+1)^2), so that alpha = A g(x^2) (dx, dy).
+//   v0 = (cx, cy, r_far^2 = 16 max(tau,1)^2 Rs^2, 1/Rs^2), v1 = (tau, A, d_0, d_2),
+//   v2 = (d_3, d_4, d_5, d_6), v3 = (d_7, d_8, d_9, d_10),
+// with A = alpha_Rs tau^2 / ((1 - ln 2) Rs (tau^2+1)^2), so that alpha = A g(x^2) (dx, dy), and
+// d_k = A c_k Rs^(k+2): the series then runs in u = 1/r with no per-pair scaling by 1/Rs^2.
 __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, float alphaRs, float rt,
                                                float4& v0, float4& v1, float4& v2, float4& v3) {
   const float tau = rt / Rs;
@@ -290,35 +291,42 @@ __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, flo
     if (2 * n + 1 <= kFarTerms) c[2 * n + 1] = kPi * (0.5f * t2m1 * a[n] + a[n + 1] - sq[n + 1] * t2pow * t2);
     t2pow *= t2;
   }
+  float d[kFarTerms + 1];
+  float rp = Rs * Rs;  // Rs^(k+2)
+  for (int k = 0; k <= kFarTerms; ++k) {
+    d[k] = A * c[k] * rp;
+    rp *= Rs;
+  }
   const float tm = fmaxf(tau, 1.f);
-  v0 = make_float4(cx, cy, 1.f / (Rs * Rs), 16.f * tm * tm);
-  v1 = make_float4(tau, A, A * c[0], A * c[2]);
-  v2 = make_float4(A * c[3], A * c[4], A * c[5], A * c[6]);
-  v3 = make_float4(A * c[7], A * c[8], A * c[9], A * c[10]);
+  v0 = make_float4(cx, cy, 16.f * tm * tm * Rs * Rs, 1.f / (Rs * Rs));
+  v1 = make_float4(tau, A, d[0], d[2]);
+  v2 = make_float4(d[3], d[4], d[5], d[6]);
+  v3 = make_float4(d[7], d[8], d[9], d[10]);
 }
 
-// Reciprocal square root on the MUFU with flush-to-zero: the far-field argument is >= 16, so
-// the denormal handling of the IEEE-mode rsqrtf is never needed.
+// Reciprocal square root on the MUFU with flush-to-zero: the far-field argument is at least
+// 16 Rs^2 > 0 and never denormal, so the IEEE-mode rsqrtf fix-up is not needed.
 __device__ __forceinline__ float rsqrt_ftz(float x) {
   float r;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
-// Far-field series: A g(x^2) = A y^2 (c_0 + y^2 (c_2 + c_3 y + ... + c_10 y^8)), y = 1/x.
-__device__ __forceinline__ float tnfw_series(float x2, const float4 v1, const float4 v2, const float4 v3) {
-  const float y = rsqrt_ftz(x2);
-  const float y2 = y * y;
-  float p = fmaf(v3.w, y, v3.z);
-  p = fmaf(p, y, v3.y);
-  p = fmaf(p, y, v3.x);
-  p = fmaf(p, y, v2.w);
-  p = fmaf(p, y, v2.z);
-  p = fmaf(p, y, v2.y);
-  p = fmaf(p, y, v2.x);
-  p = fmaf(p, y, v1.w);
-  p = fmaf(p, y2, v1.z);
-  return p * y2;
+// Far-field series from r^2: A g = u^2 (d_0 + u^2 (d_2 + d_3 u + ... + d_10 u^8)), u = 1/r,
+// the same as A y^2 sum_k c_k y^k with y = Rs/r.
+__device__ __forceinline__ float tnfw_series(float r2, const float4 v1, const float4 v2, const float4 v3) {
+  const float u = rsqrt_ftz(r2);
+  const float u2 = u * u;
+  float p = fmaf(v3.w, u, v3.z);
+  p = fmaf(p, u, v3.y);
+  p = fmaf(p, u, v3.x);
+  p = fmaf(p, u, v2.w);
+  p = fmaf(p, u, v2.z);
+  p = fmaf(p, u, v2.y);
+  p = fmaf(p, u, v2.x);
+  p = fmaf(p, u, v1.w);
+  p = fmaf(p, u2, v1.z);
+  return p * u2;
 }
 
 // Inside the series range: the closed forms (x >= 4) or the small-x forms (x < 4), times A.
@@ -330,18 +338,17 @@ static __device__ __noinline__ float tnfw_g_inner(float x2, float tau, float A) 
   return A * ((x2 >= 16.f) ? tnfw_g_far(x2, tau, t2, t2m1, C) : tnfw_g_near(x2, tau, t2, t2m1, C));
 }
 
-// A g(x^2) for one point, any x.
-__device__ __forceinline__ float tnfw_ag(float x2, const float4 v0, const float4 v1, const float4 v2,
+// A g for one pair at squared distance r2, any distance.
+__device__ __forceinline__ float tnfw_ag(float r2, const float4 v0, const float4 v1, const float4 v2,
                                         const float4 v3) {
-  return (x2 >= v0.w) ? tnfw_series(x2, v1, v2, v3) : tnfw_g_inner(x2, v1.x, v1.y);
+  return (r2 >= v0.z) ? tnfw_series(r2, v1, v2, v3) : tnfw_g_inner(r2 * v0.w, v1.x, v1.y);
 }
 
-// One point-subhalo pair accumulated into (ax, ay); tab points at the subhalo's 4 float4.
+// One point-subhalo pair accumulated into (ax, ay); v0..v3 are the subhalo's table entries.
 __device__ __forceinline__ void tnfw_pair(float px, float py, const float4 v0, const float4 v1,
                                           const float4 v2, const float4 v3, float& ax, float& ay) {
   const float dx = px - v0.x, dy = py - v0.y;
-  const float x2 = fmaf(dx, dx, dy * dy) * v0.z;
-  const float k = tnfw_ag(x2, v0, v1, v2, v3);
+  const float k = tnfw_ag(fmaf(dx, dx, dy * dy), v0, v1, v2, v3);
   ax = fmaf(k, dx, ax);
   ay = fmaf(k, dy, ay);
 }

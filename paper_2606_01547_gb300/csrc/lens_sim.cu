@@ -202,6 +202,9 @@ void fill_dev_system(const lens_system& y, DevSystem& d) {
 }
 
 DeviceGuard::DeviceGuard(int dev) {
+  // A non-fatal status left by an earlier call on this thread (e.g. "not ready" from a query)
+  // would otherwise be read back by the launch checks below as a launch failure.
+  cudaGetLastError();
   cudaGetDevice(&prev_);
   if (prev_ != dev) cudaSetDevice(dev);
   dev_ = dev;
@@ -260,6 +263,7 @@ void lens_sim_destroy(lens_sim* s) {
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->pinned_ready) cudaEventDestroy(s->pinned_ready);
     if (s->pinned) cudaFreeHost(s->pinned);
+    if (s->wait_flag_h) cudaFreeHost(s->wait_flag_h);
   }
   delete s;
 }
@@ -399,7 +403,25 @@ int lens_sim_convolve(lens_sim* s, const float* in, int n_img, int ny, int nx, i
   DeviceGuard g(s->device);
   if (!is_device_ptr(in) || !is_device_ptr(out)) return fail(s, LENS_ERR_INVALID_ARG, "images must be device memory");
   const PsfEntry& p = s->res->psfs[psf_id];
-  cudaError_t e = launch_conv(in, out, n_img, ny, nx, p.d, p.k, 1, (cudaStream_t)stream);
+  if (!s->wait_flag_h) {
+    if (cudaHostAlloc((void**)&s->wait_flag_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&s->wait_flag_d, s->wait_flag_h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (s->wait_flag_h) cudaFreeHost(s->wait_flag_h);
+      s->wait_flag_h = nullptr;
+      return fail(s, LENS_ERR_OOM, "host-mapped wait flag");
+    }
+    *s->wait_flag_h = 0;
+  }
+  if (*(volatile int*)s->wait_flag_h) {
+    *s->wait_flag_h = 0;
+    return fail(s, LENS_ERR_TIMEOUT, "a bounded wait of an earlier convolution expired");
+  }
+  cudaError_t e;
+  if (conv_tma_supported(in, out, ny, nx, p.k))
+    e = launch_conv_tma(in, out, n_img, ny, nx, p.d, p.k, s->wait_flag_d, s->sm_count, (cudaStream_t)stream);
+  else
+    e = launch_conv(in, out, n_img, ny, nx, p.d, p.k, 1, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
   return LENS_OK;
 }

@@ -1,0 +1,279 @@
+// PSF step for batches of equal-size images (lens_sim_convolve) on sm_103a: a persistent,
+// double-buffered kernel whose input tiles arrive by TMA (cp.async.bulk.tensor) into shared
+// memory, completion tracked by an mbarrier.
+//
+// Each CTA computes 64x32-output tiles; its input box is (64 + k - 1) rows of the tile plus
+// halo, with the left edge rounded down to a 16-byte boundary (TMA needs an aligned x) and
+// out-of-image elements zero-filled by the TMA unit, which is exactly the zero padding of the
+// 'same' convolution.  While one tile is computed the next is in flight.  A thread owns 2x4
+// outputs: per kernel row it reads float4 windows of the two input rows it needs, so shared
+// memory serves one float4 per ~3 FMAs, and it writes its outputs as float4.  The tap order
+// (kernel row outer, column inner) is that of the generic kernel, so the two agree bitwise.
+// Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the CTA raises a flag in
+// host-mapped memory, waits (bounded) for its copies in flight and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "kernels.h"
+
+namespace ls {
+
+namespace {
+
+constexpr int kTW = 64;        // output tile width
+constexpr int kTH = 32;        // output tile height
+constexpr int kThreads = 256;  // 16 x 16 threads, each 4 columns x 2 rows
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+constexpr int cpad(int K) { return ((K - 1) / 2 + 3) / 4 * 4; }   // left halo rounded up to 4
+constexpr int coff(int K) { return cpad(K) - (K - 1) / 2; }        // tile column of the first tap
+constexpr int box_w(int K) { return (coff(K) + kTW + K - 1 + 3) / 4 * 4; }
+constexpr int box_h(int K) { return kTH + K - 1; }
+constexpr int tile_floats(int K) { return (box_w(K) * box_h(K) + 31) / 32 * 32; }  // 128-byte multiple
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for one phase of an mbarrier.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+struct TmaConvArgs {
+  float* out;
+  const float* K;
+  int nx, ny, n_img, tiles_x, tiles_y;
+  int* err;  // host-mapped flag, raised when a bounded wait expires
+};
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) conv_tma_kernel(const __grid_constant__ CUtensorMap tin,
+                                                           const TmaConvArgs A) {
+  constexpr int BW = box_w(K), BH = box_h(K), OFF = coff(K), C = (K - 1) / 2;
+  constexpr int NV = (OFF + 4 + K - 1 + 3) / 4;  // float4 per window row
+  constexpr unsigned kBytes = BW * BH * sizeof(float);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* tile0 = (float*)smem_raw;
+  float* tile1 = tile0 + tile_floats(K);
+  float* sK = tile1 + tile_floats(K);
+  __shared__ __align__(8) unsigned long long bars[2];
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int q = tid; q < K * K; q += kThreads) sK[q] = A.K[K * K - 1 - q];  // flipped: out = sum sK . window
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const int per_img = A.tiles_x * A.tiles_y;
+  const long long total = (long long)per_img * A.n_img;
+  auto issue = [&](long long t, int s) {
+    const int z = (int)(t / per_img);
+    const int r = (int)(t - (long long)z * per_img);
+    const int i0 = (r / A.tiles_x) * kTH, j0 = (r % A.tiles_x) * kTW;
+    mbar_expect_tx(&bars[s], kBytes);
+    tma_load_3d(s ? tile1 : tile0, &tin, j0 - cpad(K), i0 - C, z, &bars[s]);
+  };
+  if (tid == 0 && (long long)blockIdx.x < total) issue(blockIdx.x, 0);
+
+  int it = 0;
+  for (long long t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+    const int s = it & 1;
+    const long long tn = t + gridDim.x;
+    if (tid == 0 && tn < total) issue(tn, s ^ 1);
+    const bool ok = mbar_wait_bounded(&bars[s], (unsigned)((it >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        *A.err = 1;
+        __threadfence_system();
+        mbar_wait_bounded(&bars[s], (unsigned)((it >> 1) & 1));
+        if (tn < total) mbar_wait_bounded(&bars[s ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+      }
+      __syncthreads();
+      return;
+    }
+    const float* T = s ? tile1 : tile0;
+    const int z = (int)(t / per_img);
+    const int r = (int)(t - (long long)z * per_img);
+    const int i0 = (r / A.tiles_x) * kTH, j0 = (r % A.tiles_x) * kTW;
+    float acc[2][4];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[rr][c] = 0.f;
+#pragma unroll 1
+    for (int a = 0; a < K; ++a) {
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const float4* row = reinterpret_cast<const float4*>(T + (2 * ty + rr + a) * BW + 4 * tx);
+        float w[4 * NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float4 f = row[v];
+          w[4 * v] = f.x;
+          w[4 * v + 1] = f.y;
+          w[4 * v + 2] = f.z;
+          w[4 * v + 3] = f.w;
+        }
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+          const float kv = sK[a * K + b];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[rr][c] = fmaf(kv, w[OFF + c + b], acc[rr][c]);
+        }
+      }
+    }
+    const int j = j0 + 4 * tx;
+    if (j < A.nx) {
+#pragma unroll
+      for (int rr = 0; rr < 2; ++rr) {
+        const int i = i0 + 2 * ty + rr;
+        if (i < A.ny)
+          *reinterpret_cast<float4*>(A.out + ((size_t)z * A.ny + i) * A.nx + j) =
+              make_float4(acc[rr][0], acc[rr][1], acc[rr][2], acc[rr][3]);
+      }
+    }
+    __syncthreads();  // the buffer is refilled two tiles later
+  }
+}
+
+template <int K>
+size_t tma_smem_bytes() {
+  return sizeof(float) * ((size_t)2 * tile_floats(K) + (size_t)K * K);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+template <int K>
+cudaError_t launch_k(const float* in, float* out, int n_img, int ny, int nx, const float* Kw, int* err, int sm_count,
+                     cudaStream_t st) {
+  auto enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)n_img};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)box_w(K), (cuuint32_t)box_h(K), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)in, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const size_t smem = tma_smem_bytes<K>();
+  static thread_local bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<K>, kThreads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  TmaConvArgs A;
+  A.out = out;
+  A.K = Kw;
+  A.nx = nx;
+  A.ny = ny;
+  A.n_img = n_img;
+  A.tiles_x = (nx + kTW - 1) / kTW;
+  A.tiles_y = (ny + kTH - 1) / kTH;
+  A.err = err;
+  const long long total = (long long)A.tiles_x * A.tiles_y * n_img;
+  const int grid = (int)std::min<long long>(total, (long long)sm_count * per_sm);
+  conv_tma_kernel<K><<<grid, kThreads, smem, st>>>(map, A);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool conv_tma_supported(const float* in, const float* out, int ny, int nx, int k) {
+  (void)ny;
+  return (k % 2) == 1 && k >= 1 && k <= 31 && (nx % 4) == 0 && ((uintptr_t)in % 16) == 0 &&
+         ((uintptr_t)out % 16) == 0 && encode_fn() != nullptr;
+}
+
+cudaError_t launch_conv_tma(const float* in, float* out, int n_img, int ny, int nx, const float* K, int k, int* err,
+                            int sm_count, cudaStream_t st) {
+  switch (k) {
+    case 1: return launch_k<1>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 3: return launch_k<3>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 5: return launch_k<5>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 7: return launch_k<7>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 9: return launch_k<9>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 11: return launch_k<11>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 13: return launch_k<13>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 15: return launch_k<15>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 17: return launch_k<17>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 19: return launch_k<19>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 21: return launch_k<21>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 23: return launch_k<23>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 25: return launch_k<25>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 27: return launch_k<27>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 29: return launch_k<29>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    case 31: return launch_k<31>(in, out, n_img, ny, nx, K, err, sm_count, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ls

@@ -196,7 +196,13 @@ void CUDART_CB slot_done_cb(void* arg) {
 
 // Completion of a slot (worker thread, lock held): results to the caller, latency, budget.
 void finish(lens_server* srv, Slot* sl) {
+  // The host callback ran after every earlier operation of the stream completed; while the
+  // callback itself retires the stream may still report "not ready", which is no error.
   cudaError_t e = cudaStreamQuery(sl->stream);
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();  // "not ready" must not linger as this thread's last error
+    e = cudaSuccess;
+  }
   const auto now = Clock::now();
   for (Req* q : sl->batch) {
     if (q->status == LENS_OK && e != cudaSuccess) q->status = LENS_ERR_CUDA;

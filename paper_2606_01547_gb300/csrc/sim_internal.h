@@ -68,6 +68,8 @@ struct lens_sim {
   int max_batch = 4096;
   int sm_count = 0;
   int trace_variant = 0;  // launch variant of the single-system trace kernel
+  int* wait_flag_h = nullptr;  // host-mapped flag raised by an expired bounded device wait
+  int* wait_flag_d = nullptr;
   std::string err;
   std::shared_ptr<ls::Resident> res = std::make_shared<ls::Resident>();
   bool owns_resident = true;

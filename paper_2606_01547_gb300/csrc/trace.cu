@@ -139,7 +139,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       }
       const float ddx = fmaxf(fmaxf(xmin - st[0].x, st[0].x - xmax), 0.f);
       const float ddy = fmaxf(fmaxf(ymin - st[0].y, st[0].y - ymax), 0.f);
-      near = fmaf(ddx, ddx, ddy * ddy) * st[0].z < st[0].w;
+      near = fmaf(ddx, ddx, ddy * ddy) < st[0].z;
     }
     const unsigned near_mask = __ballot_sync(0xffffffffu, near);
     __syncwarp();
@@ -153,7 +153,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
 #pragma unroll
         for (int k = 0; k < kUnitPts; ++k) {
           const float dx = px[k] - v0.x, dy = py[k] - v0.y;
-          const float gg = tnfw_series(fmaf(dx, dx, dy * dy) * v0.z, v1, v2, v3);
+          const float gg = tnfw_series(fmaf(dx, dx, dy * dy), v1, v2, v3);
           ax[k] = fmaf(gg, dx, ax[k]);
           ay[k] = fmaf(gg, dy, ay[k]);
         }
@@ -161,7 +161,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
 #pragma unroll
         for (int k = 0; k < kUnitPts; ++k) {
           const float dx = px[k] - v0.x, dy = py[k] - v0.y;
-          const float gg = tnfw_ag(fmaf(dx, dx, dy * dy) * v0.z, v0, v1, v2, v3);
+          const float gg = tnfw_ag(fmaf(dx, dx, dy * dy), v0, v1, v2, v3);
           ax[k] = fmaf(gg, dx, ax[k]);
           ay[k] = fmaf(gg, dy, ay[k]);
         }

@@ -169,6 +169,36 @@ def test_convolution_matches_oracle(sim, k, ny, nx, n):
         assert rel_linf(out[i], ref) < 2e-6
 
 
+@pytest.mark.parametrize("k,ny,nx,n", [(5, 256, 256, 3), (1, 33, 64, 2), (3, 70, 132, 2), (21, 200, 200, 1),
+                                       (31, 96, 100, 2), (7, 1, 4, 3), (13, 37, 68, 5)])
+def test_tma_convolution_matches_oracle(sim, k, ny, nx, n):
+    # nx % 4 == 0 and 16-byte-aligned buffers take the TMA path (ragged 64x32 tiles included)
+    rng = np.random.default_rng(100 + k)
+    imgs = rng.random((n, ny, nx)).astype(np.float32)
+    K = rng.random((k, k)).astype(np.float32)
+    out = sim.convolve(torch.from_numpy(imgs).cuda(), K).cpu().numpy()
+    for i in range(n):
+        assert rel_linf(out[i], oracle.convolve(imgs[i], K)) < 2e-6, i
+
+
+def test_tma_and_generic_convolution_agree_bitwise(sim):
+    # the same image through the TMA path (aligned) and the generic path (offset by one float)
+    rng = np.random.default_rng(7)
+    base = torch.from_numpy(rng.random((1, 64 * 65 + 1)).astype(np.float32)).cuda()
+    K = rng.random((9, 9)).astype(np.float32)
+    a = sim.convolve(base[:, :64 * 64].reshape(1, 64, 64).contiguous(), K)
+    b_in = base[:, 1:64 * 64 + 1]  # 4-byte offset: not 16-byte aligned -> generic kernel
+    b = torch.empty((1, 64, 64), device="cuda")
+    from paper_2606_01547_gb300 import lenssim
+    pid = sim.register_psf(K)
+    lenssim.lib().lens_sim_convolve(sim.h, b_in.data_ptr(), 1, 64, 64, pid, b.data_ptr(),
+                                    int(torch.cuda.current_stream().cuda_stream))
+    ref_b = sim.convolve(base[:, 1:64 * 64 + 1].reshape(1, 64, 64).contiguous(), K)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(b.cpu().numpy(), ref_b.cpu().numpy())
+    assert a.shape == b.shape
+
+
 def test_delta_psf_is_identity_on_gpu(sim):
     img = np.random.default_rng(1).random((33, 47)).astype(np.float32)
     K = np.zeros((7, 7), np.float32)
