@@ -43,7 +43,7 @@ N_SYSTEMS = 8            # distinct seeded systems cycled through the steps
 # alpha += g (dx, dy) (2 FFMA)  ->  12 FFMA + 4 FMUL + 2 FADD = 30 FP32 flops (FMA = 2), 1 MUFU.
 FLOPS_PER_PAIR = 30
 KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh")
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trace_kernel_substructure_200x200.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trace_kernel_substructure_200x200_traffic.txt")
 
 
 def kernel_hash() -> str:
@@ -229,7 +229,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         if rc:
             raise lenssim.LensSimError(rc, sim.last_error())
 
-    tune = sim.autotune(systems[0], reps=3, use_cache=False)  # untimed: picks the trace launch variant
+    if args.variant >= 0:  # fixed variant (profiling runs)
+        sim.set_variant(args.variant)
+        tune = {"variant": args.variant, "name": lenssim.TRACE_VARIANTS[args.variant], "ms": None}
+    else:
+        tune = sim.autotune(systems[0], reps=3, use_cache=False)  # untimed: picks the trace launch variant
     for i in range(args.warmup):
         flush.fill_(float(i))
         step(i)
@@ -268,9 +272,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     achieved = pairs * FLOPS_PER_PAIR / avg_trace_s / 1e12
     traffic = None
     if os.path.exists(PROFILE_TRAFFIC):
-        prof = json.load(open(PROFILE_TRAFFIC))
-        if prof.get("kernel_hash") == kernel_hash():
-            traffic = prof.get("traffic_bytes_per_launch")
+        prof = dict(l.split(": ", 1) for l in open(PROFILE_TRAFFIC).read().splitlines()
+                    if ": " in l and not l.startswith("#"))
+        if prof.get("kernel_hash") == kernel_hash() and tune["variant"] == 3:
+            traffic = int(prof["traffic_bytes_per_launch"])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": "trace_image_kernel<8> (+ tnfw_prep)",
@@ -316,7 +321,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     if rank == 0 and world == 1 and not args.no_extras:
         extras["psf_conv"] = conv_extra(sim, W, dev)
         extras["batched"] = batched_extra(sim, lenssim, W, dev, args.batch_systems)
+        extras["batched_small_systems"] = batched_extra(sim, lenssim, W, dev, args.batch_systems, small=True)
         extras["differentiation"] = grad_extra(sim, W, dev)
+        extras["fitting"] = fitting_extra(sim, W, dev)
         extras["serving"] = serving_extra(lenssim, W, args.serve_rates, args.serve_seconds)
 
     cpu = None
@@ -342,13 +349,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     sim.close()
 
 
-def batched_extra(sim, lenssim, W, dev, n_sys: int):
+def batched_extra(sim, lenssim, W, dev, n_sys: int, small: bool = False):
     """Uneven batch (grids 64..256, s 1..3, 0..20,000 subhalos, PSF 5..31): one lens_sim_image
     call (persistent fused launches replayed from a CUDA graph) against a host loop of
     single-system calls with a stream synchronisation per call, on the same device inputs."""
     import ctypes
     import torch
-    systems = W.batched_systems(2024, count=n_sys)
+    if small:  # launch-bound mix: small grids and few subhalos
+        systems = W.batched_systems(2025, count=n_sys, max_sub=100, grids=(64,))
+    else:
+        systems = W.batched_systems(2024, count=n_sys)
     subs = [torch.from_numpy(s.subhalos).to(dev) for s in systems]
     outs = [torch.empty((s.grid.ny, s.grid.nx), device=dev) for s in systems]
     keep = []
@@ -385,8 +395,9 @@ def batched_extra(sim, lenssim, W, dev, n_sys: int):
     return {"systems": n_sys, "images_per_s": n_sys / t_batch, "plain_images_per_s": n_sys / t_plain,
             "speedup_vs_plain": t_plain / t_batch, "pairs_per_s": pairs / t_batch,
             "batch_s": t_batch, "plain_s": t_plain,
-            "workload": "grids {64,100,128,200,256}^2, s in {1,2,3}, subhalos log-uniform in [0,20000], "
-                        "PSF 5..31, one graph launch vs per-image calls with a sync each"}
+            "workload": ("grids 64^2, s in {1,2,3}, subhalos log-uniform in [0,100], PSF 5..31" if small else
+                         "grids {64,100,128,200,256}^2, s in {1,2,3}, subhalos log-uniform in [0,20000], PSF 5..31")
+                        + "; one graph launch vs per-image calls with a sync each"}
 
 
 def conv_extra(sim, W, dev, n_img: int = 4096, size: int = 256):
@@ -445,6 +456,29 @@ def grad_extra(sim, W, dev):
     t = e0.elapsed_time(e1) / 1000.0 / reps
     return {"points": int(P.shape[0]), "gradients_per_s": P.shape[0] / t, "ms_per_call": 1000.0 * t,
             "workload": "100x100, 13x13 Gaussian PSF, 1000 fixed TNFW, 15 parameters, 512 points"}
+
+
+def fitting_extra(sim, W, dev):
+    """Particle swarm fit of the differentiation workload's 15 parameters (the paper's PSO
+    benchmark, here on the EPL + shear + Sersic model): 64..512 particles, 100 iterations,
+    every iteration one batched likelihood call over the swarm."""
+    import torch
+    from paper_2606_01547_gb300 import fitting
+    pb = W.diff_problem(42)
+    truth_img = sim.image(pb.system)[0].cpu().numpy()
+    data = torch.from_numpy(W.observe(truth_img, pb.sigma_bkg, pb.t_exp, 42)).to(dev)
+    tid = sim.register_subhalos(pb.system.subhalos)
+    out = []
+    for n in (64, 128, 256, 512):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fitting.pso_fit(sim, pb.system, data, pb.sigma_bkg, pb.t_exp, n_particles=n, iters=100, seed=1,
+                              subhalo_table=tid)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out.append({"particles": n, "iterations": 100, "seconds": t, "evaluations_per_s": res.evaluations / t,
+                    "best_logL": float(res.logL[0])})
+    return {"pso": out, "workload": "100x100, 13x13 PSF, 1000 fixed TNFW, 15 free parameters"}
 
 
 def serving_extra(lenssim, W, rates, seconds: float):
@@ -513,6 +547,9 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, gradient and serving lines")
+    ap.add_argument("--variant", type=int, default=-1, help="fixed trace launch variant instead of autotuning")
+    ap.add_argument("--psf-only", type=int, default=0, metavar="N_IMG",
+                    help="only the standalone PSF measurement on N_IMG 256^2 images (profiling runs)")
     ap.add_argument("--batch-systems", type=int, default=4096)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[300.0, 3000.0, 12000.0])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -524,6 +561,14 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.psf_only:
+        import torch
+        from paper_2606_01547_gb300 import lenssim
+        from paper_2606_01547_gb300 import workloads as W
+        sim = lenssim.Simulator(device=0)
+        print(json.dumps({"psf_conv": conv_extra(sim, W, torch.device("cuda", 0), n_img=args.psf_only)}), flush=True)
+        sim.close()
         return
     if world > 1:
         import torch.distributed as dist

@@ -141,13 +141,13 @@ int lens_sim_convolve(lens_sim* sim, const float* in, int n_img, int ny, int nx,
                       void* stream);
 
 /* Launch variants of the fused trace kernel (one CTA per work unit; the same capped at 80
- * registers; thread-block clusters of 2 or 4 CTAs per unit).  Every variant gives
+ * registers; thread-block clusters of 2, 4 or 8 CTAs per unit).  Every variant gives
  * bitwise-identical images; only the speed differs.  lens_sim_autotune times each variant
  * on `sample` (reps launches each, CUDA events on `stream`, synchronising it), makes the
  * fastest the handle's default for single-system calls, and reports the index and the mean
  * milliseconds of each variant (ms_per_variant may be NULL; n_ms entries are written at most).
  * lens_sim_set_variant sets it directly (0 .. LENS_TRACE_VARIANTS-1). */
-#define LENS_TRACE_VARIANTS 4
+#define LENS_TRACE_VARIANTS 5
 int lens_sim_autotune(lens_sim* sim, const lens_system* sample, int reps, int* best_variant,
                       float* ms_per_variant, int n_ms, void* stream);
 int lens_sim_set_variant(lens_sim* sim, int variant);
@@ -161,6 +161,17 @@ int lens_sim_set_variant(lens_sim* sim, int variant);
  * out_grad: DEVICE [n_points][15] or NULL for the likelihood only. */
 int lens_sim_grad(lens_sim* sim, const lens_system* sys, const float* data, float sigma_bkg, float t_exp,
                   const float* params, int n_points, float* out_logL, float* out_grad, void* stream);
+
+/* Linear amplitude solver (the paper's lens-modelling section: solving linear amplitudes reduces
+ * the number of sampled parameters).  For each of n_points parameter vectors (layout of
+ * lens_sim_grad; the amplitude entry is ignored) the source amplitude is the weighted
+ * least-squares solution against DEVICE data [ny][nx]:
+ *   amp = sum w d m1 / sum w m1^2,   w = 1 / (sigma_bkg^2 + max(d, 0)/t_exp),
+ * with m1 the PSF-convolved model per unit amplitude (data-based weights keep the problem
+ * linear), and out_logL (DEVICE [n_points], may be NULL) = -1/2 sum w (d - amp m1)^2.
+ * out_amp: DEVICE [n_points]. */
+int lens_sim_linear_amp(lens_sim* sim, const lens_system* sys, const float* data, float sigma_bkg, float t_exp,
+                        const float* params, int n_points, float* out_amp, float* out_logL, void* stream);
 
 /* ---------------------------------------------------------------- allocation-free form
  * The paper has no counterpart to this entry point; it is a deployment convenience.

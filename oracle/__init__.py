@@ -228,3 +228,21 @@ def model_image(system, params) -> np.ndarray:
     if lib().oracle_model_image(ctypes.byref(pk.st), _ptr(P), _ptr(out)) != 0:
         raise ValueError("oracle_model_image failed")
     return out
+
+
+def linear_amp(system, data, sigma_bkg: float, t_exp: float, params):
+    """Weighted least-squares source amplitude per parameter point: with w = 1/(sigma_bkg^2 +
+    max(d, 0)/t_exp) and m1 the model at unit amplitude, amp = sum w d m1 / sum w m1^2, and the
+    log-likelihood at it, -1/2 sum w (d - amp m1)^2 (straight from the definitions, FP64)."""
+    P = _f64(params).reshape(-1, 15)
+    d = _f64(data)
+    w = 1.0 / (sigma_bkg ** 2 + np.maximum(d, 0.0) / t_exp)
+    amps, logLs = [], []
+    for p in P:
+        q = p.copy()
+        q[8] = 1.0
+        m1 = model_image(system, q)
+        a = np.sum(w * d * m1) / np.sum(w * m1 * m1)
+        amps.append(a)
+        logLs.append(-0.5 * np.sum(w * (d - a * m1) ** 2))
+    return np.array(amps), np.array(logLs)

@@ -84,10 +84,11 @@ __device__ __forceinline__ float model_sample(float x, float y, float2 asub, con
 __global__ void __launch_bounds__(kGradThreads) forward_model_kernel(const __grid_constant__ DevSystem g,
                                                                      const float* __restrict__ params,
                                                                      const float2* __restrict__ asub,
-                                                                     float* __restrict__ m0) {
+                                                                     float* __restrict__ m0, int unit_amp) {
   __shared__ float P[LENS_N_FREE_PARAMS];
   const int p = blockIdx.y;
   if (threadIdx.x < LENS_N_FREE_PARAMS) P[threadIdx.x] = params[p * LENS_N_FREE_PARAMS + threadIdx.x];
+  if (unit_amp && threadIdx.x == 8) P[8] = 1.f;  // linear solve: the model per unit source amplitude
   __syncthreads();
   const int npix = g.nx * g.ny;
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
@@ -264,6 +265,50 @@ __global__ void __launch_bounds__(kGradThreads) backward_kernel(const __grid_con
   block_reduce_store<LENS_N_FREE_PARAMS>(acc, partial + ((size_t)p * nblk + blockIdx.x) * LENS_N_FREE_PARAMS);
 }
 
+// Linear amplitude solve: with data-based weights w = 1/(sigma_bkg^2 + max(d,0)/t_exp), the
+// weighted sums A = sum w d m1, B = sum w m1^2, C = sum w d^2 of the unit-amplitude model m1.
+__global__ void __launch_bounds__(kGradThreads) normal_eq_kernel(const float* __restrict__ m1,
+                                                                 const float* __restrict__ d, int npix,
+                                                                 float var_bkg, float inv_t,
+                                                                 float* __restrict__ partial, int nblk) {
+  const int p = blockIdx.y;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  float v[3] = {0.f, 0.f, 0.f};
+  if (pix < npix) {
+    const float dv = d[pix], mv = m1[(size_t)p * npix + pix];
+    const float w = 1.f / (var_bkg + fmaxf(dv, 0.f) * inv_t);
+    v[0] = w * dv * mv;
+    v[1] = w * mv * mv;
+    v[2] = w * dv * dv;
+  }
+  block_reduce_store<3>(v, partial + ((size_t)p * nblk + blockIdx.x) * 3);
+}
+
+// amp = A/B.
+__global__ void solve_amp_kernel(const float* __restrict__ sums, float* __restrict__ amp, int n_points) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_points) return;
+  const float A = sums[3 * p], B = sums[3 * p + 1];
+  amp[p] = B > 0.f ? A / B : 0.f;
+}
+
+// sum w (d - amp m1)^2, evaluated directly: near the best fit C - A^2/B cancels in FP32.
+__global__ void __launch_bounds__(kGradThreads) residual_chi2_kernel(const float* __restrict__ m1,
+                                                                     const float* __restrict__ d, int npix,
+                                                                     float var_bkg, float inv_t,
+                                                                     const float* __restrict__ amp,
+                                                                     float* __restrict__ partial, int nblk) {
+  const int p = blockIdx.y;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  float v[1] = {0.f};
+  if (pix < npix) {
+    const float dv = d[pix];
+    const float r = dv - amp[p] * m1[(size_t)p * npix + pix];
+    v[0] = r * r / (var_bkg + fmaxf(dv, 0.f) * inv_t);
+  }
+  block_reduce_store<1>(v, partial + (size_t)p * nblk + blockIdx.x);
+}
+
 }  // namespace ls
 
 using namespace ls;
@@ -327,7 +372,7 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
   for (int p0 = 0; p0 < n_points; p0 += chunk) {
     const int np = std::min(chunk, n_points - p0);
     const float* P = params + (size_t)p0 * LENS_N_FREE_PARAMS;
-    forward_model_kernel<<<dim3((npix + kGradThreads - 1) / kGradThreads, np), kGradThreads, 0, st>>>(d, P, asub, m0);
+    forward_model_kernel<<<dim3((npix + kGradThreads - 1) / kGradThreads, np), kGradThreads, 0, st>>>(d, P, asub, m0, 0);
     if (psf) e = launch_conv(m0, m, np, ny, nx, psf->d, psf->k, 1, st);
     else e = cudaMemcpyAsync(m, m0, sizeof(float) * (size_t)np * npix, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "model convolution");
@@ -344,6 +389,78 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "likelihood kernels");
+  }
+  return LENS_OK;
+}
+
+extern "C" int lens_sim_linear_amp(lens_sim* s, const lens_system* sys, const float* data, float sigma_bkg,
+                                   float t_exp, const float* params, int n_points, float* out_amp, float* out_logL,
+                                   void* stream) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (!sys || !data || !params || !out_amp) return fail(s, LENS_ERR_INVALID_ARG, "NULL argument");
+  if (n_points < 0 || n_points > s->max_batch)
+    return fail(s, LENS_ERR_INVALID_ARG, "n_points %d not in [0, %d]", n_points, s->max_batch);
+  if (!(sigma_bkg > 0.f) || !(t_exp > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "sigma_bkg and t_exp must be > 0");
+  if (n_points == 0) return LENS_OK;
+  DeviceGuard guard(s->device);
+  lens_system y = *sys;
+  y.n_deflectors = 0;
+  y.source.type = LIGHT_SERSIC;
+  y.source.p[1] = 1.f;
+  y.source.p[2] = 1.f;
+  int rc = validate_system(s, y, true);
+  if (rc) return rc;
+  if (!is_device_ptr(data) || !is_device_ptr(params) || !is_device_ptr(out_amp) ||
+      (out_logL && !is_device_ptr(out_logL)))
+    return fail(s, LENS_ERR_INVALID_ARG, "data, params and outputs must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nx = y.grid.nx, ny = y.grid.ny, ss = y.grid.supersample;
+  const int npix = nx * ny;
+  const long long n_samples = (long long)npix * ss * ss;
+  const int nblk = (npix + kGradThreads - 1) / kGradThreads;
+  const size_t sub_bytes = ((size_t)n_samples * sizeof(float2) + 255) & ~(size_t)255;
+  const size_t per_point = 2 * (size_t)npix * sizeof(float) + ((size_t)nblk * 3 + 3) * sizeof(float);
+  int chunk = n_points;
+  while (chunk > 1 && sub_bytes + per_point * chunk > ((size_t)1 << 30)) chunk = (chunk + 1) / 2;
+  if ((rc = ensure(s, s->grad_ws, sub_bytes + per_point * chunk + 256 * 4))) return rc;
+  const size_t n_sub_max = (size_t)sub_count(s, y);
+  if (y.subhalo_table < 0 && y.n_subhalos > 0) {
+    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * n_sub_max))) return rc;
+    if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * n_sub_max))) return rc;
+  }
+  DevSystem d;
+  fill_dev_system(y, d);
+  d.n_defl = 0;
+  if ((rc = prepare_subhalos(s, y, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
+  char* base = (char*)s->grad_ws.p;
+  float2* asub = (float2*)base;
+  base += sub_bytes;
+  float* m0 = (float*)base;
+  float* m1 = m0 + (size_t)chunk * npix;
+  float* part = m1 + (size_t)chunk * npix;
+  float* sums = part + (size_t)chunk * nblk * 3;
+  subhalo_field_kernel<<<(unsigned)((n_samples + 255) / 256), 256, 0, st>>>(d, asub, n_samples);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(s, e, "subhalo field");
+  const PsfEntry* psf = y.psf_id >= 0 ? &s->res->psfs[y.psf_id] : nullptr;
+  for (int p0 = 0; p0 < n_points; p0 += chunk) {
+    const int np = std::min(chunk, n_points - p0);
+    const float* P = params + (size_t)p0 * LENS_N_FREE_PARAMS;
+    forward_model_kernel<<<dim3(nblk, np), kGradThreads, 0, st>>>(d, P, asub, m0, 1);
+    if (psf) e = launch_conv(m0, m1, np, ny, nx, psf->d, psf->k, 1, st);
+    else e = cudaMemcpyAsync(m1, m0, sizeof(float) * (size_t)np * npix, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "model convolution");
+    normal_eq_kernel<<<dim3(nblk, np), kGradThreads, 0, st>>>(m1, data, npix, sigma_bkg * sigma_bkg, 1.f / t_exp,
+                                                               part, nblk);
+    reduce_partials_kernel<<<(np * 3 + 127) / 128, 128, 0, st>>>(part, nblk, 3, 1.f, sums, np);
+    solve_amp_kernel<<<(np + 127) / 128, 128, 0, st>>>(sums, out_amp + p0, np);
+    if (out_logL) {
+      residual_chi2_kernel<<<dim3(nblk, np), kGradThreads, 0, st>>>(m1, data, npix, sigma_bkg * sigma_bkg,
+                                                                      1.f / t_exp, out_amp + p0, part, nblk);
+      reduce_partials_kernel<<<(np + 127) / 128, 128, 0, st>>>(part, nblk, 1, -0.5f, out_logL + p0, np);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "linear amplitude kernels");
   }
   return LENS_OK;
 }

@@ -55,8 +55,9 @@ int unit_count(int nx, int ny, int s);
 cudaError_t launch_trace(const DevSystem& sys, TraceShape shape, cudaStream_t st);
 // The same with an explicit launch variant (all variants give bitwise-identical images):
 // 0 one CTA of 8 warps per unit, 1 the same capped at 80 registers (3 CTAs per SM),
-// 2 a cluster of 2 CTAs x 4 warps per unit, 3 a cluster of 4 CTAs x 2 warps per unit.
-constexpr int kTraceVariants = 4;
+// 2 a cluster of 2 CTAs x 4 warps per unit, 3 a cluster of 4 CTAs x 2 warps per unit,
+// 4 a cluster of 8 single-warp CTAs per unit.
+constexpr int kTraceVariants = 5;
 cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t st);
 const char* trace_variant_name(int v);
 

@@ -26,14 +26,17 @@ namespace ls {
 namespace {
 
 constexpr int kTW = 64;        // output tile width
-constexpr int kTH = 32;        // output tile height
-constexpr int kThreads = 256;  // 16 x 16 threads, each 4 columns x 2 rows
+constexpr int kThreads = 256;  // 16 x 16 threads, each 4 columns x rows_per_thread(K) rows
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
+// Small kernels (k <= 7, the HBM-bound regime) use 4 output rows per thread (64x64 tiles) with the
+// weights in registers; larger kernels (FP32-bound) use 2 rows (64x32 tiles).
+constexpr int rows_per_thread(int K) { return K <= 7 ? 4 : 2; }
+constexpr int tile_h(int K) { return 16 * rows_per_thread(K); }
 constexpr int cpad(int K) { return ((K - 1) / 2 + 3) / 4 * 4; }   // left halo rounded up to 4
 constexpr int coff(int K) { return cpad(K) - (K - 1) / 2; }        // tile column of the first tap
 constexpr int box_w(int K) { return (coff(K) + kTW + K - 1 + 3) / 4 * 4; }
-constexpr int box_h(int K) { return kTH + K - 1; }
+constexpr int box_h(int K) { return tile_h(K) + K - 1; }
 constexpr int tile_floats(int K) { return (box_w(K) * box_h(K) + 31) / 32 * 32; }  // 128-byte multiple
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -89,11 +92,73 @@ struct TmaConvArgs {
   int* err;  // host-mapped flag, raised when a bounded wait expires
 };
 
+// out[2x? rows][4 cols] of one thread from the tile in shared memory.  Small K: every input row
+// the thread needs is read once (float4 window) and applied to each output row it touches, with
+// the weights in registers; large K: per kernel row, the two input rows, weights row hoisted.
+template <int K>
+__device__ __forceinline__ void conv_tile_compute(const float* __restrict__ T, const float* __restrict__ sK,
+                                                  const float (&kreg)[K <= 7 ? K * K : 1], int tx, int ty,
+                                                  float (&acc)[rows_per_thread(K)][4]) {
+  constexpr int R = rows_per_thread(K), BW = box_w(K), OFF = coff(K);
+  constexpr int NV = (OFF + 4 + K - 1 + 3) / 4;  // float4 per window row
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[rr][c] = 0.f;
+  if constexpr (K <= 7) {
+#pragma unroll
+    for (int t = 0; t < R + K - 1; ++t) {
+      const float4* row = reinterpret_cast<const float4*>(T + (R * ty + t) * BW + 4 * tx);
+      float w[4 * NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float4 f = row[v];
+        w[4 * v] = f.x;
+        w[4 * v + 1] = f.y;
+        w[4 * v + 2] = f.z;
+        w[4 * v + 3] = f.w;
+      }
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const int a = t - rr;
+        if (a < 0 || a >= K) continue;
+#pragma unroll
+        for (int b = 0; b < K; ++b)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[rr][c] = fmaf(kreg[a * K + b], w[OFF + c + b], acc[rr][c]);
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (int a = 0; a < K; ++a) {
+      float kr[K];
+#pragma unroll
+      for (int b = 0; b < K; ++b) kr[b] = sK[a * K + b];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const float4* row = reinterpret_cast<const float4*>(T + (R * ty + rr + a) * BW + 4 * tx);
+        float w[4 * NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float4 f = row[v];
+          w[4 * v] = f.x;
+          w[4 * v + 1] = f.y;
+          w[4 * v + 2] = f.z;
+          w[4 * v + 3] = f.w;
+        }
+#pragma unroll
+        for (int b = 0; b < K; ++b)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[rr][c] = fmaf(kr[b], w[OFF + c + b], acc[rr][c]);
+      }
+    }
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kThreads) conv_tma_kernel(const __grid_constant__ CUtensorMap tin,
                                                            const TmaConvArgs A) {
-  constexpr int BW = box_w(K), BH = box_h(K), OFF = coff(K), C = (K - 1) / 2;
-  constexpr int NV = (OFF + 4 + K - 1 + 3) / 4;  // float4 per window row
+  constexpr int BW = box_w(K), BH = box_h(K), C = (K - 1) / 2, R = rows_per_thread(K), TH = tile_h(K);
   constexpr unsigned kBytes = BW * BH * sizeof(float);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* tile0 = (float*)smem_raw;
@@ -109,13 +174,20 @@ __global__ void __launch_bounds__(kThreads) conv_tma_kernel(const __grid_constan
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  float kreg[K <= 7 ? K * K : 1];
+  if constexpr (K <= 7) {
+#pragma unroll
+    for (int q = 0; q < K * K; ++q) kreg[q] = sK[q];
+  } else {
+    kreg[0] = 0.f;
+  }
 
   const int per_img = A.tiles_x * A.tiles_y;
   const long long total = (long long)per_img * A.n_img;
   auto issue = [&](long long t, int s) {
     const int z = (int)(t / per_img);
     const int r = (int)(t - (long long)z * per_img);
-    const int i0 = (r / A.tiles_x) * kTH, j0 = (r % A.tiles_x) * kTW;
+    const int i0 = (r / A.tiles_x) * TH, j0 = (r % A.tiles_x) * kTW;
     mbar_expect_tx(&bars[s], kBytes);
     tma_load_3d(s ? tile1 : tile0, &tin, j0 - cpad(K), i0 - C, z, &bars[s]);
   };
@@ -137,42 +209,16 @@ __global__ void __launch_bounds__(kThreads) conv_tma_kernel(const __grid_constan
       __syncthreads();
       return;
     }
-    const float* T = s ? tile1 : tile0;
     const int z = (int)(t / per_img);
     const int r = (int)(t - (long long)z * per_img);
-    const int i0 = (r / A.tiles_x) * kTH, j0 = (r % A.tiles_x) * kTW;
-    float acc[2][4];
-#pragma unroll
-    for (int rr = 0; rr < 2; ++rr)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[rr][c] = 0.f;
-#pragma unroll 1
-    for (int a = 0; a < K; ++a) {
-#pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const float4* row = reinterpret_cast<const float4*>(T + (2 * ty + rr + a) * BW + 4 * tx);
-        float w[4 * NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const float4 f = row[v];
-          w[4 * v] = f.x;
-          w[4 * v + 1] = f.y;
-          w[4 * v + 2] = f.z;
-          w[4 * v + 3] = f.w;
-        }
-#pragma unroll
-        for (int b = 0; b < K; ++b) {
-          const float kv = sK[a * K + b];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[rr][c] = fmaf(kv, w[OFF + c + b], acc[rr][c]);
-        }
-      }
-    }
+    const int i0 = (r / A.tiles_x) * TH, j0 = (r % A.tiles_x) * kTW;
+    float acc[R][4];
+    conv_tile_compute<K>(s ? tile1 : tile0, sK, kreg, tx, ty, acc);
     const int j = j0 + 4 * tx;
     if (j < A.nx) {
 #pragma unroll
-      for (int rr = 0; rr < 2; ++rr) {
-        const int i = i0 + 2 * ty + rr;
+      for (int rr = 0; rr < R; ++rr) {
+        const int i = i0 + R * ty + rr;
         if (i < A.ny)
           *reinterpret_cast<float4*>(A.out + ((size_t)z * A.ny + i) * A.nx + j) =
               make_float4(acc[rr][0], acc[rr][1], acc[rr][2], acc[rr][3]);
@@ -237,7 +283,7 @@ cudaError_t launch_k(const float* in, float* out, int n_img, int ny, int nx, con
   A.ny = ny;
   A.n_img = n_img;
   A.tiles_x = (nx + kTW - 1) / kTW;
-  A.tiles_y = (ny + kTH - 1) / kTH;
+  A.tiles_y = (ny + tile_h(K) - 1) / tile_h(K);
   A.err = err;
   const long long total = (long long)A.tiles_x * A.tiles_y * n_img;
   const int grid = (int)std::min<long long>(total, (long long)sm_count * per_sm);

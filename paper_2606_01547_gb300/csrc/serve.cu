@@ -42,6 +42,8 @@ struct Req {
   int status = LENS_OK;
   size_t out_off = 0;  // offset (floats) of this request's outputs in the slot buffers
   size_t in_off = 0;   // offset (floats) of its inputs (likelihood)
+  size_t sub_off = 0;  // offset (floats) of its subhalo arrays in the packed batch copy
+  const float* sub_dev = nullptr;
 };
 
 struct Slot {
@@ -57,6 +59,9 @@ struct Slot {
   float* d_in = nullptr;
   float* h_in = nullptr;
   size_t in_cap = 0;
+  float* d_sub = nullptr;  // the batch's subhalo arrays, packed (pinned copy -> one async H2D)
+  float* h_sub = nullptr;
+  size_t sub_cap = 0;
 };
 
 size_t npix_of(const lens_request& r) { return (size_t)r.sys.grid.nx * (size_t)r.sys.grid.ny; }
@@ -131,8 +136,30 @@ void issue(lens_server* srv, Slot* sl, CbArg* cb) {
     q->in_off = in_need;
     if (q->r.kind == 1) in_need += npix_of(q->r) + 16;
   }
+  size_t sub_need = 0;
+  for (Req* q : sl->batch) {
+    q->sub_off = sub_need;
+    q->sub_dev = nullptr;
+    if (q->r.sys.subhalo_table < 0 && q->r.sys.n_subhalos > 0 && !ls::is_device_ptr(q->r.sys.subhalos))
+      sub_need += 5 * (size_t)q->r.sys.n_subhalos;
+  }
   int rc = grow(&sl->d_out, &sl->h_out, &sl->out_cap, std::max<size_t>(out_need, 1));
   if (rc == LENS_OK) rc = grow(&sl->d_in, &sl->h_in, &sl->in_cap, std::max<size_t>(in_need, 1));
+  if (rc == LENS_OK) rc = grow(&sl->d_sub, &sl->h_sub, &sl->sub_cap, std::max<size_t>(sub_need, 1));
+  if (rc == LENS_OK && sub_need > 0) {
+    // host subhalo arrays: pack into pinned memory, one asynchronous copy for the batch
+    for (Req* q : sl->batch) {
+      if (q->r.sys.subhalo_table < 0 && q->r.sys.n_subhalos > 0 && !ls::is_device_ptr(q->r.sys.subhalos)) {
+        std::memcpy(sl->h_sub + q->sub_off, q->r.sys.subhalos, 5 * sizeof(float) * q->r.sys.n_subhalos);
+        q->sub_dev = sl->d_sub + q->sub_off;
+      }
+    }
+    if (cudaMemcpyAsync(sl->d_sub, sl->h_sub, sub_need * sizeof(float), cudaMemcpyHostToDevice, sl->stream) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      rc = LENS_ERR_CUDA;
+    }
+  }
   if (rc != LENS_OK) {
     for (Req* q : sl->batch) q->status = rc;
   } else {
@@ -144,6 +171,7 @@ void issue(lens_server* srv, Slot* sl, CbArg* cb) {
       if (q->r.kind == 0) {
         lens_system y = q->r.sys;
         y.deflectors = q->defl.data();
+        if (q->sub_dev) y.subhalos = q->sub_dev;
         sys.push_back(y);
         outs.push_back(sl->d_out + q->out_off);
         img.push_back(q);
@@ -171,6 +199,7 @@ void issue(lens_server* srv, Slot* sl, CbArg* cb) {
       cudaMemcpyAsync(din, hin, (npix + LENS_N_FREE_PARAMS) * sizeof(float), cudaMemcpyHostToDevice, sl->stream);
       lens_system y = q->r.sys;
       y.deflectors = q->defl.data();
+      if (q->sub_dev) y.subhalos = q->sub_dev;
       float* dout = sl->d_out + q->out_off;
       q->status = lens_sim_grad(sl->sim, &y, din, q->r.sigma_bkg, q->r.t_exp, din + npix, 1, dout,
                                 q->r.out_grad ? dout + 1 : nullptr, sl->stream);
@@ -459,6 +488,8 @@ void lens_serve_destroy(lens_server* srv) {
     if (sl->h_out) cudaFreeHost(sl->h_out);
     if (sl->d_in) cudaFree(sl->d_in);
     if (sl->h_in) cudaFreeHost(sl->h_in);
+    if (sl->d_sub) cudaFree(sl->d_sub);
+    if (sl->h_sub) cudaFreeHost(sl->h_sub);
     if (sl->stream) cudaStreamDestroy(sl->stream);
     if (sl->sim) lens_sim_destroy(sl->sim);
     delete sl;

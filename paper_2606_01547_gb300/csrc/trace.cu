@@ -298,6 +298,7 @@ const char* trace_variant_name(int v) {
     case 1: return "cta8_minblocks3";
     case 2: return "cluster2x4";
     case 3: return "cluster4x2";
+    case 4: return "cluster8x1";
     default: return "?";
   }
 }
@@ -308,6 +309,7 @@ cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t
     case 1: trace_image_kernel<3><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
     case 2: trace_cluster_kernel<2><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
     case 3: trace_cluster_kernel<4><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
+    case 4: trace_cluster_kernel<8><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
     default: trace_image_kernel<1><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
   }
   return cudaGetLastError();

@@ -28,12 +28,13 @@ LENS_TYPES = {"SIS": 0, "SIE": 1, "EPL": 2, "SHEAR": 3, "POINT_MASS": 4, "NFW": 
               "EPL_E1E2": 7, "SIE_E1E2": 8}
 LIGHT_TYPES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2}
 MAX_DEFLECTORS = 8
-TRACE_VARIANTS = ("cta8", "cta8_minblocks3", "cluster2x4", "cluster4x2")
+TRACE_VARIANTS = ("cta8", "cta8_minblocks3", "cluster2x4", "cluster4x2", "cluster8x1")
 _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
             "lens_sim_register_subhalos", "lens_sim_image", "lens_sim_deflection", "lens_sim_convolve",
-            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_grad", "lens_sim_image_noalloc", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
+            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_grad", "lens_sim_linear_amp",
+            "lens_sim_image_noalloc", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
             "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats",
             "lens_serve_reset_stats", "lens_serve_destroy")
 
@@ -112,6 +113,7 @@ def lib():
                                             ctypes.POINTER(fp), ip, vp]
             L.lens_sim_set_variant.argtypes = [vp, ip]
             L.lens_sim_image_noalloc.argtypes = [ctypes.POINTER(LensSystemC), vp, ip, vp, vp]
+            L.lens_sim_linear_amp.argtypes = [vp, ctypes.POINTER(LensSystemC), vp, fp, fp, vp, ip, vp, vp, vp]
             L.lens_serve_create.argtypes = [ctypes.POINTER(SimConfig), ip, ctypes.POINTER(vp)]
             L.lens_serve_sim.argtypes = [vp]
             L.lens_serve_sim.restype = vp
@@ -344,6 +346,24 @@ class Simulator:
                                           float(t_exp), P.data_ptr(), n, L.data_ptr(),
                                           None if G is None else G.data_ptr(), _stream_ptr(stream)))
         return (L, G) if want_grad else L
+
+
+def _linear_amp(self, system: W.LensSystem, data: torch.Tensor, sigma_bkg: float, t_exp: float,
+                params: torch.Tensor, stream=None, subhalo_table: int = -1):
+    """Weighted least-squares source amplitude (and logL at it) for [n, 15] parameter points."""
+    keep: list = []
+    c = self.system_struct(system, keep, subhalo_table=subhalo_table)
+    P = params.contiguous().float()
+    n = P.shape[0]
+    amp = torch.empty(n, dtype=torch.float32, device=P.device)
+    L = torch.empty(n, dtype=torch.float32, device=P.device)
+    self._check(self._L.lens_sim_linear_amp(self.h, ctypes.byref(c), data.contiguous().data_ptr(), float(sigma_bkg),
+                                            float(t_exp), P.data_ptr(), n, amp.data_ptr(), L.data_ptr(),
+                                            _stream_ptr(stream)))
+    return amp, L
+
+
+Simulator.linear_amp = _linear_amp
 
 
 class LensLogLike(torch.autograd.Function):

@@ -1,0 +1,64 @@
+"""Fitting clients of the batched likelihood: L-BFGS reaches the optimum that SciPy's L-BFGS-B
+finds on the FP64 oracle from the same start; the particle swarm improves monotonically."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_01547_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+scipy_opt = pytest.importorskip("scipy.optimize")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_01547_gb300 import lenssim
+    s = lenssim.Simulator(device=0)
+    yield s
+    s.close()
+
+
+def _problem():
+    pb = W.diff_problem(21, n_points=1, n_sub=30, nx=24, dpix=0.1, k=5)
+    data = W.observe(oracle.model_image(pb.system, pb.truth), pb.sigma_bkg, pb.t_exp, 21)
+    return pb, data
+
+
+def test_lbfgs_reaches_the_oracle_optimum(sim):
+    from paper_2606_01547_gb300 import fitting
+    pb, data = _problem()
+    rng = np.random.default_rng(3)
+    start = (pb.truth * (1 + 0.02 * rng.standard_normal(15))).astype(np.float32)
+    res = fitting.lbfgs_fit(sim, pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp, start[None],
+                            iters=200)
+
+    def f(p):
+        L, G = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, p[None])
+        return -L[0], -G[0]
+
+    ref = scipy_opt.minimize(f, start.astype(np.float64), jac=True, method="L-BFGS-B",
+                             options={"maxiter": 2000, "ftol": 1e-15, "gtol": 1e-10})
+    L_gpu_at_gpu = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, res.params.astype(np.float64),
+                                  grad=False)[0]
+    # same optimum: the FP64 likelihood at the GPU optimum is within 1e-6 of SciPy's optimum
+    assert abs(L_gpu_at_gpu - (-ref.fun)) <= 1e-6 * abs(ref.fun) + 1e-3, (L_gpu_at_gpu, -ref.fun)
+    np.testing.assert_allclose(res.params[0], ref.x, rtol=2e-3, atol=2e-4)
+    assert res.logL[0] >= oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, start[None], grad=False)[0]
+
+
+def test_particle_swarm_improves_monotonically(sim):
+    from paper_2606_01547_gb300 import fitting
+    pb, data = _problem()
+    res = fitting.pso_fit(sim, pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp, n_particles=128,
+                          iters=40, seed=5)
+    h = np.array(res.history)
+    assert np.all(np.diff(h) >= 0)
+    assert h[-1] > h[0]
+    assert res.evaluations == 128 * 41
+    # the reported best is the likelihood of the reported parameters
+    L = sim.grad(pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp,
+                 torch.from_numpy(res.params).cuda(), want_grad=False)
+    assert abs(L.item() - res.logL[0]) <= 1e-6 * abs(res.logL[0])

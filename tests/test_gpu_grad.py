@@ -103,3 +103,18 @@ def test_gpu_gradient_consistent_with_gpu_finite_differences(sim):
               - sim.grad(pb.system, data, 0.01, 1000.0, Pm, want_grad=False)).item() / (2 * h)
         scale = max(abs(G[0, k]), 1e-2 * np.abs(G[0]).max())
         assert abs(fd - G[0, k]) <= 2e-2 * scale, (k, fd, G[0, k])
+
+
+@pytest.mark.parametrize("nx,s,k,nsub", [(24, 1, 5, 20), (19, 2, 7, 50), (100, 1, 13, 1000)])
+def test_linear_amplitude_solver_matches_oracle(sim, nx, s, k, nsub):
+    pb = W.diff_problem(12, n_points=6, n_sub=nsub, nx=nx, dpix=0.1 if nx < 50 else 0.05, k=k)
+    pb.system = W.LensSystem(W.Grid(nx, nx, s, pb.system.grid.dpix), pb.system.deflectors, pb.system.subhalos,
+                             pb.system.source, pb.system.psf)
+    data = W.observe(oracle.model_image(pb.system, pb.truth), pb.sigma_bkg, pb.t_exp, 12)
+    pts = np.concatenate([pb.truth[None], pb.points[:5]]).astype(np.float32)
+    amp, L = sim.linear_amp(pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp,
+                            torch.from_numpy(pts).cuda())
+    ar, Lr = oracle.linear_amp(pb.system, data, pb.sigma_bkg, pb.t_exp, pts)
+    np.testing.assert_allclose(amp.cpu().numpy(), ar, rtol=2e-5)
+    np.testing.assert_allclose(L.cpu().numpy(), Lr, rtol=2e-5)
+    assert abs(amp[0].item() - pb.truth[8]) < 0.05 * pb.truth[8]  # the truth point recovers its amplitude

@@ -404,3 +404,21 @@ def test_nfw_tnfw_mass_against_40_digit_golden():
     # atol: the plain FP64 formulas cancel terms of size ~ tau^2 ln(2/x) at small x
     np.testing.assert_allclose(_oracle_M("NFW", xs, Rs=Rs), nfw, rtol=2e-9, atol=1e-14)
     np.testing.assert_allclose(_oracle_M("TNFW", xs, Rs=Rs, rt=5 * Rs), tnfw, rtol=2e-9, atol=1e-14)
+
+
+def test_linear_amplitude_recovers_truth_and_minimises_chi2():
+    pb = _small_diff()
+    truth = pb.truth.astype(np.float64)
+    data = oracle.model_image(pb.system, truth)  # noise-free, amplitude truth[8]
+    a, L = oracle.linear_amp(pb.system, data, 0.01, 1000.0, truth[None])
+    assert abs(a[0] - truth[8]) < 1e-10 * truth[8] and abs(L[0]) < 1e-12
+    # with noise the solution is the minimum of the weighted chi^2 along the amplitude
+    noisy = W.observe(data, 0.01, 1000.0, 9).astype(np.float64)
+    p = pb.points[0].astype(np.float64)
+    a, L = oracle.linear_amp(pb.system, noisy, 0.01, 1000.0, p[None])
+    w = 1.0 / (0.01 ** 2 + np.maximum(noisy, 0) / 1000.0)
+    q = p.copy(); q[8] = 1.0
+    m1 = oracle.model_image(pb.system, q)
+    chi = lambda amp: np.sum(w * (noisy - amp * m1) ** 2)
+    assert chi(a[0]) < chi(a[0] * (1 + 1e-4)) and chi(a[0]) < chi(a[0] * (1 - 1e-4))
+    assert abs(L[0] + 0.5 * chi(a[0])) < 1e-9 * chi(a[0])
