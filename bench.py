@@ -38,11 +38,12 @@ WORKLOAD = ("substructure image: 200x200 grid at 0.04\", supersampling 3 (360,00
             "EPL + shear, 10,000 truncated-NFW subhalos, elliptical Sersic, 21x21 Moffat PSF, FP32")
 N_SYSTEMS = 8            # distinct seeded systems cycled through the steps
 # Algorithmic work of one point-subhalo pair, frozen from the far-field series pair formula that
-# almost every pair takes: dx, dy (2 FADD); x^2 = (dx^2 + dy^2)/Rs^2 (FMUL, FFMA, FMUL);
-# y = rsqrt(x^2) (1 MUFU); y^2 (FMUL); Horner over 10 coefficients (9 FFMA); g = p y^2 (FMUL);
-# alpha += g (dx, dy) (2 FFMA)  ->  12 FFMA + 4 FMUL + 2 FADD = 30 FP32 flops (FMA = 2), 1 MUFU.
-FLOPS_PER_PAIR = 30
-KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh")
+# almost every pair takes: dx, dy (2 FADD); r^2 = dx^2 + dy^2 (FMUL, FFMA); u = rsqrt(r^2)
+# (1 MUFU); u^2 (FMUL); Horner over the 10 coefficients (9 FFMA); g = p u^2 (FMUL);
+# alpha += g (dx, dy) (2 FFMA)  ->  12 FFMA + 3 FMUL + 2 FADD = 29 FP32 flops (FMA = 2), 1 MUFU.
+FLOPS_PER_PAIR = 29
+KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh",
+                  "paper_2606_01547_gb300/csrc/kernels.h")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trace_kernel_substructure_200x200_traffic.txt")
 
 
@@ -274,11 +275,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     if os.path.exists(PROFILE_TRAFFIC):
         prof = dict(l.split(": ", 1) for l in open(PROFILE_TRAFFIC).read().splitlines()
                     if ": " in l and not l.startswith("#"))
-        if prof.get("kernel_hash") == kernel_hash() and tune["variant"] == 3:
+        if prof.get("kernel_hash") == kernel_hash() and prof.get("variant") == tune["name"]:
             traffic = int(prof["traffic_bytes_per_launch"])
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": "trace_image_kernel<8> (+ tnfw_prep)",
+                "kernel": f"fused trace kernel, launch variant {tune['name']} (+ tnfw_prep)",
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived, FP32 FMA)",
                 "frac_at_median_clock": (achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
                                          if clocks["sm_mhz"] else None),

@@ -23,14 +23,11 @@ __global__ void prep_batch_meta_kernel(const BatchMeta* __restrict__ meta) {
   for (int jb = blockIdx.x; jb < n_jobs; jb += gridDim.x) {
     const PrepJob j = meta->prep[jb];
     for (int t = threadIdx.x; t < j.n; t += blockDim.x) {
-      float4 v0, v1, v2, v3;
-      tnfw_constants(j.soa[t], j.soa[j.ld + t], j.soa[2 * j.ld + t], j.soa[3 * j.ld + t], j.soa[4 * j.ld + t],
-                     v0, v1, v2, v3);
+      float4 v[kSubStride];
+      tnfw_constants(j.soa[t], j.soa[j.ld + t], j.soa[2 * j.ld + t], j.soa[3 * j.ld + t], j.soa[4 * j.ld + t], v);
       float4* o = j.tab + (size_t)kSubStride * t;
-      o[0] = v0;
-      o[1] = v1;
-      o[2] = v2;
-      o[3] = v3;
+#pragma unroll
+      for (int c = 0; c < kSubStride; ++c) o[c] = v[c];
     }
   }
 }

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) subhalo_field_kernel(const __grid_constan
     __syncwarp();
     const int cnt = min(32, sys.n_sub - base);
     for (int q = 0; q < cnt; ++q)
-      tnfw_pair(px, py, s_sub[w][q][0], s_sub[w][q][1], s_sub[w][q][2], s_sub[w][q][3], ax, ay);
+      tnfw_pair(px, py, s_sub[w][q], ax, ay);
     __syncwarp();
   }
   if (idx < n_samples) out[idx] = make_float2(ax, ay);

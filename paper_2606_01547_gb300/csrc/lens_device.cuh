@@ -259,15 +259,16 @@ __device__ __forceinline__ float tnfw_g_far(float x2, float tau, float t2, float
 // tau >= 0.6 (below 1e-8 for tau >= 2) on that range, and Horner in FP32 is well conditioned
 // (sum |c_k y^k| / |G| < 1.1).
 constexpr int kFarTerms = 10;
-constexpr int kSubStride = 4;  // float4 per subhalo in the table
+constexpr int kSubStride = 8;  // float4 per subhalo in the table
 
-// Four float4 per subhalo:
-//   v0 = (cx, cy, r_far^2 = 16 max(tau,1)^2 Rs^2, 1/Rs^2), v1 = (tau, A, d_0, d_2),
-//   v2 = (d_3, d_4, d_5, d_6), v3 = (d_7, d_8, d_9, d_10),
+// Eight float4 (128 B) per subhalo, laid out for packed FP32x2 arithmetic (two samples per
+// instruction): centres negated and every series coefficient stored as a duplicated pair,
+//   t0 = (-cx, -cx, -cy, -cy),           t1 = (r_far^2 = 16 max(tau,1)^2 Rs^2, 1/Rs^2, tau, A),
+//   t2 = (d_0, d_0, d_2, d_2),  t3 = (d_3, d_3, d_4, d_4),  t4 = (d_5, d_5, d_6, d_6),
+//   t5 = (d_7, d_7, d_8, d_8),  t6 = (d_9, d_9, d_10, d_10), t7 = 0,
 // with A = alpha_Rs tau^2 / ((1 - ln 2) Rs (tau^2+1)^2), so that alpha = A g(x^2) (dx, dy), and
 // d_k = A c_k Rs^(k+2): the series then runs in u = 1/r with no per-pair scaling by 1/Rs^2.
-__device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, float alphaRs, float rt,
-                                               float4& v0, float4& v1, float4& v2, float4& v3) {
+__device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, float alphaRs, float rt, float4* t) {
   const float tau = rt / Rs;
   const float t2 = tau * tau, t2m1 = t2 - 1.f, t2p1 = t2 + 1.f;
   const float A = alphaRs * t2 / (kOneMinusLn2 * Rs * t2p1 * t2p1);
@@ -298,10 +299,14 @@ __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, flo
     rp *= Rs;
   }
   const float tm = fmaxf(tau, 1.f);
-  v0 = make_float4(cx, cy, 16.f * tm * tm * Rs * Rs, 1.f / (Rs * Rs));
-  v1 = make_float4(tau, A, d[0], d[2]);
-  v2 = make_float4(d[3], d[4], d[5], d[6]);
-  v3 = make_float4(d[7], d[8], d[9], d[10]);
+  t[0] = make_float4(-cx, -cx, -cy, -cy);
+  t[1] = make_float4(16.f * tm * tm * Rs * Rs, 1.f / (Rs * Rs), tau, A);
+  t[2] = make_float4(d[0], d[0], d[2], d[2]);
+  t[3] = make_float4(d[3], d[3], d[4], d[4]);
+  t[4] = make_float4(d[5], d[5], d[6], d[6]);
+  t[5] = make_float4(d[7], d[7], d[8], d[8]);
+  t[6] = make_float4(d[9], d[9], d[10], d[10]);
+  t[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Reciprocal square root on the MUFU with flush-to-zero: the far-field argument is at least
@@ -313,20 +318,37 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
 }
 
 // Far-field series from r^2: A g = u^2 (d_0 + u^2 (d_2 + d_3 u + ... + d_10 u^8)), u = 1/r,
-// the same as A y^2 sum_k c_k y^k with y = Rs/r.
-__device__ __forceinline__ float tnfw_series(float r2, const float4 v1, const float4 v2, const float4 v3) {
+// the same as A y^2 sum_k c_k y^k with y = Rs/r.  Scalar form (one sample).
+__device__ __forceinline__ float tnfw_series(float r2, const float4* t) {
   const float u = rsqrt_ftz(r2);
   const float u2 = u * u;
-  float p = fmaf(v3.w, u, v3.z);
-  p = fmaf(p, u, v3.y);
-  p = fmaf(p, u, v3.x);
-  p = fmaf(p, u, v2.w);
-  p = fmaf(p, u, v2.z);
-  p = fmaf(p, u, v2.y);
-  p = fmaf(p, u, v2.x);
-  p = fmaf(p, u, v1.w);
-  p = fmaf(p, u2, v1.z);
+  float p = fmaf(t[6].z, u, t[6].x);
+  p = fmaf(p, u, t[5].z);
+  p = fmaf(p, u, t[5].x);
+  p = fmaf(p, u, t[4].z);
+  p = fmaf(p, u, t[4].x);
+  p = fmaf(p, u, t[3].z);
+  p = fmaf(p, u, t[3].x);
+  p = fmaf(p, u, t[2].z);
+  p = fmaf(p, u2, t[2].x);
   return p * u2;
+}
+
+// Packed form (two samples per instruction): element-wise the same operations, hence the same
+// rounding, as the scalar form.
+__device__ __forceinline__ float2 tnfw_series2(float2 r2, const float4* t) {
+  const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+  const float2 u2 = __fmul2_rn(u, u);
+  float2 p = __ffma2_rn(make_float2(t[6].z, t[6].w), u, make_float2(t[6].x, t[6].y));
+  p = __ffma2_rn(p, u, make_float2(t[5].z, t[5].w));
+  p = __ffma2_rn(p, u, make_float2(t[5].x, t[5].y));
+  p = __ffma2_rn(p, u, make_float2(t[4].z, t[4].w));
+  p = __ffma2_rn(p, u, make_float2(t[4].x, t[4].y));
+  p = __ffma2_rn(p, u, make_float2(t[3].z, t[3].w));
+  p = __ffma2_rn(p, u, make_float2(t[3].x, t[3].y));
+  p = __ffma2_rn(p, u, make_float2(t[2].z, t[2].w));
+  p = __ffma2_rn(p, u2, make_float2(t[2].x, t[2].y));
+  return __fmul2_rn(p, u2);
 }
 
 // Inside the series range: the closed forms (x >= 4) or the small-x forms (x < 4), times A.
@@ -339,16 +361,14 @@ static __device__ __noinline__ float tnfw_g_inner(float x2, float tau, float A) 
 }
 
 // A g for one pair at squared distance r2, any distance.
-__device__ __forceinline__ float tnfw_ag(float r2, const float4 v0, const float4 v1, const float4 v2,
-                                        const float4 v3) {
-  return (r2 >= v0.z) ? tnfw_series(r2, v1, v2, v3) : tnfw_g_inner(r2 * v0.w, v1.x, v1.y);
+__device__ __forceinline__ float tnfw_ag(float r2, const float4* t) {
+  return (r2 >= t[1].x) ? tnfw_series(r2, t) : tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w);
 }
 
-// One point-subhalo pair accumulated into (ax, ay); v0..v3 are the subhalo's table entries.
-__device__ __forceinline__ void tnfw_pair(float px, float py, const float4 v0, const float4 v1,
-                                          const float4 v2, const float4 v3, float& ax, float& ay) {
-  const float dx = px - v0.x, dy = py - v0.y;
-  const float k = tnfw_ag(fmaf(dx, dx, dy * dy), v0, v1, v2, v3);
+// One point-subhalo pair accumulated into (ax, ay); t is the subhalo's table record.
+__device__ __forceinline__ void tnfw_pair(float px, float py, const float4* t, float& ax, float& ay) {
+  const float dx = px + t[0].x, dy = py + t[0].z;
+  const float k = tnfw_ag(fmaf(dx, dx, dy * dy), t);
   ax = fmaf(k, dx, ax);
   ay = fmaf(k, dy, ay);
 }
@@ -364,10 +384,10 @@ __device__ __forceinline__ void alpha_nfw(float x, float y, float Rs, float alph
 
 __device__ __forceinline__ void alpha_tnfw(float x, float y, float Rs, float alphaRs, float rt, float cx,
                                            float cy, float& ax, float& ay) {
-  float4 v0, v1, v2, v3;
-  tnfw_constants(cx, cy, Rs, alphaRs, rt, v0, v1, v2, v3);
+  float4 t[kSubStride];
+  tnfw_constants(cx, cy, Rs, alphaRs, rt, t);
   ax = 0.f; ay = 0.f;
-  tnfw_pair(x, y, v0, v1, v2, v3, ax, ay);
+  tnfw_pair(x, y, t, ax, ay);
 }
 
 // Deflection of one deflector-list profile at (x, y); returns (ax, ay).

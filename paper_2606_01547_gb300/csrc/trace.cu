@@ -23,13 +23,11 @@ namespace ls {
 __global__ void tnfw_prep_kernel(const float* __restrict__ soa, int n, int ld, float4* __restrict__ tab) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  float4 v0, v1, v2, v3;
-  tnfw_constants(soa[j], soa[ld + j], soa[2 * ld + j], soa[3 * ld + j], soa[4 * ld + j], v0, v1, v2, v3);
-  float4* t = tab + (size_t)kSubStride * j;
-  t[0] = v0;
-  t[1] = v1;
-  t[2] = v2;
-  t[3] = v3;
+  float4 t[kSubStride];
+  tnfw_constants(soa[j], soa[ld + j], soa[2 * ld + j], soa[3 * ld + j], soa[4 * ld + j], t);
+  float4* o = tab + (size_t)kSubStride * j;
+#pragma unroll
+  for (int c = 0; c < kSubStride; ++c) o[c] = t[c];
 }
 
 cudaError_t launch_tnfw_prep(const float* soa, int n, int ld, float4* table, cudaStream_t st) {
@@ -60,8 +58,12 @@ int unit_count(int nx, int ny, int s) {
 
 template <int NW>
 struct TraceSmem {
-  float4 sub[NW][32][kSubStride];
-  float2 part[NW][kUnitPts][32];
+  // Per warp: the 32 staged subhalo records, reused for the warp's partials once its subhalo
+  // loop has ended (so a warp never overwrites what another warp is still reading).
+  union WarpArea {
+    float4 sub[32][kSubStride];
+    float2 part[kUnitPts][32];
+  } wa[NW];
   float I[kUnitPts * 32];
 };
 
@@ -90,10 +92,19 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
 }
 
 // Partial subhalo deflections of one unit: warp w of this CTA sums slice (slice0 + w) of the
-// kTraceWarps-way split of the subhalo list and writes its 288 partials to part[w].
+// kTraceWarps-way split of the subhalo list and writes its 288 partials to wa[w].part.
+//
+// A lane's first 2 kPackedPairs samples run as packed pairs (FP32x2 instructions, two samples
+// per issue slot), the rest as scalars; the two kinds run on different FP32 pipes.  The packed
+// operations are element-wise the same IEEE operations as the scalar ones, so every sample's
+// deflection is the same whichever kind it is.
 template <int NWC>
 __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGeom& g, int slice0,
                                               TraceSmem<NWC>& sm) {
+  constexpr int kP = kPackedPairs;
+  constexpr int kS = kUnitPts - 2 * kP;
+  static_assert(kS >= 0, "more packed samples than samples");
+  constexpr int kPa = kP > 0 ? kP : 1, kSa = kS > 0 ? kS : 1;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int n = sys.n_sub;
@@ -101,18 +112,39 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   const int lo = (int)(((long long)n * slice) / kTraceWarps);
   const int hi = (int)(((long long)n * (slice + 1)) / kTraceWarps);
   const float4* __restrict__ tab = sys.sub;
+  auto& area = sm.wa[w];
 
-  float px[kUnitPts], py[kUnitPts], ax[kUnitPts], ay[kUnitPts];
+  float2 px2[kPa], py2[kPa], ax2[kPa], ay2[kPa];
+  float pxs[kSa], pys[kSa], axs[kSa], ays[kSa];
   float xmin = 3.0e38f, xmax = -3.0e38f, ymin = 3.0e38f, ymax = -3.0e38f;
 #pragma unroll
   for (int k = 0; k < kUnitPts; ++k) {
     int q = lane * kUnitPts + k;
     if (q >= g.nsamp) q = 0;
-    sample_xy(sys, g, q, px[k], py[k]);
-    xmin = fminf(xmin, px[k]); xmax = fmaxf(xmax, px[k]);
-    ymin = fminf(ymin, py[k]); ymax = fmaxf(ymax, py[k]);
-    ax[k] = 0.f;
-    ay[k] = 0.f;
+    float x, y;
+    sample_xy(sys, g, q, x, y);
+    xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
+    ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
+    if (k >= 2 * kP) {
+      pxs[k - 2 * kP] = x;
+      pys[k - 2 * kP] = y;
+    } else if (k & 1) {
+      px2[k >> 1].y = x;
+      py2[k >> 1].y = y;
+    } else {
+      px2[k >> 1].x = x;
+      py2[k >> 1].x = y;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kPa; ++i) {
+    ax2[i] = make_float2(0.f, 0.f);
+    ay2[i] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < kSa; ++i) {
+    axs[i] = 0.f;
+    ays[i] = 0.f;
   }
   // bounding box of the unit's samples (uniform across the warp)
 #pragma unroll
@@ -135,42 +167,81 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
 #pragma unroll
       for (int c = 0; c < kSubStride; ++c) {
         st[c] = __ldg(tab + (size_t)kSubStride * idx + c);
-        sm.sub[w][lane][c] = st[c];
+        area.sub[lane][c] = st[c];
       }
-      const float ddx = fmaxf(fmaxf(xmin - st[0].x, st[0].x - xmax), 0.f);
-      const float ddy = fmaxf(fmaxf(ymin - st[0].y, st[0].y - ymax), 0.f);
-      near = fmaf(ddx, ddx, ddy * ddy) < st[0].z;
+      // st[0] holds the negated centre
+      const float ddx = fmaxf(fmaxf(xmin + st[0].x, -st[0].x - xmax), 0.f);
+      const float ddy = fmaxf(fmaxf(ymin + st[0].z, -st[0].z - ymax), 0.f);
+      near = fmaf(ddx, ddx, ddy * ddy) < st[1].x;
     }
     const unsigned near_mask = __ballot_sync(0xffffffffu, near);
     __syncwarp();
     const int cnt = min(32, hi - base);
-    for (int q = 0; q < cnt; ++q) {
-      const float4 v0 = sm.sub[w][q][0];
-      const float4 v1 = sm.sub[w][q][1];
-      const float4 v2 = sm.sub[w][q][2];
-      const float4 v3 = sm.sub[w][q][3];
-      if (!((near_mask >> q) & 1u)) {
+    // far-field series for subhalo record t, all samples of the lane
+    auto far_pairs = [&](const float4* t) {
+      const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
 #pragma unroll
-        for (int k = 0; k < kUnitPts; ++k) {
-          const float dx = px[k] - v0.x, dy = py[k] - v0.y;
-          const float gg = tnfw_series(fmaf(dx, dx, dy * dy), v1, v2, v3);
-          ax[k] = fmaf(gg, dx, ax[k]);
-          ay[k] = fmaf(gg, dy, ay[k]);
-        }
-      } else {
+      for (int i = 0; i < kP; ++i) {
+        const float2 dx = __fadd2_rn(px2[i], ncx), dy = __fadd2_rn(py2[i], ncy);
+        const float2 gg = tnfw_series2(__ffma2_rn(dx, dx, __fmul2_rn(dy, dy)), t);
+        ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
+        ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
+      }
 #pragma unroll
-        for (int k = 0; k < kUnitPts; ++k) {
-          const float dx = px[k] - v0.x, dy = py[k] - v0.y;
-          const float gg = tnfw_ag(fmaf(dx, dx, dy * dy), v0, v1, v2, v3);
-          ax[k] = fmaf(gg, dx, ax[k]);
-          ay[k] = fmaf(gg, dy, ay[k]);
+      for (int i = 0; i < kS; ++i) {
+        const float dx = pxs[i] + t[0].x, dy = pys[i] + t[0].z;
+        const float gg = tnfw_series(fmaf(dx, dx, dy * dy), t);
+        axs[i] = fmaf(gg, dx, axs[i]);
+        ays[i] = fmaf(gg, dy, ays[i]);
+      }
+    };
+    // any form, per sample (subhalos the bounding-box test marked)
+    auto all_pairs = [&](const float4* t) {
+#pragma unroll
+      for (int i = 0; i < kP; ++i) {
+        tnfw_pair(px2[i].x, py2[i].x, t, ax2[i].x, ay2[i].x);
+        tnfw_pair(px2[i].y, py2[i].y, t, ax2[i].y, ay2[i].y);
+      }
+#pragma unroll
+      for (int i = 0; i < kS; ++i) tnfw_pair(pxs[i], pys[i], t, axs[i], ays[i]);
+    };
+    auto one = [&](int q) {
+      float4 t[kSubStride];
+#pragma unroll
+      for (int c = 0; c < kSubStride - 1; ++c) t[c] = area.sub[q][c];
+      if (!((near_mask >> q) & 1u)) far_pairs(t); else all_pairs(t);
+    };
+    int q = 0;
+    if constexpr (kFuseSubhalos == 2) {
+      // two far-field subhalos in one basic block: the scheduler overlaps one's reciprocal
+      // square roots with the other's polynomial (the sums still run in subhalo order)
+      for (; q + 1 < cnt; q += 2) {
+        if (!((near_mask >> q) & 3u)) {
+          float4 ta[kSubStride], tb[kSubStride];
+#pragma unroll
+          for (int c = 0; c < kSubStride - 1; ++c) {
+            ta[c] = area.sub[q][c];
+            tb[c] = area.sub[q + 1][c];
+          }
+          far_pairs(ta);
+          far_pairs(tb);
+        } else {
+          one(q);
+          one(q + 1);
         }
       }
     }
+    for (; q < cnt; ++q) one(q);
     __syncwarp();
   }
+  // the warp's staged records are dead from here on: its partials take their place
 #pragma unroll
-  for (int k = 0; k < kUnitPts; ++k) sm.part[w][k][lane] = make_float2(ax[k], ay[k]);
+  for (int i = 0; i < kP; ++i) {
+    area.part[2 * i][lane] = make_float2(ax2[i].x, ay2[i].x);
+    area.part[2 * i + 1][lane] = make_float2(ax2[i].y, ay2[i].y);
+  }
+#pragma unroll
+  for (int i = 0; i < kS; ++i) area.part[2 * kP + i][lane] = make_float2(axs[i], ays[i]);
 }
 
 // Finalise a unit from its kTraceWarps slice partials (part(slice, k, lane) in slice order):
@@ -219,7 +290,7 @@ __device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceS
   const UnitGeom g = unit_geom(sys, blk);
   unit_partials<kTraceWarps>(sys, g, 0, sm);
   __syncthreads();
-  unit_finalize(sys, g, sm.I, 32 * kTraceWarps, [&](int sl, int k, int l) { return sm.part[sl][k][l]; });
+  unit_finalize(sys, g, sm.I, 32 * kTraceWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; });
   __syncthreads();
   unit_bin_down(sys, g, sm.I, 32 * kTraceWarps);
   __syncthreads();
@@ -250,7 +321,7 @@ trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
 #pragma unroll
     for (int r = 0; r < CL; ++r) peers[r] = cluster.map_shared_rank(&sm, r);
     unit_finalize(sys, g, sm.I, 32 * NWC,
-                  [&](int sl, int k, int l) { return peers[sl / NWC]->part[sl % NWC][k][l]; });
+                  [&](int sl, int k, int l) { return peers[sl / NWC]->wa[sl % NWC].part[k][l]; });
     __syncthreads();
     unit_bin_down(sys, g, sm.I, 32 * NWC);
   }
@@ -360,7 +431,7 @@ __global__ void __launch_bounds__(256) deflection_kernel(const __grid_constant__
     __syncwarp();
     const int cnt = min(32, sys.n_sub - base);
     for (int q = 0; q < cnt; ++q)
-      tnfw_pair(px, py, s_sub[w][q][0], s_sub[w][q][1], s_sub[w][q][2], s_sub[w][q][3], ax, ay);
+      tnfw_pair(px, py, s_sub[w][q], ax, ay);
     __syncwarp();
   }
   for (int d = 0; d < sys.n_defl; ++d) {

@@ -33,30 +33,47 @@ class FitResult:
 
 
 def lbfgs_fit(sim: lenssim.Simulator, system: W.LensSystem, data: torch.Tensor, sigma_bkg: float, t_exp: float,
-              starts: np.ndarray, iters: int = 50, lr: float = 1.0, subhalo_table: int = -1) -> FitResult:
+              starts: np.ndarray, iters: int = 50, lr: float = 1.0, subhalo_table: int = -1,
+              restarts: int = 10, scale: Optional[np.ndarray] = None) -> FitResult:
     """Maximise logL from each row of `starts` ([n, 15]) with L-BFGS (strong-Wolfe line search).
 
     The n problems are independent; their negative log-likelihoods are summed so that one
-    batched lens_sim_grad call serves all of them at every function evaluation."""
-    P = torch.tensor(np.asarray(starts, np.float32), device=data.device).requires_grad_(True)
-    opt = torch.optim.LBFGS([P], lr=lr, max_iter=iters, history_size=20, line_search_fn="strong_wolfe",
-                            tolerance_grad=1e-9, tolerance_change=1e-12)
+    batched lens_sim_grad call serves all of them at every function evaluation.  L-BFGS runs on
+    parameters divided by `scale` (default: the prior widths), which evens out the very different
+    sensitivities of the 15 parameters, and is restarted with a fresh history (up to `restarts`
+    times, `iters` iterations each) until a restart no longer improves the summed likelihood."""
+    sc = torch.tensor(np.asarray(PRIOR_HI - PRIOR_LO if scale is None else scale, np.float32), device=data.device)
+    Z = (torch.tensor(np.asarray(starts, np.float32), device=data.device) / sc).requires_grad_(True)
     history = []
     evals = [0]
 
-    def closure():
-        opt.zero_grad()
-        L = lenssim.LensLogLike.apply(P, sim, system, data, sigma_bkg, t_exp, subhalo_table)
-        evals[0] += P.shape[0]
-        loss = -L.sum()
-        loss.backward()
-        history.append(float(L.max()))
-        return loss
+    def closure_for(opt):
+        def closure():
+            opt.zero_grad()
+            L = lenssim.LensLogLike.apply(Z * sc, sim, system, data, sigma_bkg, t_exp, subhalo_table)
+            evals[0] += Z.shape[0]
+            loss = -L.sum()
+            loss.backward()
+            history.append(float(L.max()))
+            return loss
+        return closure
 
-    opt.step(closure)
+    best = -float("inf")
+    for _ in range(max(1, restarts)):
+        opt = torch.optim.LBFGS([Z], lr=lr, max_iter=iters, history_size=20, line_search_fn="strong_wolfe",
+                                tolerance_grad=1e-12, tolerance_change=1e-14)
+        opt.step(closure_for(opt))
+        with torch.no_grad():
+            L = sim.grad(system, data, sigma_bkg, t_exp, (Z * sc).detach(), want_grad=False,
+                         subhalo_table=subhalo_table)
+        total = float(L.sum())
+        if total <= best + 1e-7 * abs(best):
+            break
+        best = total
+    P = (Z * sc).detach()
     with torch.no_grad():
-        L = sim.grad(system, data, sigma_bkg, t_exp, P.detach(), want_grad=False, subhalo_table=subhalo_table)
-    return FitResult(P.detach().cpu().numpy(), L.cpu().numpy(), history, evals[0] + P.shape[0])
+        L = sim.grad(system, data, sigma_bkg, t_exp, P, want_grad=False, subhalo_table=subhalo_table)
+    return FitResult(P.cpu().numpy(), L.cpu().numpy(), history, evals[0] + P.shape[0])
 
 
 def pso_fit(sim: lenssim.Simulator, system: W.LensSystem, data: torch.Tensor, sigma_bkg: float, t_exp: float,
