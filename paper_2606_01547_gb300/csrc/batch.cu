@@ -23,11 +23,8 @@ __global__ void prep_batch_meta_kernel(const BatchMeta* __restrict__ meta) {
   for (int jb = blockIdx.x; jb < n_jobs; jb += gridDim.x) {
     const PrepJob j = meta->prep[jb];
     for (int t = threadIdx.x; t < j.n; t += blockDim.x) {
-      float4 v[kSubStride];
-      tnfw_constants(j.soa[t], j.soa[j.ld + t], j.soa[2 * j.ld + t], j.soa[3 * j.ld + t], j.soa[4 * j.ld + t], v);
-      float4* o = j.tab + (size_t)kSubStride * t;
-#pragma unroll
-      for (int c = 0; c < kSubStride; ++c) o[c] = v[c];
+      tnfw_write_table(j.soa[t], j.soa[j.ld + t], j.soa[2 * j.ld + t], j.soa[3 * j.ld + t], j.soa[4 * j.ld + t], t,
+                       j.n, j.tab);
     }
   }
 }
@@ -96,7 +93,7 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
     }
     if (!dev_out[i]) stage_total += align256(npix * sizeof(float));
     if (y.subhalo_table < 0 && nsub[i] > 0) {
-      tab_total += align256((size_t)kSubStride * sizeof(float4) * nsub[i]);
+      tab_total += align256((size_t)kTableStride * sizeof(float4) * nsub[i]);
       if (!is_device_ptr(y.subhalos)) raw_total += align256(5 * sizeof(float) * (size_t)nsub[i]);
       ++n_prep;
     }
@@ -143,7 +140,7 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
     const lens_system& y = systems[i];
     if (y.subhalo_table < 0 && nsub[i] > 0) {
       tabs[i] = (float4*)(dbase + off);
-      off += align256((size_t)kSubStride * sizeof(float4) * nsub[i]);
+      off += align256((size_t)kTableStride * sizeof(float4) * nsub[i]);
     }
   }
   for (int i = 0; i < n; ++i) {

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) subhalo_field_kernel(const __grid_constan
   int pix;
   if (idx < n_samples) sample_coords(sys, idx, px, py, pix);
   float ax = 0.f, ay = 0.f;
+  const float4* __restrict__ mid_tab = sys.sub + (size_t)kSubStride * sys.n_sub;
   for (int base = 0; base < sys.n_sub; base += 32) {
     const int t = base + lane;
     if (t < sys.n_sub) {
@@ -60,7 +61,7 @@ __global__ void __launch_bounds__(256) subhalo_field_kernel(const __grid_constan
     __syncwarp();
     const int cnt = min(32, sys.n_sub - base);
     for (int q = 0; q < cnt; ++q)
-      tnfw_pair(px, py, s_sub[w][q], ax, ay);
+      tnfw_pair(px, py, s_sub[w][q], mid_tab + (size_t)kMidStride * (base + q), ax, ay);
     __syncwarp();
   }
   if (idx < n_samples) out[idx] = make_float2(ax, ay);
@@ -349,7 +350,7 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
   size_t need = sub_bytes + per_point * chunk + 256 * 8;
   if ((rc = ensure(s, s->grad_ws, need))) return rc;
   if (y.subhalo_table < 0 && y.n_subhalos > 0) {
-    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * n_sub_max))) return rc;
+    if ((rc = ensure(s, s->tab, kTableStride * sizeof(float4) * n_sub_max))) return rc;
     if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * n_sub_max))) return rc;
   }
   DevSystem d;
@@ -425,7 +426,7 @@ extern "C" int lens_sim_linear_amp(lens_sim* s, const lens_system* sys, const fl
   if ((rc = ensure(s, s->grad_ws, sub_bytes + per_point * chunk + 256 * 4))) return rc;
   const size_t n_sub_max = (size_t)sub_count(s, y);
   if (y.subhalo_table < 0 && y.n_subhalos > 0) {
-    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * n_sub_max))) return rc;
+    if ((rc = ensure(s, s->tab, kTableStride * sizeof(float4) * n_sub_max))) return rc;
     if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * n_sub_max))) return rc;
   }
   DevSystem d;

@@ -28,8 +28,9 @@ struct DevProfile {
   float p[8];
 };
 
-// One lens system as the kernels see it.  `sub` is the precomputed subhalo table (two
-// float4 per subhalo, see tnfw_prep); `out` receives the binned, unconvolved image.
+// One lens system as the kernels see it.  `sub` is the precomputed table of its n_sub subhalos
+// (kTableStride float4 per subhalo, see tnfw_write_table); `out` receives the binned,
+// unconvolved image.
 struct DevSystem {
   int nx, ny, s, n_defl;
   float dpix, x0, y0;
@@ -259,15 +260,28 @@ __device__ __forceinline__ float tnfw_g_far(float x2, float tau, float t2, float
 // tau >= 0.6 (below 1e-8 for tau >= 2) on that range, and Horner in FP32 is well conditioned
 // (sum |c_k y^k| / |G| < 1.1).
 constexpr int kFarTerms = 10;
-constexpr int kSubStride = 8;  // float4 per subhalo in the table
+constexpr int kSubStride = 8;   // float4 per subhalo record (staged through shared memory)
+constexpr int kMidTerms = 12;   // coefficients of the annulus polynomial
+constexpr int kMidStride = 3;   // float4 per subhalo in the annulus block
+constexpr int kTableStride = kSubStride + kMidStride;  // float4 per subhalo in a whole table
+// Largest tau whose annulus 4 <= x < 4 tau the 12-term polynomial covers to 1e-7 (relative, in
+// FP64 arithmetic); beyond it the annulus takes the closed form.
+constexpr float kMidTauMax = 9.5f;
 
-// Eight float4 (128 B) per subhalo, laid out for packed FP32x2 arithmetic (two samples per
-// instruction): centres negated and every series coefficient stored as a duplicated pair,
+// A subhalo table of n subhalos is n records of kSubStride float4 followed by n annulus blocks of
+// kMidStride float4.  The record (128 B) is laid out for packed FP32x2 arithmetic (two samples
+// per instruction): centres negated and every series coefficient stored as a duplicated pair,
 //   t0 = (-cx, -cx, -cy, -cy),           t1 = (r_far^2 = 16 max(tau,1)^2 Rs^2, 1/Rs^2, tau, A),
 //   t2 = (d_0, d_0, d_2, d_2),  t3 = (d_3, d_3, d_4, d_4),  t4 = (d_5, d_5, d_6, d_6),
-//   t5 = (d_7, d_7, d_8, d_8),  t6 = (d_9, d_9, d_10, d_10), t7 = 0,
+//   t5 = (d_7, d_7, d_8, d_8),  t6 = (d_9, d_9, d_10, d_10), t7 = (a_t, b_t, r_in^2, C),
 // with A = alpha_Rs tau^2 / ((1 - ln 2) Rs (tau^2+1)^2), so that alpha = A g(x^2) (dx, dy), and
 // d_k = A c_k Rs^(k+2): the series then runs in u = 1/r with no per-pair scaling by 1/Rs^2.
+// C = tau pi + (tau^2-1) ln tau.  The annulus block holds the 12 coefficients e_0..e_11 of
+//   A g = u^2 sum_j e_j t^j,  t = a_t u + b_t,
+// the polynomial in t in [-1, 1] that interpolates A Rs^2 G at the 12 Chebyshev nodes of
+// y = Rs u in [1/(4 tau), 1/4], i.e. on the annulus r_in = 4 Rs <= r < r_far.  When the annulus
+// is empty (tau <= 1) or too wide for 12 terms (tau > kMidTauMax), r_in^2 = r_far^2 and the
+// block is zero.
 __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, float alphaRs, float rt, float4* t) {
   const float tau = rt / Rs;
   const float t2 = tau * tau, t2m1 = t2 - 1.f, t2p1 = t2 + 1.f;
@@ -299,17 +313,86 @@ __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, flo
     rp *= Rs;
   }
   const float tm = fmaxf(tau, 1.f);
+  const float r_far2 = 16.f * tm * tm * Rs * Rs;
+  const bool annulus = tau > 1.f && tau <= kMidTauMax;
+  // t = (2y - (ylo + yhi)) / (yhi - ylo) with y = Rs u, ylo = 1/(4 tau), yhi = 1/4
+  const float ylo = 0.25f / tau, yhi = 0.25f;
+  const float at = annulus ? 2.f * Rs / (yhi - ylo) : 0.f;
+  const float bt = annulus ? -(ylo + yhi) / (yhi - ylo) : 0.f;
   t[0] = make_float4(-cx, -cx, -cy, -cy);
-  t[1] = make_float4(16.f * tm * tm * Rs * Rs, 1.f / (Rs * Rs), tau, A);
+  t[1] = make_float4(r_far2, 1.f / (Rs * Rs), tau, A);
   t[2] = make_float4(d[0], d[0], d[2], d[2]);
   t[3] = make_float4(d[3], d[3], d[4], d[4]);
   t[4] = make_float4(d[5], d[5], d[6], d[6]);
   t[5] = make_float4(d[7], d[7], d[8], d[8]);
   t[6] = make_float4(d[9], d[9], d[10], d[10]);
-  t[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+  t[7] = make_float4(at, bt, annulus ? 16.f * Rs * Rs : r_far2, C);
 }
 
-// Reciprocal square root on the MUFU with flush-to-zero: the far-field argument is at least
+// Annulus block of a subhalo from its record t (Rs = its scale radius): G at the 12 Chebyshev
+// nodes of y in [1/(4 tau), 1/4] by the x >= 4 closed form, Chebyshev coefficients by the
+// discrete cosine sum, then the monomial coefficients in t (T_j expanded by its recurrence,
+// whose integer coefficients are exact in FP32; the monomial form's FP32 condition number on
+// [-1, 1] is below 2 for tau <= kMidTauMax), scaled by A Rs^2.
+__device__ __forceinline__ void tnfw_mid_constants(float Rs, const float4* t, float4* m) {
+  float e[kMidTerms];
+#pragma unroll
+  for (int j = 0; j < kMidTerms; ++j) e[j] = 0.f;
+  if (t[7].z < t[1].x) {
+    const float tau = t[1].z, A = t[1].w, C = t[7].w;
+    const float t2 = tau * tau, t2m1 = t2 - 1.f;
+    const float ylo = 0.25f / tau, yhi = 0.25f;
+    float ch[kMidTerms];
+#pragma unroll
+    for (int j = 0; j < kMidTerms; ++j) ch[j] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMidTerms; ++k) {
+      const float tk = cospif((k + 0.5f) / kMidTerms);
+      const float y = fmaf(0.5f * (yhi - ylo), tk, 0.5f * (yhi + ylo));
+      const float x2 = 1.f / (y * y);
+      const float G = tnfw_g_far(x2, tau, t2, t2m1, C) * x2;
+      float Tm = 1.f, Tj = tk;  // T_0, T_1 at the node
+      ch[0] += G;
+      ch[1] += G * tk;
+#pragma unroll
+      for (int j = 2; j < kMidTerms; ++j) {
+        const float Tn = fmaf(2.f * tk, Tj, -Tm);
+        ch[j] += G * Tn;
+        Tm = Tj;
+        Tj = Tn;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kMidTerms; ++j) ch[j] *= (j == 0 ? 1.f : 2.f) / kMidTerms;
+    // monomial coefficients: e += ch_j * T_j, with T_j's coefficients from T_(j+1) = 2t T_j - T_(j-1)
+    float Tp[kMidTerms], Tc[kMidTerms];
+#pragma unroll
+    for (int i = 0; i < kMidTerms; ++i) { Tp[i] = 0.f; Tc[i] = 0.f; }
+    Tp[0] = 1.f;  // T_0
+    Tc[1] = 1.f;  // T_1
+    e[0] = ch[0];
+    e[1] = ch[1];
+#pragma unroll
+    for (int j = 2; j < kMidTerms; ++j) {
+#pragma unroll
+      for (int i = kMidTerms - 1; i >= 0; --i) {
+        const float Tn = (i > 0 ? 2.f * Tc[i - 1] : 0.f) - Tp[i];
+        Tp[i] = Tc[i];
+        Tc[i] = Tn;
+      }
+#pragma unroll
+      for (int i = 0; i < kMidTerms; ++i) e[i] = fmaf(ch[j], Tc[i], e[i]);
+    }
+    const float s = A * Rs * Rs;
+#pragma unroll
+    for (int j = 0; j < kMidTerms; ++j) e[j] *= s;
+  }
+  m[0] = make_float4(e[0], e[1], e[2], e[3]);
+  m[1] = make_float4(e[4], e[5], e[6], e[7]);
+  m[2] = make_float4(e[8], e[9], e[10], e[11]);
+}
+
+// Reciprocal square root on the MUFU with flush-to-zero: every argument it gets is at least
 // 16 Rs^2 > 0 and never denormal, so the IEEE-mode rsqrtf fix-up is not needed.
 __device__ __forceinline__ float rsqrt_ftz(float x) {
   float r;
@@ -317,11 +400,9 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
   return r;
 }
 
-// Far-field series from r^2: A g = u^2 (d_0 + u^2 (d_2 + d_3 u + ... + d_10 u^8)), u = 1/r,
+// Far-field series: A g = u^2 (d_0 + u^2 (d_2 + d_3 u + ... + d_10 u^8)), u = 1/r, u2 = u^2,
 // the same as A y^2 sum_k c_k y^k with y = Rs/r.  Scalar form (one sample).
-__device__ __forceinline__ float tnfw_series(float r2, const float4* t) {
-  const float u = rsqrt_ftz(r2);
-  const float u2 = u * u;
+__device__ __forceinline__ float tnfw_series_u(float u, float u2, const float4* t) {
   float p = fmaf(t[6].z, u, t[6].x);
   p = fmaf(p, u, t[5].z);
   p = fmaf(p, u, t[5].x);
@@ -334,11 +415,14 @@ __device__ __forceinline__ float tnfw_series(float r2, const float4* t) {
   return p * u2;
 }
 
-// Packed form (two samples per instruction): element-wise the same operations, hence the same
-// rounding, as the scalar form.
-__device__ __forceinline__ float2 tnfw_series2(float2 r2, const float4* t) {
-  const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-  const float2 u2 = __fmul2_rn(u, u);
+__device__ __forceinline__ float tnfw_series(float r2, const float4* t) {
+  const float u = rsqrt_ftz(r2);
+  return tnfw_series_u(u, u * u, t);
+}
+
+// Packed forms (two samples per instruction): element-wise the same operations, hence the same
+// rounding, as the scalar forms.
+__device__ __forceinline__ float2 tnfw_series2_u(float2 u, float2 u2, const float4* t) {
   float2 p = __ffma2_rn(make_float2(t[6].z, t[6].w), u, make_float2(t[6].x, t[6].y));
   p = __ffma2_rn(p, u, make_float2(t[5].z, t[5].w));
   p = __ffma2_rn(p, u, make_float2(t[5].x, t[5].y));
@@ -351,26 +435,88 @@ __device__ __forceinline__ float2 tnfw_series2(float2 r2, const float4* t) {
   return __fmul2_rn(p, u2);
 }
 
-// Inside the series range: the closed forms (x >= 4) or the small-x forms (x < 4), times A.
+__device__ __forceinline__ float2 tnfw_series2(float2 r2, const float4* t) {
+  const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+  return tnfw_series2_u(u, __fmul2_rn(u, u), t);
+}
+
+// Annulus polynomial: A g = u^2 sum_j e_j t^j, t = a_t u + b_t (Horner in t).
+__device__ __forceinline__ float tnfw_mid_u(float u, float u2, const float4* t, const float4* m) {
+  const float x = fmaf(t[7].x, u, t[7].y);
+  float p = fmaf(m[2].w, x, m[2].z);
+  p = fmaf(p, x, m[2].y);
+  p = fmaf(p, x, m[2].x);
+  p = fmaf(p, x, m[1].w);
+  p = fmaf(p, x, m[1].z);
+  p = fmaf(p, x, m[1].y);
+  p = fmaf(p, x, m[1].x);
+  p = fmaf(p, x, m[0].w);
+  p = fmaf(p, x, m[0].z);
+  p = fmaf(p, x, m[0].y);
+  p = fmaf(p, x, m[0].x);
+  return p * u2;
+}
+
+__device__ __forceinline__ float2 tnfw_mid2_u(float2 u, float2 u2, const float4* t, const float4* m) {
+  auto d = [](float v) { return make_float2(v, v); };
+  const float2 x = __ffma2_rn(d(t[7].x), u, d(t[7].y));
+  float2 p = __ffma2_rn(d(m[2].w), x, d(m[2].z));
+  p = __ffma2_rn(p, x, d(m[2].y));
+  p = __ffma2_rn(p, x, d(m[2].x));
+  p = __ffma2_rn(p, x, d(m[1].w));
+  p = __ffma2_rn(p, x, d(m[1].z));
+  p = __ffma2_rn(p, x, d(m[1].y));
+  p = __ffma2_rn(p, x, d(m[1].x));
+  p = __ffma2_rn(p, x, d(m[0].w));
+  p = __ffma2_rn(p, x, d(m[0].z));
+  p = __ffma2_rn(p, x, d(m[0].y));
+  p = __ffma2_rn(p, x, d(m[0].x));
+  return __fmul2_rn(p, u2);
+}
+
+// Inside the annulus or closer: the closed forms (x >= 4) or the small-x forms (x < 4), times A.
 // The x floor of 1e-6 (x^2 >= 1e-12) makes alpha vanish continuously at the subhalo centre.
-static __device__ __noinline__ float tnfw_g_inner(float x2, float tau, float A) {
+static __device__ __noinline__ float tnfw_g_inner(float x2, float tau, float A, float C) {
   x2 = fmaxf(x2, 1e-12f);
   const float t2 = tau * tau, t2m1 = t2 - 1.f;
-  const float C = tau * kPi + t2m1 * logf(tau);
   return A * ((x2 >= 16.f) ? tnfw_g_far(x2, tau, t2, t2m1, C) : tnfw_g_near(x2, tau, t2, t2m1, C));
 }
 
-// A g for one pair at squared distance r2, any distance.
-__device__ __forceinline__ float tnfw_ag(float r2, const float4* t) {
-  return (r2 >= t[1].x) ? tnfw_series(r2, t) : tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w);
+// A g for one pair at squared distance r2, any distance: the series beyond r_far, the annulus
+// polynomial on [r_in, r_far) when the annulus block m is given, the closed forms inside.
+__device__ __forceinline__ float tnfw_ag(float r2, const float4* t, const float4* m) {
+  if (r2 >= t[1].x) return tnfw_series(r2, t);
+  if (m != nullptr && r2 >= t[7].z) {
+    const float u = rsqrt_ftz(r2);
+    return tnfw_mid_u(u, u * u, t, m);
+  }
+  return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[7].w);
 }
 
-// One point-subhalo pair accumulated into (ax, ay); t is the subhalo's table record.
-__device__ __forceinline__ void tnfw_pair(float px, float py, const float4* t, float& ax, float& ay) {
+// One point-subhalo pair accumulated into (ax, ay); t is the subhalo's record, m its annulus
+// block (or nullptr: closed forms inside r_far).
+__device__ __forceinline__ void tnfw_pair(float px, float py, const float4* t, const float4* m, float& ax,
+                                          float& ay) {
   const float dx = px + t[0].x, dy = py + t[0].z;
-  const float k = tnfw_ag(fmaf(dx, dx, dy * dy), t);
+  const float k = tnfw_ag(fmaf(dx, dx, dy * dy), t, m);
   ax = fmaf(k, dx, ax);
   ay = fmaf(k, dy, ay);
+}
+
+// Writes subhalo j's record and annulus block into a table of n subhalos.  Not inlined, so
+// that every prep kernel (one system, batched) runs the very same code and tables built by
+// different launch paths are bitwise identical.
+static __device__ __noinline__ void tnfw_write_table(float cx, float cy, float Rs, float alphaRs, float rt, int j,
+                                                 int n, float4* __restrict__ tab) {
+  float4 t[kSubStride], m[kMidStride];
+  tnfw_constants(cx, cy, Rs, alphaRs, rt, t);
+  tnfw_mid_constants(Rs, t, m);
+  float4* o = tab + (size_t)kSubStride * j;
+#pragma unroll
+  for (int c = 0; c < kSubStride; ++c) o[c] = t[c];
+  float4* om = tab + (size_t)kSubStride * n + (size_t)kMidStride * j;
+#pragma unroll
+  for (int c = 0; c < kMidStride; ++c) om[c] = m[c];
 }
 
 __device__ __forceinline__ void alpha_nfw(float x, float y, float Rs, float alphaRs, float cx, float cy,
@@ -387,7 +533,7 @@ __device__ __forceinline__ void alpha_tnfw(float x, float y, float Rs, float alp
   float4 t[kSubStride];
   tnfw_constants(cx, cy, Rs, alphaRs, rt, t);
   ax = 0.f; ay = 0.f;
-  tnfw_pair(x, y, t, ax, ay);
+  tnfw_pair(x, y, t, nullptr, ax, ay);
 }
 
 // Deflection of one deflector-list profile at (x, y); returns (ax, ay).

@@ -160,8 +160,8 @@ int sub_count(lens_sim* s, const lens_system& y) {
   return y.subhalo_table >= 0 ? s->res->tables[y.subhalo_table].n : y.n_subhalos;
 }
 
-// Resolve the subhalo table of a system into device constants (kSubStride float4 per subhalo).
-// `tab_buf` must hold 16 * kSubStride * n bytes when the system carries raw subhalos.
+// Resolve the subhalo table of a system into device constants (kTableStride float4 per subhalo).
+// `tab_buf` must hold 16 * kTableStride * n bytes when the system carries raw subhalos.
 int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* raw_buf,
                      const float4** out_tab, int* out_n, cudaStream_t st) {
   if (y.subhalo_table >= 0) {
@@ -294,7 +294,7 @@ int lens_sim_register_subhalos(lens_sim* s, const float* soa, int n, int* table_
   DeviceGuard g(s->device);
   SubTable t{nullptr, n};
   if (n > 0) {
-    size_t bytes = kSubStride * sizeof(float4) * (size_t)n;
+    size_t bytes = kTableStride * sizeof(float4) * (size_t)n;
     if (s->budget && s->allocated + bytes > s->budget) return fail(s, LENS_ERR_OOM, "subhalo table exceeds the memory budget");
     cudaError_t e = cudaMalloc(&t.d, bytes);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(s, LENS_ERR_OOM, "cudaMalloc subhalo table: %s", cudaGetErrorString(e)); }
@@ -336,7 +336,7 @@ int lens_sim_image(lens_sim* s, const lens_system* systems, int n_sys, float* co
   if ((rc = ensure(s, s->img, sizeof(float) * max_pix))) return rc;
   if ((rc = ensure(s, s->stage, sizeof(float) * max_pix))) return rc;
   if (max_sub) {
-    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * max_sub))) return rc;
+    if ((rc = ensure(s, s->tab, kTableStride * sizeof(float4) * max_sub))) return rc;
     if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * max_sub))) return rc;
   }
   bool host_out = false;
@@ -381,7 +381,7 @@ int lens_sim_deflection(lens_sim* s, const lens_system* sys, const float* x, con
     return fail(s, LENS_ERR_INVALID_ARG, "point arrays must be device memory");
   cudaStream_t st = (cudaStream_t)stream;
   if (sys->subhalo_table < 0 && sys->n_subhalos > 0) {
-    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * sys->n_subhalos))) return rc;
+    if ((rc = ensure(s, s->tab, kTableStride * sizeof(float4) * sys->n_subhalos))) return rc;
     if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * sys->n_subhalos))) return rc;
   }
   DevSystem d;
@@ -444,7 +444,7 @@ int lens_sim_autotune(lens_sim* s, const lens_system* sample, int reps, int* bes
   const size_t npix = (size_t)sample->grid.nx * sample->grid.ny;
   if ((rc = ensure(s, s->img, sizeof(float) * npix))) return rc;
   if (sample->subhalo_table < 0 && sample->n_subhalos > 0) {
-    if ((rc = ensure(s, s->tab, kSubStride * sizeof(float4) * sample->n_subhalos))) return rc;
+    if ((rc = ensure(s, s->tab, kTableStride * sizeof(float4) * sample->n_subhalos))) return rc;
     if ((rc = ensure(s, s->raw_sub, 5 * sizeof(float) * sample->n_subhalos))) return rc;
   }
   DevSystem d;

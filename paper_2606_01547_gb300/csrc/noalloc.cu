@@ -20,7 +20,7 @@ int validate_light(lens_sim* s, const light_profile& p);
 
 namespace {
 
-constexpr size_t kTableBytes = (size_t)LENS_NOALLOC_MAX_SUBHALOS * ls::kSubStride * sizeof(float4);
+constexpr size_t kTableBytes = (size_t)LENS_NOALLOC_MAX_SUBHALOS * ls::kTableStride * sizeof(float4);
 constexpr size_t kImageBytes = (size_t)LENS_NOALLOC_MAX_PIXELS * sizeof(float);
 static_assert(kTableBytes + kImageBytes == LENS_NOALLOC_SCRATCH_BYTES, "scratch size mismatch");
 

@@ -97,8 +97,8 @@ size_t estimate_bytes(lens_server* srv, const lens_request& r) {
   const size_t s2 = (size_t)r.sys.grid.supersample * r.sys.grid.supersample;
   const size_t nsub = r.sys.subhalo_table >= 0 ? 0 : (size_t)std::max(r.sys.n_subhalos, 0);
   (void)srv;
-  if (r.kind == 0) return npix * 4 * 3 + nsub * (20 + 128) + 4096;
-  return npix * 4 * 6 + npix * s2 * 8 + nsub * (20 + 128) + 64 * 4 * 16 + 4096;
+  if (r.kind == 0) return npix * 4 * 3 + nsub * (20 + 176) + 4096;
+  return npix * 4 * 6 + npix * s2 * 8 + nsub * (20 + 176) + 64 * 4 * 16 + 4096;
 }
 
 int grow(float** d, float** h, size_t* cap, size_t need) {

@@ -23,11 +23,7 @@ namespace ls {
 __global__ void tnfw_prep_kernel(const float* __restrict__ soa, int n, int ld, float4* __restrict__ tab) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  float4 t[kSubStride];
-  tnfw_constants(soa[j], soa[ld + j], soa[2 * ld + j], soa[3 * ld + j], soa[4 * ld + j], t);
-  float4* o = tab + (size_t)kSubStride * j;
-#pragma unroll
-  for (int c = 0; c < kSubStride; ++c) o[c] = t[c];
+  tnfw_write_table(soa[j], soa[ld + j], soa[2 * ld + j], soa[3 * ld + j], soa[4 * ld + j], j, n, tab);
 }
 
 cudaError_t launch_tnfw_prep(const float* soa, int n, int ld, float4* table, cudaStream_t st) {
@@ -58,10 +54,14 @@ int unit_count(int nx, int ny, int s) {
 
 template <int NW>
 struct TraceSmem {
-  // Per warp: the 32 staged subhalo records, reused for the warp's partials once its subhalo
-  // loop has ended (so a warp never overwrites what another warp is still reading).
+  // Per warp: the 32 staged subhalo records (and the annulus blocks of those the bounding-box
+  // test marked), reused for the warp's partials once its subhalo loop has ended (so a warp
+  // never overwrites what another warp is still reading).
   union WarpArea {
-    float4 sub[32][kSubStride];
+    struct {
+      float4 sub[32][kSubStride];
+      float4 mid[32][kMidStride];
+    };
     float2 part[kUnitPts][32];
   } wa[NW];
   float I[kUnitPts * 32];
@@ -112,6 +112,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   const int lo = (int)(((long long)n * slice) / kTraceWarps);
   const int hi = (int)(((long long)n * (slice + 1)) / kTraceWarps);
   const float4* __restrict__ tab = sys.sub;
+  const float4* __restrict__ mid_tab = sys.sub + (size_t)kSubStride * n;
   auto& area = sm.wa[w];
 
   float2 px2[kPa], py2[kPa], ax2[kPa], ay2[kPa];
@@ -173,6 +174,10 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       const float ddx = fmaxf(fmaxf(xmin + st[0].x, -st[0].x - xmax), 0.f);
       const float ddy = fmaxf(fmaxf(ymin + st[0].z, -st[0].z - ymax), 0.f);
       near = fmaf(ddx, ddx, ddy * ddy) < st[1].x;
+      if (near) {
+#pragma unroll
+        for (int c = 0; c < kMidStride; ++c) area.mid[lane][c] = __ldg(mid_tab + (size_t)kMidStride * idx + c);
+      }
     }
     const unsigned near_mask = __ballot_sync(0xffffffffu, near);
     __syncwarp();
@@ -195,39 +200,70 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
         ays[i] = fmaf(gg, dy, ays[i]);
       }
     };
-    // any form, per sample (subhalos the bounding-box test marked)
-    auto all_pairs = [&](const float4* t) {
+    // subhalos the bounding-box test marked: series and annulus polynomial for every sample
+    // (packed, branch-free), each sample then keeps the form of its distance; only samples
+    // inside r_in call the closed forms
+    auto near_pairs = [&](const float4* t, const float4* m) {
+      const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
+      const float r_far2 = t[1].x, r_in2 = t[7].z;
+      auto pick = [&](float r2, float gs, float gm) {
+        if (r2 >= r_far2) return gs;
+        if (r2 >= r_in2) return gm;
+        return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[7].w);
+      };
 #pragma unroll
       for (int i = 0; i < kP; ++i) {
-        tnfw_pair(px2[i].x, py2[i].x, t, ax2[i].x, ay2[i].x);
-        tnfw_pair(px2[i].y, py2[i].y, t, ax2[i].y, ay2[i].y);
+        const float2 dx = __fadd2_rn(px2[i], ncx), dy = __fadd2_rn(py2[i], ncy);
+        const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+        const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+        const float2 u2 = __fmul2_rn(u, u);
+        const float2 gs = tnfw_series2_u(u, u2, t);
+        const float2 gm = tnfw_mid2_u(u, u2, t, m);
+        const float2 gg = make_float2(pick(r2.x, gs.x, gm.x), pick(r2.y, gs.y, gm.y));
+        ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
+        ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
       }
 #pragma unroll
-      for (int i = 0; i < kS; ++i) tnfw_pair(pxs[i], pys[i], t, axs[i], ays[i]);
+      for (int i = 0; i < kS; ++i) {
+        const float dx = pxs[i] + t[0].x, dy = pys[i] + t[0].z;
+        const float r2 = fmaf(dx, dx, dy * dy);
+        const float u = rsqrt_ftz(r2), u2 = u * u;
+        const float gg = pick(r2, tnfw_series_u(u, u2, t), tnfw_mid_u(u, u2, t, m));
+        axs[i] = fmaf(gg, dx, axs[i]);
+        ays[i] = fmaf(gg, dy, ays[i]);
+      }
     };
     auto one = [&](int q) {
       float4 t[kSubStride];
 #pragma unroll
-      for (int c = 0; c < kSubStride - 1; ++c) t[c] = area.sub[q][c];
-      if (!((near_mask >> q) & 1u)) far_pairs(t); else all_pairs(t);
+      for (int c = 0; c < kSubStride; ++c) t[c] = area.sub[q][c];
+      if (!((near_mask >> q) & 1u)) {
+        far_pairs(t);
+      } else {
+        float4 m[kMidStride];
+#pragma unroll
+        for (int c = 0; c < kMidStride; ++c) m[c] = area.mid[q][c];
+        near_pairs(t, m);
+      }
     };
     int q = 0;
-    if constexpr (kFuseSubhalos == 2) {
-      // two far-field subhalos in one basic block: the scheduler overlaps one's reciprocal
-      // square roots with the other's polynomial (the sums still run in subhalo order)
-      for (; q + 1 < cnt; q += 2) {
-        if (!((near_mask >> q) & 3u)) {
-          float4 ta[kSubStride], tb[kSubStride];
+    if constexpr (kFuseSubhalos > 1) {
+      // kFuseSubhalos far-field subhalos in one basic block: the scheduler overlaps one's
+      // reciprocal square roots and loads with another's polynomial (the sums still run in
+      // subhalo order)
+      constexpr unsigned kGroup = (1u << kFuseSubhalos) - 1u;
+      for (; q + kFuseSubhalos <= cnt; q += kFuseSubhalos) {
+        if (!((near_mask >> q) & kGroup)) {
+          float4 tg[kFuseSubhalos][kSubStride];
 #pragma unroll
-          for (int c = 0; c < kSubStride - 1; ++c) {
-            ta[c] = area.sub[q][c];
-            tb[c] = area.sub[q + 1][c];
-          }
-          far_pairs(ta);
-          far_pairs(tb);
+          for (int f = 0; f < kFuseSubhalos; ++f)
+#pragma unroll
+            for (int c = 0; c < kSubStride - 1; ++c) tg[f][c] = area.sub[q + f][c];
+#pragma unroll
+          for (int f = 0; f < kFuseSubhalos; ++f) far_pairs(tg[f]);
         } else {
-          one(q);
-          one(q + 1);
+#pragma unroll
+          for (int f = 0; f < kFuseSubhalos; ++f) one(q + f);
         }
       }
     }
@@ -422,6 +458,7 @@ __global__ void __launch_bounds__(256) deflection_kernel(const __grid_constant__
   const float px = valid ? xs[idx] : 0.f;
   const float py = valid ? ys[idx] : 0.f;
   float ax = 0.f, ay = 0.f;
+  const float4* __restrict__ mid_tab = sys.sub + (size_t)kSubStride * sys.n_sub;
   for (int base = 0; base < sys.n_sub; base += 32) {
     const int t = base + lane;
     if (t < sys.n_sub) {
@@ -431,7 +468,7 @@ __global__ void __launch_bounds__(256) deflection_kernel(const __grid_constant__
     __syncwarp();
     const int cnt = min(32, sys.n_sub - base);
     for (int q = 0; q < cnt; ++q)
-      tnfw_pair(px, py, s_sub[w][q], ax, ay);
+      tnfw_pair(px, py, s_sub[w][q], mid_tab + (size_t)kMidStride * (base + q), ax, ay);
     __syncwarp();
   }
   for (int d = 0; d < sys.n_defl; ++d) {
