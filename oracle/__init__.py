@@ -27,8 +27,9 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liblensoracle.so")
 
 LENS_CODES = {"SIS": 0, "SIE": 1, "EPL": 2, "SHEAR": 3, "POINT_MASS": 4, "NFW": 5, "TNFW": 6,
-              "EPL_E1E2": 7, "SIE_E1E2": 8}
-LIGHT_CODES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2}
+              "EPL_E1E2": 7, "SIE_E1E2": 8, "MULTIPOLE": 9, "EPL_MULTIPOLE_M1M3M4": 10}
+LIGHT_CODES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2, "SHAPELETS": 3}
+DEFL_PARAMS = 12   # parameters per deflector in the oracle's layout
 
 _lock = threading.Lock()
 _lib = None
@@ -56,7 +57,9 @@ class _OSys(ctypes.Structure):
                 ("src_type", ctypes.c_int),
                 ("src_p", ctypes.c_double * 8),
                 ("k", ctypes.c_int),
-                ("psf", ctypes.POINTER(ctypes.c_double))]
+                ("psf", ctypes.POINTER(ctypes.c_double)),
+                ("src_coef", ctypes.POINTER(ctypes.c_double)),
+                ("n_src_coef", ctypes.c_int)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -68,7 +71,7 @@ def lib():
         if _lib is None:
             L = ctypes.CDLL(build())
             L.oracle_alpha.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]
-            L.oracle_light.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp]
+            L.oracle_light.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
             L.oracle_alpha_system.argtypes = [ctypes.POINTER(_OSys), ctypes.c_int, _dp, _dp, _dp, _dp,
                                               ctypes.c_int]
             L.oracle_image_rows.argtypes = [ctypes.POINTER(_OSys), ctypes.c_int, ctypes.c_int, _dp,
@@ -109,7 +112,7 @@ class _Packed:
     def __init__(self, system):
         g = system.grid
         self.types = np.array([LENS_CODES[n] for n, _ in system.deflectors] or [0], np.int32)
-        p = np.zeros((max(len(system.deflectors), 1), 8))
+        p = np.zeros((max(len(system.deflectors), 1), DEFL_PARAMS))
         for i, (_, vals) in enumerate(system.deflectors):
             p[i, :len(vals)] = vals
         self.p = np.ascontiguousarray(p)
@@ -129,12 +132,16 @@ class _Packed:
             st.src_p[i] = float(v)
         st.k = k
         st.psf = _ptr(self.psf)
+        coef = getattr(system, "source_coeffs", None)
+        self.coef = _f64(coef).ravel().copy() if coef is not None else np.zeros(1)
+        st.src_coef = _ptr(self.coef)
+        st.n_src_coef = 0 if coef is None else int(self.coef.size)
         self.st = st
 
 
 def alpha(name: str, params, x, y) -> Tuple[np.ndarray, np.ndarray]:
     """Deflection of one profile at points (x, y)."""
-    p = np.zeros(8)
+    p = np.zeros(DEFL_PARAMS)
     p[:len(params)] = params
     x = _f64(x).ravel(); y = _f64(y).ravel()
     ax = np.empty_like(x); ay = np.empty_like(x)
@@ -144,13 +151,16 @@ def alpha(name: str, params, x, y) -> Tuple[np.ndarray, np.ndarray]:
     return ax, ay
 
 
-def light(name: str, params, x, y) -> np.ndarray:
-    """Source surface brightness of one light profile at points (x, y)."""
+def light(name: str, params, x, y, coeffs=None) -> np.ndarray:
+    """Source surface brightness of one light profile at points (x, y) (SHAPELETS: with its
+    amplitudes `coeffs`)."""
     p = np.zeros(8)
     p[:len(params)] = params
     x = _f64(x).ravel(); y = _f64(y).ravel()
     out = np.empty_like(x)
-    if lib().oracle_light(LIGHT_CODES[name], _ptr(p), x.size, _ptr(x), _ptr(y), _ptr(out)) != 0:
+    c = _f64(coeffs).ravel().copy() if coeffs is not None else np.zeros(1)
+    nc = 0 if coeffs is None else int(c.size)
+    if lib().oracle_light(LIGHT_CODES[name], _ptr(p), _ptr(c), nc, x.size, _ptr(x), _ptr(y), _ptr(out)) != 0:
         raise ValueError(f"oracle_light failed for {name}")
     return out
 

@@ -38,14 +38,19 @@ typedef struct {
   double dpix, x0, y0;
   int n_defl;
   const int* defl_type;     // [n_defl]
-  const double* defl_p;     // [n_defl][8]
+  const double* defl_p;     // [n_defl][kDeflParams]
   int n_sub;
   const double* sub;        // SoA [5][n_sub]: cx, cy, Rs, alpha_Rs, r_t (TNFW)
   int src_type;
   double src_p[8];
   int k;                    // PSF size (odd); 0 = no PSF
   const double* psf;        // [k][k]
+  const double* src_coef;   // SHAPELETS amplitudes (n_src_coef of them), else unused
+  int n_src_coef;
 } oracle_system;
+
+// Parameters per deflector in defl_p (the widest layout, EPL_MULTIPOLE_M1M3M4, has 12).
+constexpr int kDeflParams = 12;
 
 namespace {
 
@@ -115,8 +120,8 @@ constexpr double kLn2 = 0.69314718055994530942;
 
 // Profile type codes of this oracle's C interface (its own numbering).
 enum { O_SIS = 0, O_SIE = 1, O_EPL = 2, O_SHEAR = 3, O_POINT_MASS = 4, O_NFW = 5,
-       O_TNFW = 6, O_EPL_E1E2 = 7, O_SIE_E1E2 = 8 };
-enum { O_SERSIC_ELLIPSE_Q_PHI = 0, O_SERSIC_ELLIPSE = 1, O_SERSIC = 2 };
+       O_TNFW = 6, O_EPL_E1E2 = 7, O_SIE_E1E2 = 8, O_MULTIPOLE = 9, O_EPL_MULTIPOLE_M1M3M4 = 10 };
+enum { O_SERSIC_ELLIPSE_Q_PHI = 0, O_SERSIC_ELLIPSE = 1, O_SERSIC = 2, O_SHAPELETS = 3 };
 
 // ---------------------------------------------------------------------------
 // Ellipticity helpers.
@@ -301,6 +306,38 @@ void alpha_tnfw(const T& x, const T& y, const T& Rs, const T& alphaRs, const T& 
   ay = k * dy;
 }
 
+// Circular multipole of order m (deflection table rows MULTIPOLE and EPL_MULTIPOLE_M1M3M4;
+// the m-th angular Fourier mode of the convergence about a centre, as in Chu et al. 2013):
+//   kappa = r_E a_m cos(m (phi - phi_m)) / (2 r),
+// whose potential is psi = r_E a_m r cos(m dphi) / (1 - m^2) for m >= 2 and
+// psi = (r_E a_1 / 2) r ln(r / r_E) cos(dphi) for m = 1 (dphi = phi - phi_m); alpha = grad psi,
+// written as the radial and tangential derivatives rotated back to (x, y).
+// reading: parameters m, a_m, phi_m, cx, cy, r_E; a_m is dimensionless, relative to the
+// isothermal convergence r_E / (2 r); alpha = 0 when r < 1e-12 arcsec.
+template <class T>
+void alpha_multipole(const T& x, const T& y, int m, const T& am, const T& phim, const T& cx, const T& cy,
+                     const T& rE, T& ax, T& ay) {
+  T dx = x - cx, dy = y - cy;
+  T r = sqrt(dx * dx + dy * dy);
+  if (val(r) < 1e-12) { ax = T(0.0); ay = T(0.0); return; }
+  T phi = atan2(dy, dx);
+  T d = phi - phim;
+  T ar, at;  // d psi / d r and (1/r) d psi / d phi
+  if (m == 1) {
+    T B = 0.5 * rE * am;
+    T L = log(r / rE);
+    ar = B * (L + 1.0) * cos(d);
+    at = -B * L * sin(d);
+  } else {
+    T A = rE * am / (1.0 - (double)m * m);
+    ar = A * cos((double)m * d);
+    at = -A * (double)m * sin((double)m * d);
+  }
+  T c = cos(phi), sn = sin(phi);
+  ax = ar * c - at * sn;
+  ay = ar * sn + at * c;
+}
+
 // Dispatch one profile; p holds the profile's parameters in the order of its layout.
 template <class T>
 int alpha_profile(int type, const T* p, const T& x, const T& y, T& ax, T& ay) {
@@ -319,6 +356,25 @@ int alpha_profile(int type, const T* p, const T& x, const T& y, T& ax, T& ay) {
     case O_SIE_E1E2: {
       T q, phi; e1e2_to_qphi(p[1], p[2], q, phi);
       alpha_sie(x, y, p[0], q, phi, p[3], p[4], ax, ay); return 0;
+    }
+    case O_MULTIPOLE: {
+      const int m = (int)std::lround(val(p[0]));
+      if (m < 1 || std::fabs(val(p[0]) - m) > 1e-6 || !(val(p[5]) > 0.0)) return -1;
+      alpha_multipole(x, y, m, p[1], p[2], p[3], p[4], p[5], ax, ay); return 0;
+    }
+    case O_EPL_MULTIPOLE_M1M3M4: {
+      // reading: EPL_E1E2 (theta_E, gamma, e1, e2, cx, cy) plus the m = 1, 3, 4 multipoles about
+      // the same centre with r_E = theta_E and phi_m = phi + dphi_m, phi = atan2(e2, e1)/2 the
+      // EPL position angle; p = theta_E, gamma, e1, e2, cx, cy, a_1, dphi_1, a_3, dphi_3, a_4, dphi_4.
+      T q, phi; e1e2_to_qphi(p[2], p[3], q, phi);
+      alpha_epl(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay);
+      const int ms[3] = {1, 3, 4};
+      for (int i = 0; i < 3; ++i) {
+        T mx, my;
+        alpha_multipole(x, y, ms[i], p[6 + 2 * i], phi + p[7 + 2 * i], p[4], p[5], p[0], mx, my);
+        ax += mx; ay += my;
+      }
+      return 0;
     }
     default: return -1;
   }
@@ -358,6 +414,51 @@ int light_profile(int type, const T* p, const T& x, const T& y, T& I) {
   }
 }
 
+// Cartesian shapelets (light table row SHAPELETS; Refregier 2003):
+//   phi_n(u) = H_n(u) exp(-u^2/2) / sqrt(2^n n! sqrt(pi))   (H_n physicists' Hermite),
+//   B_(n1,n2)(x, y) = phi_n1((x-cx)/beta) phi_n2((y-cy)/beta) / beta,   orthonormal in the plane,
+//   I = sum_k amp_k B_(n1(k), n2(k)).
+// reading: p = n_max, beta, cx, cy; the (n_max+1)(n_max+2)/2 amplitudes are ordered by
+// n = n1 + n2 = 0, 1, ..., n_max and, within n, by n1 = n, n-1, ..., 0.
+// H_n by its three-term recurrence H_(n+1) = 2u H_n - 2n H_(n-1), the normalisation as a product.
+template <class T>
+int shapelets_I(const T* p, const double* coef, int n_coef, const T& x, const T& y, T& I) {
+  const int nmax = (int)std::lround(val(p[0]));
+  if (nmax < 0 || nmax > 30 || n_coef != (nmax + 1) * (nmax + 2) / 2 || !(val(p[1]) > 0.0) || !coef) return -1;
+  T u = (x - p[2]) / p[1], v = (y - p[3]) / p[1];
+  std::vector<T> hu(nmax + 1), hv(nmax + 1);
+  std::vector<double> norm(nmax + 1);
+  hu[0] = T(1.0); hv[0] = T(1.0);
+  if (nmax >= 1) { hu[1] = 2.0 * u; hv[1] = 2.0 * v; }
+  for (int n = 1; n < nmax; ++n) {
+    hu[n + 1] = 2.0 * u * hu[n] - 2.0 * n * hu[n - 1];
+    hv[n + 1] = 2.0 * v * hv[n] - 2.0 * n * hv[n - 1];
+  }
+  double f = std::sqrt(std::sqrt(kPi));  // 2^n n! sqrt(pi), n = 0
+  norm[0] = 1.0 / f;
+  double prod = std::sqrt(kPi);
+  for (int n = 1; n <= nmax; ++n) {
+    prod *= 2.0 * n;
+    norm[n] = 1.0 / std::sqrt(prod);
+  }
+  T sum = T(0.0);
+  int k = 0;
+  for (int n = 0; n <= nmax; ++n)
+    for (int n1 = n; n1 >= 0; --n1, ++k) {
+      const int n2 = n - n1;
+      sum += coef[k] * norm[n1] * norm[n2] * hu[n1] * hv[n2];
+    }
+  I = sum * exp(-0.5 * (u * u + v * v)) / p[1];
+  return 0;
+}
+
+// Any light profile: the table rows above, or shapelets with their amplitudes.
+template <class T>
+int source_I(int type, const T* p, const double* coef, int n_coef, const T& x, const T& y, T& I) {
+  if (type == O_SHAPELETS) return shapelets_I(p, coef, n_coef, x, y, I);
+  return light_profile(type, p, x, y, I);
+}
+
 inline double round32(double v) { return (double)(float)v; }
 // Round the value of a number to FP32, keeping its tangents (conditioning-floor mode).
 inline double r32(double v) { return round32(v); }
@@ -392,9 +493,10 @@ extern "C" int oracle_alpha(int type, const double* p, int n, const double* x, c
   return 0;
 }
 
-extern "C" int oracle_light(int type, const double* p, int n, const double* x, const double* y, double* I) {
+extern "C" int oracle_light(int type, const double* p, const double* coef, int n_coef, int n, const double* x,
+                            const double* y, double* I) {
   for (int i = 0; i < n; ++i)
-    if (light_profile<double>(type, p, x[i], y[i], I[i]) != 0) return -1;
+    if (source_I<double>(type, p, coef, n_coef, x[i], y[i], I[i]) != 0) return -1;
   return 0;
 }
 
@@ -416,7 +518,7 @@ static int total_alpha(const oracle_system* S, double x, double y, int fp32, dou
   ax = 0.0; ay = 0.0;
   for (int d = 0; d < S->n_defl; ++d) {
     double px, py;
-    if (alpha_profile<double>(S->defl_type[d], S->defl_p + 8 * d, x, y, px, py) != 0) return -1;
+    if (alpha_profile<double>(S->defl_type[d], S->defl_p + kDeflParams * d, x, y, px, py) != 0) return -1;
     if (fp32) { px = round32(px); py = round32(py); }
     ax += px; ay += py;
   }
@@ -458,7 +560,7 @@ extern "C" int oracle_image_rows(const oracle_system* S, int row0, int row1, dou
           double bx = x - ax, by = y - ay;
           if (fp32) { bx = round32(bx); by = round32(by); }
           double I;
-          err |= light_profile<double>(S->src_type, S->src_p, bx, by, I) != 0;
+          err |= source_I<double>(S->src_type, S->src_p, S->src_coef, S->n_src_coef, bx, by, I) != 0;
           sum += I;
         }
       }

@@ -146,6 +146,27 @@ def test_tnfw_pair_term_across_all_regimes(sim, tau):
     assert np.all(d <= 1e-5 * mag + 1e-10), float((d / (mag + 1e-30)).max())
 
 
+@pytest.mark.parametrize("tau", [0.8, 2.0, 5.0, 9.0, 12.0])
+def test_tnfw_subhalo_table_pair_term_across_all_regimes(sim, tau):
+    # one subhalo through the precomputed table: closed forms inside 4 Rs, the annulus polynomial
+    # on [4 Rs, 4 tau Rs) (none for tau <= 1, the closed form again for tau > 9.5), the series
+    # beyond; points crowd both annulus edges
+    Rs, ars = 0.02, 5e-3
+    tm = max(tau, 1.0)
+    xs = np.concatenate([np.logspace(-5, 3.5, 3000), np.linspace(3.9, 4.1, 300),
+                         np.linspace(4.0 * tm * 0.98, 4.0 * tm * 1.02, 300), np.linspace(4.0, 4.0 * tm, 1000)])
+    ang = np.random.default_rng(4).uniform(0, 2 * np.pi, xs.size)
+    x = (0.3 + xs * Rs * np.cos(ang)).astype(np.float32)
+    y = (-0.2 + xs * Rs * np.sin(ang)).astype(np.float32)
+    sub = np.array([[0.3], [-0.2], [Rs], [ars], [tau * Rs]], np.float32)
+    system = W.LensSystem(W.Grid(1, 1, 1, 1.0), [], sub, ("SERSIC", [1.0, 0.1, 1.0, 0.0, 0.0]))
+    ax, ay = sim.deflection(system, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    rx, ry = oracle.alpha("TNFW", [float(v) for v in sub[2:, 0]] + [float(sub[0, 0]), float(sub[1, 0])], x, y)
+    mag = np.hypot(rx, ry)
+    d = np.hypot(ax.cpu().numpy() - rx, ay.cpu().numpy() - ry)
+    assert np.all(d <= 1e-5 * mag + 1e-10), float((d / (mag + 1e-30)).max())
+
+
 def test_subhalo_sum_deflection_matches_oracle(sim):
     system = W.substructure_system(21, n_sub=2500, nx=8, s=1, k=0)
     x, y = _points(4096, 8, -4.0, 4.0)

@@ -422,3 +422,155 @@ def test_linear_amplitude_recovers_truth_and_minimises_chi2():
     chi = lambda amp: np.sum(w * (noisy - amp * m1) ** 2)
     assert chi(a[0]) < chi(a[0] * (1 + 1e-4)) and chi(a[0]) < chi(a[0] * (1 - 1e-4))
     assert abs(L[0] + 0.5 * chi(a[0])) < 1e-9 * chi(a[0])
+
+
+# ----------------------------------------------------------------------------- multipoles
+def _kappa_multipole(x, y, m, am, phim, cx, cy, rE):
+    # convergence of the m-th circular multipole: r_E a_m cos(m (phi - phi_m)) / (2 r)
+    dx, dy = x - cx, y - cy
+    return rE * am * np.cos(m * (np.arctan2(dy, dx) - phim)) / (2.0 * np.hypot(dx, dy))
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 6])
+def test_multipole_divergence_is_twice_kappa_and_curl_free(m):
+    p = [m, 0.07, 0.4, 0.1, -0.15, 1.3]
+    x, y = _pts(400, 40 + m, -2.5, 2.5)
+    r = np.hypot(x - 0.1, y + 0.15)
+    x, y = x[r > 0.2], y[r > 0.2]
+    div, curl = _fd_div_curl("MULTIPOLE", p, x, y, 1e-5)
+    k = _kappa_multipole(x, y, *p)
+    scale = np.abs(2 * k).max()
+    assert np.abs(div - 2 * k).max() < 1e-7 * scale
+    assert np.abs(curl).max() < 1e-7 * scale
+
+
+def _multipole_potential(x, y, m, am, phim, cx, cy, rE):
+    dx, dy = x - cx, y - cy
+    r = np.hypot(dx, dy)
+    d = np.arctan2(dy, dx) - phim
+    if m == 1:
+        return 0.5 * rE * am * r * np.log(r / rE) * np.cos(d)
+    return rE * am * r * np.cos(m * d) / (1.0 - m * m)
+
+
+@pytest.mark.parametrize("m", [1, 2, 4])
+def test_multipole_deflection_is_gradient_of_its_potential(m):
+    # the defining potential, differentiated numerically (Richardson-extrapolated central
+    # differences), against the oracle's analytic radial/tangential derivatives
+    p = [m, 0.05, -0.7, 0.0, 0.2, 0.9]
+    x, y = _pts(200, 50 + m, -2.0, 2.0)
+    x, y = x[np.hypot(x, y - 0.2) > 0.3], y[np.hypot(x, y - 0.2) > 0.3]
+
+    def grad(h):
+        gx = (_multipole_potential(x + h, y, *p) - _multipole_potential(x - h, y, *p)) / (2 * h)
+        gy = (_multipole_potential(x, y + h, *p) - _multipole_potential(x, y - h, *p)) / (2 * h)
+        return gx, gy
+    g1, g2 = grad(1e-3), grad(5e-4)
+    gx = (4 * g2[0] - g1[0]) / 3
+    gy = (4 * g2[1] - g1[1]) / 3
+    ax, ay = oracle.alpha("MULTIPOLE", p, x, y)
+    scale = np.abs(np.concatenate([ax, ay])).max()
+    assert np.abs(ax - gx).max() < 1e-9 * scale and np.abs(ay - gy).max() < 1e-9 * scale
+
+
+def test_multipole_m_ge_2_is_scale_free_and_rotates_with_phi_m():
+    # alpha of an m >= 2 multipole is homogeneous of degree 0 in r; turning phi_m by t turns
+    # the pattern by t
+    p = [3, 0.04, 0.3, 0.0, 0.0, 1.1]
+    x, y = _pts(100, 61, -1.5, 1.5)
+    a1 = oracle.alpha("MULTIPOLE", p, x, y)
+    a2 = oracle.alpha("MULTIPOLE", p, 2.7 * x, 2.7 * y)
+    np.testing.assert_allclose(a2[0], a1[0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(a2[1], a1[1], rtol=0, atol=1e-15)
+    t = 0.45
+    c, s = math.cos(t), math.sin(t)
+    q = list(p); q[2] = p[2] + t
+    b = oracle.alpha("MULTIPOLE", q, c * x - s * y, s * x + c * y)
+    np.testing.assert_allclose(b[0], c * a1[0] - s * a1[1], atol=1e-14)
+    np.testing.assert_allclose(b[1], s * a1[0] + c * a1[1], atol=1e-14)
+
+
+def test_epl_multipole_m1m3m4_is_epl_plus_three_multipoles():
+    th, g, e1, e2, cx, cy = 1.1, 2.05, 0.05, -0.03, 0.01, 0.02
+    a = [(1, 0.01, 0.2), (3, 0.02, 0.1), (4, 0.015, -0.3)]
+    p = [th, g, e1, e2, cx, cy] + [v for _, am, dp in a for v in (am, dp)]
+    x, y = _pts(300, 62)
+    ax, ay = oracle.alpha("EPL_MULTIPOLE_M1M3M4", p, x, y)
+    rx, ry = oracle.alpha("EPL_E1E2", [th, g, e1, e2, cx, cy], x, y)
+    phi = 0.5 * math.atan2(e2, e1)
+    for m, am, dp in a:
+        mx, my = oracle.alpha("MULTIPOLE", [m, am, phi + dp, cx, cy, th], x, y)
+        rx, ry = rx + mx, ry + my
+    np.testing.assert_allclose(ax, rx, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(ay, ry, rtol=1e-13, atol=1e-15)
+    # zero amplitudes reduce it to the EPL exactly
+    z = [th, g, e1, e2, cx, cy, 0.0, 0.3, 0.0, 1.0, 0.0, -2.0]
+    np.testing.assert_array_equal(oracle.alpha("EPL_MULTIPOLE_M1M3M4", z, x, y)[0],
+                                  oracle.alpha("EPL_E1E2", z[:6], x, y)[0])
+
+
+# ----------------------------------------------------------------------------- shapelets
+def _shapelet_index(nmax):
+    return [(n1, n - n1) for n in range(nmax + 1) for n1 in range(n, -1, -1)]
+
+
+def _phi_numpy(n, u):
+    # physicists' Hermite polynomial from numpy's library routine, with the orthonormal weight
+    from numpy.polynomial import hermite
+    c = np.zeros(n + 1); c[n] = 1.0
+    return hermite.hermval(u, c) * np.exp(-0.5 * u * u) / math.sqrt(2.0 ** n * math.factorial(n) * math.sqrt(math.pi))
+
+
+def test_shapelet_basis_matches_numpy_hermite():
+    nmax, beta, cx, cy = 8, 0.35, 0.05, -0.1
+    x, y = _pts(300, 70, -1.5, 1.5)
+    idx = _shapelet_index(nmax)
+    for k in (0, 1, 2, 5, 11, 20, 44):
+        c = np.zeros(len(idx)); c[k] = 1.0
+        n1, n2 = idx[k]
+        got = oracle.light("SHAPELETS", [nmax, beta, cx, cy], x, y, coeffs=c)
+        ref = _phi_numpy(n1, (x - cx) / beta) * _phi_numpy(n2, (y - cy) / beta) / beta
+        np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-13)
+
+
+def test_shapelet_basis_is_orthonormal_and_ordered():
+    # Gram matrix by the trapezoid rule on a wide fine grid (spectrally accurate for these
+    # Gaussian-damped functions), and parity of each basis function: B_(n1,n2) has parity
+    # (-1)^n1 in x and (-1)^n2 in y, which fixes the amplitude ordering
+    nmax, beta = 4, 0.5
+    idx = _shapelet_index(nmax)
+    g = np.linspace(-6.0, 6.0, 481)
+    X, Y = np.meshgrid(g, g)
+    dA = (g[1] - g[0]) ** 2
+    B = []
+    for k in range(len(idx)):
+        c = np.zeros(len(idx)); c[k] = 1.0
+        B.append(oracle.light("SHAPELETS", [nmax, beta, 0.0, 0.0], X.ravel(), Y.ravel(), coeffs=c))
+    B = np.array(B)
+    gram = B @ B.T * dA
+    np.testing.assert_allclose(gram, np.eye(len(idx)), atol=1e-10)
+    x, y = _pts(50, 71, 0.1, 1.0)
+    for k, (n1, n2) in enumerate(idx):
+        c = np.zeros(len(idx)); c[k] = 1.0
+        f = lambda u, v: oracle.light("SHAPELETS", [nmax, beta, 0.0, 0.0], u, v, coeffs=c)
+        np.testing.assert_allclose(f(-x, y), (-1) ** n1 * f(x, y), atol=1e-14)
+        np.testing.assert_allclose(f(x, -y), (-1) ** n2 * f(x, y), atol=1e-14)
+
+
+def _shapelet_flux(nmax, beta, coeffs):
+    # closed form: int phi_n du = pi^(1/4) 2^((1-n)/2) sqrt(n!) / (n/2)! for even n, 0 for odd n
+    def f1(n):
+        if n % 2:
+            return 0.0
+        return math.pi ** 0.25 * 2.0 ** ((1 - n) / 2) * math.sqrt(math.factorial(n)) / math.factorial(n // 2)
+    return sum(c * f1(n1) * f1(n2) * beta for c, (n1, n2) in zip(coeffs, _shapelet_index(nmax)))
+
+
+def test_unlensed_shapelet_image_sums_to_closed_form_flux():
+    nmax, beta = 6, 0.3
+    coeffs = np.random.default_rng(72).normal(size=(nmax + 1) * (nmax + 2) // 2)
+    system = W.LensSystem(W.Grid(120, 120, 2, 0.05), [], np.zeros((5, 0), np.float32),
+                          ("SHAPELETS", [nmax, beta, 0.02, -0.03]), None, coeffs)
+    img = oracle.image(system)
+    flux = _shapelet_flux(nmax, beta, coeffs)
+    assert abs(img.sum() - flux) < 1e-8 * np.abs(coeffs).sum()
