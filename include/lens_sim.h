@@ -53,6 +53,10 @@ typedef enum {
 #define LENS_MAX_SUPERSAMPLE 8
 #define LENS_MAX_PSF 135
 #define LENS_N_FREE_PARAMS 15
+#define LENS_PROFILE_PARAMS 12       /* floats in lens_profile.p (the widest layout uses 12) */
+#define LENS_MAX_SHAPELET_NMAX 10    /* SHAPELETS order limit: at most 66 amplitudes */
+#define LENS_MAX_SHAPELET_COEFFS ((LENS_MAX_SHAPELET_NMAX + 1) * (LENS_MAX_SHAPELET_NMAX + 2) / 2)
+#define LENS_MAX_MULTIPOLE_ORDER 32
 
 /* Deflector profile types and their parameter layouts p[] (deflection table rows). */
 typedef enum {
@@ -64,7 +68,15 @@ typedef enum {
   LENS_NFW = 5,         /* Rs, alpha_Rs, cx, cy             alpha_Rs = deflection at Rs        */
   LENS_TNFW = 6,        /* Rs, alpha_Rs, r_t, cx, cy        Baltz, Marshall & Oguri 2009       */
   LENS_EPL_E1E2 = 7,    /* theta_E, gamma, e1, e2, cx, cy  q = (1-c)/(1+c), c = |e|, phi = arg(e)/2 */
-  LENS_SIE_E1E2 = 8     /* theta_E, e1, e2, cx, cy                                              */
+  LENS_SIE_E1E2 = 8,    /* theta_E, e1, e2, cx, cy                                              */
+  LENS_MULTIPOLE = 9,   /* m, a_m, phi_m, cx, cy, r_E      circular multipole of integer order
+                         * m in [1, LENS_MAX_MULTIPOLE_ORDER], r_E > 0:
+                         * kappa = r_E a_m cos(m (phi - phi_m)) / (2 r); potential
+                         * r_E a_m r cos(m dphi) / (1 - m^2), or (r_E a_1 / 2) r ln(r/r_E) cos(dphi)
+                         * for m = 1                                                           */
+  LENS_EPL_MULTIPOLE_M1M3M4 = 10 /* theta_E, gamma, e1, e2, cx, cy, a_1, dphi_1, a_3, dphi_3, a_4,
+                         * dphi_4: EPL_E1E2 plus the m = 1, 3, 4 multipoles about its centre with
+                         * r_E = theta_E and phi_m = phi + dphi_m (phi = the EPL position angle) */
 } lens_profile_type;
 
 /* Source light profile types (light table rows). I = amp exp(-b_n [(R/R_s)^(1/n) - 1]),
@@ -72,10 +84,16 @@ typedef enum {
 typedef enum {
   LIGHT_SERSIC_ELLIPSE_Q_PHI = 0, /* amp, R_sersic, n, q, phi, cx, cy */
   LIGHT_SERSIC_ELLIPSE = 1,       /* amp, R_sersic, n, e1, e2, cx, cy */
-  LIGHT_SERSIC = 2                /* amp, R_sersic, n, cx, cy         */
+  LIGHT_SERSIC = 2,               /* amp, R_sersic, n, cx, cy         */
+  LIGHT_SHAPELETS = 3             /* n_max, beta, cx, cy: Cartesian shapelets (Refregier 2003),
+                                   * I = sum_k amp_k phi_n1(x'/beta) phi_n2(y'/beta) / beta with
+                                   * the orthonormal Hermite functions phi_n; integer n_max in
+                                   * [0, LENS_MAX_SHAPELET_NMAX]; the (n_max+1)(n_max+2)/2
+                                   * amplitudes come from lens_system.source_coeffs, ordered by
+                                   * n = n1 + n2 = 0..n_max and within n by n1 = n, n-1, ..., 0 */
 } light_profile_type;
 
-typedef struct { int type; float p[8]; } lens_profile;
+typedef struct { int type; float p[LENS_PROFILE_PARAMS]; } lens_profile;
 typedef struct { int type; float p[8]; } light_profile;
 
 /* Grid spec: nx, ny >= 1; supersample in [1, 8]; pixel_scale > 0; (x0, y0) = grid centre. */
@@ -95,6 +113,8 @@ typedef struct {
   int subhalo_table;
   light_profile source;
   int psf_id;
+  const float* source_coeffs;  /* HOST memory: SHAPELETS amplitudes (else NULL, 0) */
+  int n_source_coeffs;
 } lens_system;
 
 typedef struct {

@@ -25,7 +25,7 @@ constexpr float kOneMinusLn2 = 0.30685281944005469058f;
 
 struct DevProfile {
   int type;
-  float p[8];
+  float p[LENS_PROFILE_PARAMS];
 };
 
 // One lens system as the kernels see it.  `sub` is the precomputed table of its n_sub subhalos
@@ -36,6 +36,7 @@ struct DevSystem {
   float dpix, x0, y0;
   int src_type;
   float src[8];
+  float src_coef[LENS_MAX_SHAPELET_COEFFS];  // SHAPELETS amplitudes
   DevProfile defl[LENS_MAX_DEFLECTORS];
   int n_sub;
   int pad_;
@@ -537,6 +538,41 @@ __device__ __forceinline__ void alpha_tnfw(float x, float y, float Rs, float alp
 }
 
 // Deflection of one deflector-list profile at (x, y); returns (ax, ay).
+// Circular multipole of integer order m: kappa = r_E a_m cos(m (phi - phi_m)) / (2 r), alpha the
+// gradient of its potential (r_E a_m r cos(m dphi) / (1 - m^2); (r_E a_1 / 2) r ln(r/r_E) cos(dphi)
+// for m = 1), as radial and tangential components.  cos(m dphi), sin(m dphi) come from complex
+// powers of e^(i dphi) = ((dx, dy)/r) e^(-i phi_m), so no arctangent is needed.
+__device__ __forceinline__ void alpha_multipole(float x, float y, int m, float am, float phim, float cx, float cy,
+                                                float rE, float& ax, float& ay) {
+  const float dx = x - cx, dy = y - cy;
+  const float r2 = dx * dx + dy * dy;
+  if (!(r2 > 1e-40f)) { ax = 0.f; ay = 0.f; return; }
+  const float inv = rsqrtf(r2), r = r2 * inv;
+  const float c1 = dx * inv, s1 = dy * inv;
+  float sm, cm;
+  sincosf(phim, &sm, &cm);
+  const float cd = c1 * cm + s1 * sm, sd = s1 * cm - c1 * sm;
+  float ar, at;
+  if (m == 1) {
+    const float B = 0.5f * rE * am;
+    const float L = logf(r / rE);
+    ar = B * (L + 1.f) * cd;
+    at = -B * L * sd;
+  } else {
+    float cmd = cd, smd = sd;
+    for (int k = 1; k < m; ++k) {
+      const float c2 = cmd * cd - smd * sd;
+      smd = smd * cd + cmd * sd;
+      cmd = c2;
+    }
+    const float A = rE * am / (1.f - (float)(m * m));
+    ar = A * cmd;
+    at = -A * (float)m * smd;
+  }
+  ax = ar * c1 - at * s1;
+  ay = ar * s1 + at * c1;
+}
+
 static __device__ __noinline__ void alpha_profile(const DevProfile& P, float x, float y, float& ax, float& ay) {
   const float* p = P.p;
   switch (P.type) {
@@ -559,6 +595,21 @@ static __device__ __noinline__ void alpha_profile(const DevProfile& P, float x, 
       alpha_sie(x, y, p[0], q, phi, p[3], p[4], ax, ay);
       return;
     }
+    case LENS_MULTIPOLE: alpha_multipole(x, y, __float2int_rn(p[0]), p[1], p[2], p[3], p[4], p[5], ax, ay); return;
+    case LENS_EPL_MULTIPOLE_M1M3M4: {
+      float q, phi;
+      e1e2_to_qphi(p[2], p[3], q, phi);
+      alpha_epl(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay);
+      const int ms[3] = {1, 3, 4};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float mx, my;
+        alpha_multipole(x, y, ms[i], p[6 + 2 * i], phi + p[7 + 2 * i], p[4], p[5], p[0], mx, my);
+        ax += mx;
+        ay += my;
+      }
+      return;
+    }
     default: ax = 0.f; ay = 0.f; return;
   }
 }
@@ -576,8 +627,39 @@ __device__ __forceinline__ float sersic(float x, float y, float amp, float Rs, f
   return amp * expf(-bn * (pw - 1.f));
 }
 
-static __device__ __noinline__ float source_light(int type, const float* p, float x, float y) {
+// Cartesian shapelets: the orthonormal Hermite functions phi_n(u) by their normalised
+// three-term recurrence phi_(n+1) = sqrt(2/(n+1)) u phi_n - sqrt(n/(n+1)) phi_(n-1),
+// phi_0 = pi^(-1/4) exp(-u^2/2), then I = sum_k amp_k phi_n1(u) phi_n2(v) / beta in the
+// amplitude order n = n1 + n2 ascending, n1 descending.
+__device__ __forceinline__ float shapelets(const float* p, const float* coef, float x, float y) {
+  constexpr int N = LENS_MAX_SHAPELET_NMAX;
+  const int nmax = __float2int_rn(p[0]);
+  const float ib = 1.f / p[1];
+  const float u = (x - p[2]) * ib, v = (y - p[3]) * ib;
+  float fu[N + 1], fv[N + 1];
+  fu[0] = 0.75112554446494248f * expf(-0.5f * u * u);
+  fv[0] = 0.75112554446494248f * expf(-0.5f * v * v);
+  fu[1] = 1.41421356237309505f * u * fu[0];
+  fv[1] = 1.41421356237309505f * v * fv[0];
+#pragma unroll
+  for (int n = 1; n < N; ++n) {
+    const float a = sqrtf(2.f / (n + 1)), b = sqrtf((float)n / (n + 1));
+    fu[n + 1] = a * u * fu[n] - b * fu[n - 1];
+    fv[n + 1] = a * v * fv[n] - b * fv[n - 1];
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int n = 0; n <= N; ++n) {
+    if (n > nmax) break;
+#pragma unroll
+    for (int n1 = n; n1 >= 0; --n1) sum = fmaf(coef[n * (n + 1) / 2 + (n - n1)], fu[n1] * fv[n - n1], sum);
+  }
+  return sum * ib;
+}
+
+static __device__ __noinline__ float source_light(int type, const float* p, const float* coef, float x, float y) {
   switch (type) {
+    case LIGHT_SHAPELETS: return shapelets(p, coef, x, y);
     case LIGHT_SERSIC_ELLIPSE_Q_PHI: return sersic(x, y, p[0], p[1], p[2], p[3], p[4], p[5], p[6]);
     case LIGHT_SERSIC_ELLIPSE: {
       float q, phi;

@@ -79,8 +79,12 @@ void release(lens_sim* s, DevBuffer& b) {
 
 static bool finite(float v) { return v == v && v < 3.0e38f && v > -3.0e38f; }
 
+static bool is_integer_in(float v, int lo, int hi) {
+  return v >= (float)lo && v <= (float)hi && v == (float)(int)v;
+}
+
 int validate_profile(lens_sim* s, const lens_profile& p) {
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < LENS_PROFILE_PARAMS; ++k)
     if (!finite(p.p[k])) return fail(s, LENS_ERR_INVALID_ARG, "deflector parameter %d is not finite", k);
   switch (p.type) {
     case LENS_SIS: case LENS_SHEAR: case LENS_POINT_MASS: return LENS_OK;
@@ -104,13 +108,37 @@ int validate_profile(lens_sim* s, const lens_profile& p) {
     case LENS_TNFW:
       if (!(p.p[0] > 0.f && p.p[2] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "TNFW Rs and r_t must be > 0");
       return LENS_OK;
+    case LENS_MULTIPOLE:
+      if (!is_integer_in(p.p[0], 1, LENS_MAX_MULTIPOLE_ORDER))
+        return fail(s, LENS_ERR_INVALID_ARG, "multipole order m=%g not an integer in [1, %d]", p.p[0],
+                    LENS_MAX_MULTIPOLE_ORDER);
+      if (!(p.p[5] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "multipole r_E must be > 0");
+      return LENS_OK;
+    case LENS_EPL_MULTIPOLE_M1M3M4:
+      if (!(p.p[0] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL theta_E must be > 0");
+      if (!(p.p[1] > 1.f && p.p[1] < 3.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL gamma=%g not in (1,3)", p.p[1]);
+      if (!(p.p[2] * p.p[2] + p.p[3] * p.p[3] < 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL |e| >= 1");
+      return LENS_OK;
     default: return fail(s, LENS_ERR_INVALID_ARG, "unknown deflector type %d", p.type);
   }
 }
 
-int validate_light(lens_sim* s, const light_profile& p) {
+int validate_light(lens_sim* s, const light_profile& p, const float* coeffs, int n_coeffs) {
   for (int k = 0; k < 8; ++k)
     if (!finite(p.p[k])) return fail(s, LENS_ERR_INVALID_ARG, "source parameter %d is not finite", k);
+  if (p.type == LIGHT_SHAPELETS) {
+    if (!is_integer_in(p.p[0], 0, LENS_MAX_SHAPELET_NMAX))
+      return fail(s, LENS_ERR_INVALID_ARG, "shapelet n_max=%g not an integer in [0, %d]", p.p[0],
+                  LENS_MAX_SHAPELET_NMAX);
+    if (!(p.p[1] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "shapelet beta must be > 0");
+    const int nm = (int)p.p[0], want = (nm + 1) * (nm + 2) / 2;
+    if (!coeffs || n_coeffs != want)
+      return fail(s, LENS_ERR_INVALID_ARG, "shapelets need %d amplitudes in source_coeffs, got %d", want,
+                  coeffs ? n_coeffs : 0);
+    for (int k = 0; k < n_coeffs; ++k)
+      if (!finite(coeffs[k])) return fail(s, LENS_ERR_INVALID_ARG, "shapelet amplitude %d is not finite", k);
+    return LENS_OK;
+  }
   if (!(p.p[1] > 0.f) || !(p.p[2] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "Sersic R and n must be > 0");
   switch (p.type) {
     case LIGHT_SERSIC: return LENS_OK;
@@ -133,7 +161,7 @@ int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
       return fail(s, LENS_ERR_INVALID_ARG, "supersample %d not in [1, %d]", g.supersample, LENS_MAX_SUPERSAMPLE);
     if (!(g.pixel_scale > 0.f) || !finite(g.pixel_scale) || !finite(g.x0) || !finite(g.y0))
       return fail(s, LENS_ERR_INVALID_ARG, "bad pixel scale or grid centre");
-    int rc = validate_light(s, y.source);
+    int rc = validate_light(s, y.source, y.source_coeffs, y.n_source_coeffs);
     if (rc) return rc;
     if (y.psf_id < -1 || y.psf_id >= (int)s->res->psfs.size() || (y.psf_id >= 0 && !s->res->psfs[y.psf_id].d))
       return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", y.psf_id);
@@ -195,10 +223,12 @@ void fill_dev_system(const lens_system& y, DevSystem& d) {
   d.n_defl = y.n_deflectors;
   for (int k = 0; k < y.n_deflectors; ++k) {
     d.defl[k].type = y.deflectors[k].type;
-    for (int q = 0; q < 8; ++q) d.defl[k].p[q] = y.deflectors[k].p[q];
+    for (int q = 0; q < LENS_PROFILE_PARAMS; ++q) d.defl[k].p[q] = y.deflectors[k].p[q];
   }
   d.src_type = y.source.type;
   for (int q = 0; q < 8; ++q) d.src[q] = y.source.p[q];
+  if (y.source.type == LIGHT_SHAPELETS && y.source_coeffs)
+    for (int q = 0; q < y.n_source_coeffs && q < LENS_MAX_SHAPELET_COEFFS; ++q) d.src_coef[q] = y.source_coeffs[q];
 }
 
 DeviceGuard::DeviceGuard(int dev) {

@@ -36,6 +36,7 @@ struct Req {
   unsigned long long ticket = 0;
   lens_request r{};
   std::vector<lens_profile> defl;
+  std::vector<float> coef;  // source amplitudes (SHAPELETS), copied at submit
   size_t est_bytes = 0;
   Clock::time_point t_submit, t_done;
   int state = kQueued;
@@ -171,6 +172,7 @@ void issue(lens_server* srv, Slot* sl, CbArg* cb) {
       if (q->r.kind == 0) {
         lens_system y = q->r.sys;
         y.deflectors = q->defl.data();
+        y.source_coeffs = q->coef.empty() ? nullptr : q->coef.data();
         if (q->sub_dev) y.subhalos = q->sub_dev;
         sys.push_back(y);
         outs.push_back(sl->d_out + q->out_off);
@@ -199,6 +201,7 @@ void issue(lens_server* srv, Slot* sl, CbArg* cb) {
       cudaMemcpyAsync(din, hin, (npix + LENS_N_FREE_PARAMS) * sizeof(float), cudaMemcpyHostToDevice, sl->stream);
       lens_system y = q->r.sys;
       y.deflectors = q->defl.data();
+      y.source_coeffs = q->coef.empty() ? nullptr : q->coef.data();
       if (q->sub_dev) y.subhalos = q->sub_dev;
       float* dout = sl->d_out + q->out_off;
       q->status = lens_sim_grad(sl->sim, &y, din, q->r.sigma_bkg, q->r.t_exp, din + npix, 1, dout,
@@ -367,6 +370,8 @@ int lens_serve_submit(lens_server* srv, const lens_request* req, unsigned long l
   if (!q) return LENS_ERR_OOM;
   q->r = *req;
   q->defl.assign(req->sys.deflectors, req->sys.deflectors + req->sys.n_deflectors);
+  if (req->sys.source_coeffs && req->sys.n_source_coeffs > 0 && req->sys.n_source_coeffs <= LENS_MAX_SHAPELET_COEFFS)
+    q->coef.assign(req->sys.source_coeffs, req->sys.source_coeffs + req->sys.n_source_coeffs);
   q->est_bytes = estimate_bytes(srv, *req);
   std::lock_guard<std::mutex> lk(srv->mu);
   if (q->est_bytes > srv->budget) {

@@ -304,7 +304,7 @@ __device__ __forceinline__ void unit_finalize(const DevSystem& sys, const UnitGe
       sx += dax;
       sy += day;
     }
-    I[q] = source_light(sys.src_type, sys.src, x - sx, y - sy);
+    I[q] = source_light(sys.src_type, sys.src, sys.src_coef, x - sx, y - sy);
   }
 }
 

@@ -25,8 +25,8 @@ STATUS_NAMES = {0: "LENS_OK", -1: "LENS_ERR_INVALID_ARG", -2: "LENS_ERR_OOM", -3
                 -7: "LENS_ERR_CANCELLED"}
 
 LENS_TYPES = {"SIS": 0, "SIE": 1, "EPL": 2, "SHEAR": 3, "POINT_MASS": 4, "NFW": 5, "TNFW": 6,
-              "EPL_E1E2": 7, "SIE_E1E2": 8}
-LIGHT_TYPES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2}
+              "EPL_E1E2": 7, "SIE_E1E2": 8, "MULTIPOLE": 9, "EPL_MULTIPOLE_M1M3M4": 10}
+LIGHT_TYPES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2, "SHAPELETS": 3}
 MAX_DEFLECTORS = 8
 TRACE_VARIANTS = ("cta8", "cta8_minblocks3", "cluster2x4", "cluster4x2", "cluster8x1")
 _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
@@ -39,8 +39,11 @@ EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_
             "lens_serve_reset_stats", "lens_serve_destroy")
 
 
+PROFILE_PARAMS = 12   # floats in lens_profile.p
+
+
 class LensProfile(ctypes.Structure):
-    _fields_ = [("type", ctypes.c_int), ("p", ctypes.c_float * 8)]
+    _fields_ = [("type", ctypes.c_int), ("p", ctypes.c_float * PROFILE_PARAMS)]
 
 
 class LightProfile(ctypes.Structure):
@@ -60,7 +63,9 @@ class LensSystemC(ctypes.Structure):
                 ("n_subhalos", ctypes.c_int),
                 ("subhalo_table", ctypes.c_int),
                 ("source", LightProfile),
-                ("psf_id", ctypes.c_int)]
+                ("psf_id", ctypes.c_int),
+                ("source_coeffs", ctypes.POINTER(ctypes.c_float)),
+                ("n_source_coeffs", ctypes.c_int)]
 
 
 class SimConfig(ctypes.Structure):
@@ -250,6 +255,12 @@ class Simulator:
             c.n_subhalos = n
             c.subhalo_table = -1
         c.source = profile_struct(system.source[0], system.source[1], LIGHT_TYPES, LightProfile)
+        coef = getattr(system, "source_coeffs", None)
+        if coef is not None:
+            coef = np.ascontiguousarray(coef, dtype=np.float32).ravel()
+            keep.append(coef)
+            c.source_coeffs = coef.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+            c.n_source_coeffs = int(coef.size)
         c.psf_id = self.register_psf(system.psf) if (use_psf and system.psf is not None) else -1
         return c
 

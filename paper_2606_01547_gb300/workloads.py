@@ -180,6 +180,29 @@ def substructure_system(seed: int, n_sub: int = 10000, nx: int = 200, s: int = 3
                       moffat_psf(3.0, 0.12, dpix, k) if k > 0 else None)
 
 
+def multipole_shapelet_system(seed: int, n_max: int = 6, n_sub: int = 1000, nx: int = 60, s: int = 2,
+                              dpix: float = 0.05, k: int = 5) -> LensSystem:
+    """Profile-variant workload: EPL_MULTIPOLE_M1M3M4 (EPL as the substructure workload plus
+    m = 1, 3, 4 multipoles with a_m ~ U[0, 0.02], dphi_m ~ U[0, pi)) + shear + TNFW subhalos,
+    and a SHAPELETS source (beta ~ U[0.08, 0.2]", centre ~ U[-0.1, 0.1]", amplitudes
+    N(0, 1) / (1 + n1 + n2) plus 3 on the (0, 0) mode); Gaussian PSF (FWHM 0.1")."""
+    rng = _rng(seed)
+    epl, shear = _main_and_shear(rng)
+    th, g, q, phi, cx, cy = epl[1]
+    c = (1.0 - q) / (1.0 + q)
+    e1, e2 = c * math.cos(2.0 * phi), c * math.sin(2.0 * phi)
+    mult = [v for _ in range(3) for v in (rng.uniform(0.0, 0.02), rng.uniform(0.0, math.pi))]
+    lens = _profile("EPL_MULTIPOLE_M1M3M4", [th, g, e1, e2, cx, cy] + mult)
+    sub = subhalo_population(rng, n_sub)
+    beta = rng.uniform(0.08, 0.2)
+    src = _profile("SHAPELETS", [n_max, beta, rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1)])
+    idx = [(n1, n - n1) for n in range(n_max + 1) for n1 in range(n, -1, -1)]
+    coeffs = np.array([rng.normal() / (1.0 + n1 + n2) for n1, n2 in idx])
+    coeffs[0] += 3.0
+    return LensSystem(Grid(nx, nx, s, f32(dpix)), [lens, shear], sub, src,
+                      gaussian_psf(0.1, dpix, k) if k > 0 else None, coeffs.astype(np.float32))
+
+
 BATCH_GRIDS = (64, 100, 128, 200, 256)
 BATCH_SUPERSAMPLE = (1, 2, 3)
 BATCH_PSF = tuple(range(5, 32, 2))

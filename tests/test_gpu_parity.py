@@ -62,6 +62,35 @@ def test_substructure_small_images_match_oracle(sim, seed, nx, s, nsub, k):
     assert err <= tol, (err, floor)
 
 
+@pytest.mark.parametrize("seed,n_max,nx,s,nsub,k", [(0, 6, 44, 2, 300, 5), (1, 10, 37, 3, 120, 7),
+                                                     (2, 0, 25, 1, 0, 3), (3, 3, 30, 2, 50, 0)])
+def test_multipole_lens_and_shapelet_source_images_match_oracle(sim, seed, n_max, nx, s, nsub, k):
+    system = W.multipole_shapelet_system(seed, n_max=n_max, n_sub=nsub, nx=nx, s=s, k=k)
+    ref = oracle.image(system)
+    tol, floor = image_tol(system, ref)
+    err = rel_linf(gpu_image(sim, system), ref)
+    assert err <= tol, (err, floor)
+
+
+def test_shapelet_source_needs_its_amplitudes(sim):
+    from paper_2606_01547_gb300 import lenssim
+    system = W.multipole_shapelet_system(4, n_max=4, n_sub=0, nx=16, s=1, k=0)
+    for bad in (None, system.source_coeffs[:-1]):
+        b = W.LensSystem(system.grid, system.deflectors, system.subhalos, system.source, None, bad)
+        with pytest.raises(lenssim.LensSimError) as ei:
+            sim.image(b)
+        assert ei.value.code == lenssim.LENS_ERR_INVALID_ARG
+    for bad_src in (("SHAPELETS", [11, 0.1, 0.0, 0.0]), ("SHAPELETS", [2.5, 0.1, 0.0, 0.0]),
+                    ("SHAPELETS", [4, 0.0, 0.0, 0.0])):
+        b = W.LensSystem(system.grid, system.deflectors, system.subhalos, bad_src, None, system.source_coeffs)
+        with pytest.raises(lenssim.LensSimError):
+            sim.image(b)
+    bad_m = W.LensSystem(system.grid, [("MULTIPOLE", [2.5, 0.01, 0.0, 0.0, 0.0, 1.0])], system.subhalos,
+                         system.source, None, system.source_coeffs)
+    with pytest.raises(lenssim.LensSimError):
+        sim.image(bad_m)
+
+
 def test_unconvolved_image_and_no_subhalos(sim):
     system = W.substructure_system(5, n_sub=0, nx=40, s=2, k=0)
     ref = oracle.image(system)
@@ -112,7 +141,11 @@ PROFILES = [("SIS", [1.1, 0.05, -0.02]), ("SIE", [1.0, 0.8, 0.3, 0.0, 0.0]),
             ("EPL", [0.9, 2.17, 0.9, 2.5, -0.05, 0.0]), ("EPL", [1.0, 2.0, 0.7, 0.3, 0.0, 0.0]),
             ("SHEAR", [0.04, -0.03]), ("POINT_MASS", [0.3, 0.1, 0.2]), ("NFW", [0.4, 0.2, 0.05, 0.1]),
             ("TNFW", [0.3, 0.15, 1.5, -0.1, 0.0]), ("EPL_E1E2", [1.1, 2.05, 0.08, -0.05, 0.0, 0.03]),
-            ("SIE_E1E2", [1.0, -0.1, 0.06, 0.0, 0.0])]
+            ("SIE_E1E2", [1.0, -0.1, 0.06, 0.0, 0.0]),
+            ("MULTIPOLE", [1, 0.05, 0.4, 0.1, -0.1, 1.2]), ("MULTIPOLE", [2, 0.08, -0.3, 0.0, 0.0, 1.0]),
+            ("MULTIPOLE", [3, 0.03, 1.1, 0.05, 0.02, 1.3]), ("MULTIPOLE", [4, 0.02, 0.2, 0.0, 0.0, 0.9]),
+            ("MULTIPOLE", [7, 0.01, 2.0, 0.1, 0.1, 1.1]),
+            ("EPL_MULTIPOLE_M1M3M4", [1.1, 2.05, 0.08, -0.05, 0.0, 0.03, 0.01, 0.3, 0.02, -0.2, 0.015, 0.5])]
 
 
 @pytest.mark.parametrize("name,params", PROFILES)
