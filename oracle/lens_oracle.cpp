@@ -28,6 +28,7 @@
 #include <cstdint>
 #include <vector>
 #include <algorithm>
+#include <type_traits>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -120,7 +121,8 @@ constexpr double kLn2 = 0.69314718055994530942;
 
 // Profile type codes of this oracle's C interface (its own numbering).
 enum { O_SIS = 0, O_SIE = 1, O_EPL = 2, O_SHEAR = 3, O_POINT_MASS = 4, O_NFW = 5,
-       O_TNFW = 6, O_EPL_E1E2 = 7, O_SIE_E1E2 = 8, O_MULTIPOLE = 9, O_EPL_MULTIPOLE_M1M3M4 = 10 };
+       O_TNFW = 6, O_EPL_E1E2 = 7, O_SIE_E1E2 = 8, O_MULTIPOLE = 9, O_EPL_MULTIPOLE_M1M3M4 = 10,
+       O_CSE = 11 };
 enum { O_SERSIC_ELLIPSE_Q_PHI = 0, O_SERSIC_ELLIPSE = 1, O_SERSIC = 2, O_SHAPELETS = 3 };
 
 // ---------------------------------------------------------------------------
@@ -338,6 +340,59 @@ void alpha_multipole(const T& x, const T& y, int m, const T& am, const T& phim, 
   ay = ar * sn + at * c;
 }
 
+// Adaptive Gauss-Kronrod (7/15 points) on [a, b] to an absolute tolerance, for smooth
+// integrands; plain recursion, no tricks.
+template <class F>
+double gk15(const F& f, double a, double b, double tol, int depth = 0) {
+  static const double xk[8] = {0.991455371120812639206854697526329, 0.949107912342758524526189684047851,
+                               0.864864423359769072789712788640926, 0.741531185599394439863864773280788,
+                               0.586087235467691130294144845693013, 0.405845151377397166906606412076961,
+                               0.207784955007898467600689403773245, 0.0};
+  static const double wk[8] = {0.022935322010529224963732008058970, 0.063092092629978553290700663189204,
+                               0.104790010322250183839876322541518, 0.140653259715525918745189590510238,
+                               0.169004726639267902826583426598550, 0.190350578064785409913256402421014,
+                               0.204432940075298892414161999234649, 0.209482141084727828012999174891714};
+  static const double wg[4] = {0.129484966168869693270611432679082, 0.279705391489276667901467771423780,
+                               0.381830050505118944950369775488975, 0.417959183673469387755102040816327};
+  const double c = 0.5 * (a + b), h = 0.5 * (b - a);
+  double fc = f(c);
+  double K = wk[7] * fc, G = wg[3] * fc;
+  for (int j = 0; j < 7; ++j) {
+    const double f1 = f(c - h * xk[j]), f2 = f(c + h * xk[j]);
+    K += wk[j] * (f1 + f2);
+    if (j & 1) G += wg[j / 2] * (f1 + f2);
+  }
+  K *= h; G *= h;
+  if (std::fabs(K - G) <= tol || depth > 40) return K;
+  return gk15(f, a, c, 0.5 * tol, depth + 1) + gk15(f, c, b, 0.5 * tol, depth + 1);
+}
+
+// Cored steep ellipsoid (deflection table row CSE; Oguri 2021):
+//   kappa = A / (2 (s^2 + xi^2)^(3/2)),  xi^2 = x'^2 + y'^2 / q^2  (ellipse frame of phi),
+// deflection from the Schramm (1990) integrals for an elliptical convergence,
+//   alpha'_x = q x' J_0,  alpha'_y = q y' J_1,
+//   J_n = int_0^1 kappa(xi(u)^2) / (1 - (1 - q^2) u)^(n + 1/2) du,  xi(u)^2 = u (x'^2 + y'^2 / (1 - (1-q^2) u)),
+// by adaptive quadrature (FP64 only; not part of the differentiated model).
+// reading: parameters A, s, e1, e2, cx, cy with the e1/e2 convention of the other profiles.
+inline void alpha_cse(double x, double y, double A, double s, double q, double phi, double cx, double cy,
+                      double& ax, double& ay) {
+  const double c = std::cos(phi), sn = std::sin(phi);
+  const double dx = x - cx, dy = y - cy;
+  const double xp = c * dx + sn * dy, yp = -sn * dx + c * dy;
+  const double e = 1.0 - q * q;
+  auto kap = [&](double u) {
+    const double w = 1.0 - e * u;
+    const double xi2 = u * (xp * xp + yp * yp / w);
+    return A / (2.0 * std::pow(s * s + xi2, 1.5));
+  };
+  const double scale = A / (s * s * s) + 1e-300;
+  const double J0 = gk15([&](double u) { return kap(u) / std::sqrt(1.0 - e * u); }, 0.0, 1.0, 1e-15 * scale);
+  const double J1 = gk15([&](double u) { return kap(u) / std::pow(1.0 - e * u, 1.5); }, 0.0, 1.0, 1e-15 * scale);
+  const double axp = q * xp * J0, ayp = q * yp * J1;
+  ax = c * axp - sn * ayp;
+  ay = sn * axp + c * ayp;
+}
+
 // Dispatch one profile; p holds the profile's parameters in the order of its layout.
 template <class T>
 int alpha_profile(int type, const T* p, const T& x, const T& y, T& ax, T& ay) {
@@ -375,6 +430,15 @@ int alpha_profile(int type, const T* p, const T& x, const T& y, T& ax, T& ay) {
         ax += mx; ay += my;
       }
       return 0;
+    }
+    case O_CSE: {
+      if constexpr (std::is_same<T, double>::value) {
+        if (!(p[0] == p[0]) || !(p[1] > 0.0)) return -1;
+        double q, phi; e1e2_to_qphi<double>(p[2], p[3], q, phi);
+        alpha_cse(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay); return 0;
+      } else {
+        return -1;
+      }
     }
     default: return -1;
   }

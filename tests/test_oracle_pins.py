@@ -574,3 +574,32 @@ def test_unlensed_shapelet_image_sums_to_closed_form_flux():
     img = oracle.image(system)
     flux = _shapelet_flux(nmax, beta, coeffs)
     assert abs(img.sum() - flux) < 1e-8 * np.abs(coeffs).sum()
+
+
+# ----------------------------------------------------------------------------- cored steep ellipsoid
+def _kappa_cse(x, y, A, s, e1, e2, cx, cy):
+    phi = 0.5 * math.atan2(e2, e1)
+    c = math.hypot(e1, e2)
+    q = (1 - c) / (1 + c)
+    xp, yp = _ell_frame(x, y, phi, cx, cy)
+    return A / (2.0 * (s * s + xp * xp + yp * yp / (q * q)) ** 1.5)
+
+
+@pytest.mark.parametrize("p", [[0.5, 0.2, 0.2, -0.1, 0.1, 0.0], [1.3, 0.03, 0.35, 0.2, 0.0, 0.1],
+                               [0.1, 1.5, -0.4, 0.1, 0.0, 0.0]])
+def test_cse_divergence_is_twice_kappa_and_curl_free(p):
+    x, y = _pts(300, 80)
+    div, curl = _fd_div_curl("CSE", p, x, y, 1e-5)
+    k = _kappa_cse(x, y, *p)
+    np.testing.assert_allclose(div, 2 * k, rtol=2e-7, atol=1e-9 * np.abs(k).max())
+    assert np.abs(curl).max() < 1e-7 * np.abs(2 * k).max()
+
+
+def test_cse_round_closed_form():
+    # q = 1: enclosed mass of A / (2 (s^2 + r^2)^(3/2)) gives alpha = (A/r)(1/s - 1/sqrt(s^2 + r^2))
+    A, s = 0.7, 0.15
+    x, y = _pts(300, 81, -4.0, 4.0)
+    ax, ay = oracle.alpha("CSE", [A, s, 0.0, 0.0, 0.2, -0.1], x, y)
+    r = np.hypot(x - 0.2, y + 0.1)
+    np.testing.assert_allclose(np.hypot(ax, ay), (A / r) * (1 / s - 1 / np.sqrt(s * s + r * r)), rtol=1e-12)
+    np.testing.assert_allclose(ax * (y + 0.1) - ay * (x - 0.2), 0.0, atol=1e-13)
