@@ -122,7 +122,7 @@ constexpr double kLn2 = 0.69314718055994530942;
 // Profile type codes of this oracle's C interface (its own numbering).
 enum { O_SIS = 0, O_SIE = 1, O_EPL = 2, O_SHEAR = 3, O_POINT_MASS = 4, O_NFW = 5,
        O_TNFW = 6, O_EPL_E1E2 = 7, O_SIE_E1E2 = 8, O_MULTIPOLE = 9, O_EPL_MULTIPOLE_M1M3M4 = 10,
-       O_CSE = 11 };
+       O_CSE = 11, O_NFW_ELLIPSE_CSE = 12, O_HERNQUIST_ELLIPSE_CSE = 13 };
 enum { O_SERSIC_ELLIPSE_Q_PHI = 0, O_SERSIC_ELLIPSE = 1, O_SERSIC = 2, O_SHAPELETS = 3 };
 
 // ---------------------------------------------------------------------------
@@ -341,7 +341,8 @@ void alpha_multipole(const T& x, const T& y, int m, const T& am, const T& phim, 
 }
 
 // Adaptive Gauss-Kronrod (7/15 points) on [a, b] to an absolute tolerance, for smooth
-// integrands; plain recursion, no tricks.
+// integrands; plain recursion.  An interval is also accepted once the Gauss-Kronrod difference
+// is at the rounding level of its own sum (50 eps sum |w f|), and recursion stops at depth 20.
 template <class F>
 double gk15(const F& f, double a, double b, double tol, int depth = 0) {
   static const double xk[8] = {0.991455371120812639206854697526329, 0.949107912342758524526189684047851,
@@ -356,41 +357,99 @@ double gk15(const F& f, double a, double b, double tol, int depth = 0) {
                                0.381830050505118944950369775488975, 0.417959183673469387755102040816327};
   const double c = 0.5 * (a + b), h = 0.5 * (b - a);
   double fc = f(c);
-  double K = wk[7] * fc, G = wg[3] * fc;
+  double K = wk[7] * fc, G = wg[3] * fc, Kabs = wk[7] * std::fabs(fc);
   for (int j = 0; j < 7; ++j) {
     const double f1 = f(c - h * xk[j]), f2 = f(c + h * xk[j]);
     K += wk[j] * (f1 + f2);
+    Kabs += wk[j] * (std::fabs(f1) + std::fabs(f2));
     if (j & 1) G += wg[j / 2] * (f1 + f2);
   }
-  K *= h; G *= h;
-  if (std::fabs(K - G) <= tol || depth > 40) return K;
+  K *= h; G *= h; Kabs *= std::fabs(h);
+  const double err = std::fabs(K - G);
+  if (!(err == err) || err <= tol || err <= 50.0 * 2.220446049250313e-16 * Kabs || depth >= 20) return K;
   return gk15(f, a, c, 0.5 * tol, depth + 1) + gk15(f, c, b, 0.5 * tol, depth + 1);
 }
 
-// Cored steep ellipsoid (deflection table row CSE; Oguri 2021):
-//   kappa = A / (2 (s^2 + xi^2)^(3/2)),  xi^2 = x'^2 + y'^2 / q^2  (ellipse frame of phi),
-// deflection from the Schramm (1990) integrals for an elliptical convergence,
+// Deflection of an elliptical convergence kappa(xi_c^2), xi_c^2 = x'^2 + y'^2/q^2, in its frame,
+// by the Schramm (1990) integrals
 //   alpha'_x = q x' J_0,  alpha'_y = q y' J_1,
 //   J_n = int_0^1 kappa(xi(u)^2) / (1 - (1 - q^2) u)^(n + 1/2) du,  xi(u)^2 = u (x'^2 + y'^2 / (1 - (1-q^2) u)),
-// by adaptive quadrature (FP64 only; not part of the differentiated model).
-// reading: parameters A, s, e1, e2, cx, cy with the e1/e2 convention of the other profiles.
-inline void alpha_cse(double x, double y, double A, double s, double q, double phi, double cx, double cy,
+// with u = t^2 so that a logarithmic central cusp leaves a smooth integrand; adaptive quadrature
+// to the absolute tolerance `tol` (FP64 only; not part of the differentiated model).
+template <class K>
+void schramm_alpha(const K& kappa, double xp, double yp, double q, double tol, double& axp, double& ayp) {
+  const double e = 1.0 - q * q;
+  auto xi2 = [&](double u) { return u * (xp * xp + yp * yp / (1.0 - e * u)); };
+  const double J0 = gk15([&](double t) { const double u = t * t; return 2.0 * t * kappa(xi2(u)) / std::sqrt(1.0 - e * u); },
+                         0.0, 1.0, tol);
+  const double J1 = gk15([&](double t) { const double u = t * t; return 2.0 * t * kappa(xi2(u)) / std::pow(1.0 - e * u, 1.5); },
+                         0.0, 1.0, tol);
+  axp = q * xp * J0;
+  ayp = q * yp * J1;
+}
+
+// Elliptical-convergence profile: the frame of (q, phi, cx, cy), then the Schramm integrals.
+template <class K>
+void alpha_elliptical(const K& kappa, double x, double y, double q, double phi, double cx, double cy, double tol,
                       double& ax, double& ay) {
   const double c = std::cos(phi), sn = std::sin(phi);
   const double dx = x - cx, dy = y - cy;
   const double xp = c * dx + sn * dy, yp = -sn * dx + c * dy;
-  const double e = 1.0 - q * q;
-  auto kap = [&](double u) {
-    const double w = 1.0 - e * u;
-    const double xi2 = u * (xp * xp + yp * yp / w);
-    return A / (2.0 * std::pow(s * s + xi2, 1.5));
-  };
-  const double scale = A / (s * s * s) + 1e-300;
-  const double J0 = gk15([&](double u) { return kap(u) / std::sqrt(1.0 - e * u); }, 0.0, 1.0, 1e-15 * scale);
-  const double J1 = gk15([&](double u) { return kap(u) / std::pow(1.0 - e * u, 1.5); }, 0.0, 1.0, 1e-15 * scale);
-  const double axp = q * xp * J0, ayp = q * yp * J1;
+  double axp, ayp;
+  schramm_alpha(kappa, xp, yp, q, tol, axp, ayp);
   ax = c * axp - sn * ayp;
   ay = sn * axp + c * ayp;
+}
+
+// Cored steep ellipsoid (deflection table row CSE; Oguri 2021):
+//   kappa = A / (2 (s^2 + xi_c^2)^(3/2)).
+// reading: parameters A, s, e1, e2, cx, cy with the e1/e2 convention of the other profiles.
+inline void alpha_cse(double x, double y, double A, double s, double q, double phi, double cx, double cy,
+                      double& ax, double& ay) {
+  auto kap = [&](double xi2) { return A / (2.0 * std::pow(s * s + xi2, 1.5)); };
+  alpha_elliptical(kap, x, y, q, phi, cx, cy, 1e-15 * (std::fabs(A) / (s * s * s) + 1e-300), ax, ay);
+}
+
+// Projected NFW and Hernquist convergences in units of their normalisation, x = xi / Rs
+// (Bartelmann 1996; Hernquist 1990), with F(x) the NFW function:
+//   kappa_NFW = 2 (1 - F(x)) / (x^2 - 1),   kappa_Hernquist = ((2 + x^2) F(x) - 3) / (x^2 - 1)^2;
+// for |v| < 0.1, v = x^2 - 1, both use their series in v (F = sum (-v)^k / (2k+1)), which
+// removes the cancellation of the closed forms there (30 terms: below 1e-30 truncation).
+inline double kappa_hat_nfw(double x) {
+  const double v = x * x - 1.0;
+  if (std::fabs(v) < 0.1) {
+    double s = 0.0, pw = 1.0;  // (1 - F)/v = sum_{k>=1} (-1)^(k+1) v^(k-1) / (2k+1)
+    for (int k = 1; k <= 30; ++k) { s += ((k & 1) ? 1.0 : -1.0) * pw / (2.0 * k + 1.0); pw *= v; }
+    return 2.0 * s;
+  }
+  return 2.0 * (1.0 - nfw_F<double>(x)) / v;
+}
+inline double kappa_hat_hernquist(double x) {
+  const double v = x * x - 1.0;
+  if (std::fabs(v) < 0.1) {
+    double s = 0.0, pw = 1.0;  // bracket / v^2 = sum_{n>=2} (-1)^n 4 (n-1) / (4n^2 - 1) v^(n-2)
+    for (int n = 2; n <= 32; ++n) { s += ((n & 1) ? -1.0 : 1.0) * 4.0 * (n - 1) / (4.0 * n * n - 1.0) * pw; pw *= v; }
+    return s;
+  }
+  return ((2.0 + x * x) * nfw_F<double>(x) - 3.0) / (v * v);
+}
+
+// Elliptical NFW and Hernquist convergences (deflection table rows NFW_ELLIPSE_CSE and
+// HERNQUIST_ELLIPSE_CSE; the oracle takes the exact profiles, not a CSE decomposition).
+// reading: xi^2 = q x'^2 + y'^2/q (area-preserving, as for SIE and the Sersic source);
+// NFW: Rs, alpha_Rs, e1, e2, cx, cy with kappa = kappa_s kappa_hat_NFW(xi/Rs),
+// kappa_s Rs = alpha_Rs / (4 (1 - ln 2)); Hernquist: sigma0, Rs, e1, e2, cx, cy with
+// kappa = sigma0 kappa_hat_Hernquist(xi/Rs).
+inline void alpha_nfw_ellipse(double x, double y, double Rs, double alphaRs, double q, double phi, double cx,
+                              double cy, double& ax, double& ay) {
+  const double ks = alphaRs / (4.0 * (1.0 - kLn2) * Rs);
+  auto kap = [&](double xi2c) { return ks * kappa_hat_nfw(std::max(std::sqrt(q * xi2c), 1e-300) / Rs); };
+  alpha_elliptical(kap, x, y, q, phi, cx, cy, 1e-15 * std::fabs(ks), ax, ay);
+}
+inline void alpha_hernquist_ellipse(double x, double y, double sigma0, double Rs, double q, double phi, double cx,
+                                    double cy, double& ax, double& ay) {
+  auto kap = [&](double xi2c) { return sigma0 * kappa_hat_hernquist(std::max(std::sqrt(q * xi2c), 1e-300) / Rs); };
+  alpha_elliptical(kap, x, y, q, phi, cx, cy, 1e-15 * std::fabs(sigma0), ax, ay);
 }
 
 // Dispatch one profile; p holds the profile's parameters in the order of its layout.
@@ -436,6 +495,22 @@ int alpha_profile(int type, const T* p, const T& x, const T& y, T& ax, T& ay) {
         if (!(p[0] == p[0]) || !(p[1] > 0.0)) return -1;
         double q, phi; e1e2_to_qphi<double>(p[2], p[3], q, phi);
         alpha_cse(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay); return 0;
+      } else {
+        return -1;
+      }
+    }
+    case O_NFW_ELLIPSE_CSE:
+    case O_HERNQUIST_ELLIPSE_CSE: {
+      if constexpr (std::is_same<T, double>::value) {
+        double q, phi; e1e2_to_qphi<double>(p[2], p[3], q, phi);
+        if (type == O_NFW_ELLIPSE_CSE) {
+          if (!(p[0] > 0.0)) return -1;
+          alpha_nfw_ellipse(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay);
+        } else {
+          if (!(p[1] > 0.0)) return -1;
+          alpha_hernquist_ellipse(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay);
+        }
+        return 0;
       } else {
         return -1;
       }

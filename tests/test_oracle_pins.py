@@ -603,3 +603,80 @@ def test_cse_round_closed_form():
     r = np.hypot(x - 0.2, y + 0.1)
     np.testing.assert_allclose(np.hypot(ax, ay), (A / r) * (1 / s - 1 / np.sqrt(s * s + r * r)), rtol=1e-12)
     np.testing.assert_allclose(ax * (y + 0.1) - ay * (x - 0.2), 0.0, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------- elliptical NFW / Hernquist
+def _F_scalar(x):
+    if x < 1:
+        return math.acosh(1 / x) / math.sqrt(1 - x * x)
+    if x > 1:
+        return math.acos(1 / x) / math.sqrt(x * x - 1)
+    return 1.0
+
+
+def _kappa_hat(name, x):
+    # projected NFW (Bartelmann 1996) and Hernquist (Hernquist 1990) profiles, written from the
+    # 3-D densities' standard projections; x = 1 by its limit
+    v = x * x - 1
+    if name == "NFW_ELLIPSE_CSE":
+        return 2 / 3 if v == 0 else 2 * (1 - _F_scalar(x)) / v
+    return 4 / 15 if v == 0 else ((2 + x * x) * _F_scalar(x) - 3) / (v * v)
+
+
+def _kappa_ell(name, p, x, y):
+    a, Rs = (p[1] / (4 * (1 - LN2) * p[0]), p[0]) if name == "NFW_ELLIPSE_CSE" else (p[0], p[1])
+    phi = 0.5 * math.atan2(p[3], p[2])
+    c = math.hypot(p[2], p[3])
+    q = (1 - c) / (1 + c)
+    xp, yp = _ell_frame(x, y, phi, p[4], p[5])
+    xi = np.sqrt(q * xp * xp + yp * yp / q)
+    return np.array([a * _kappa_hat(name, v / Rs) for v in xi])
+
+
+def test_nfw_ellipse_round_equals_nfw_closed_form():
+    x, y = _pts(300, 90, -3.0, 3.0)
+    ax, ay = oracle.alpha("NFW_ELLIPSE_CSE", [0.8, 0.3, 0.0, 0.0, 0.05, -0.1], x, y)
+    rx, ry = oracle.alpha("NFW", [0.8, 0.3, 0.05, -0.1], x, y)
+    np.testing.assert_allclose(ax, rx, rtol=1e-11, atol=1e-14)
+    np.testing.assert_allclose(ay, ry, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("name,p", [("NFW_ELLIPSE_CSE", [0.8, 0.3, 0.15, -0.2, 0.05, 0.0]),
+                                    ("NFW_ELLIPSE_CSE", [0.2, 0.05, -0.3, 0.1, 0.0, 0.0]),
+                                    ("HERNQUIST_ELLIPSE_CSE", [0.5, 0.8, 0.1, -0.2, 0.0, 0.1]),
+                                    ("HERNQUIST_ELLIPSE_CSE", [1.2, 0.3, 0.25, 0.2, 0.0, 0.0])])
+def test_nfw_hernquist_ellipse_divergence_is_twice_kappa(name, p):
+    x, y = _pts(150, 91, -2.5, 2.5)
+    keep = np.hypot(x - p[4], y - p[5]) > 0.05
+    x, y = x[keep], y[keep]
+    div, curl = _fd_div_curl(name, p, x, y, 1e-5)
+    k = _kappa_ell(name, p, x, y)
+    np.testing.assert_allclose(div, 2 * k, rtol=1e-6, atol=1e-8 * np.abs(k).max())
+    assert np.abs(curl).max() < 1e-6 * np.abs(2 * k).max()
+
+
+def test_hernquist_round_enclosed_mass():
+    # alpha(r) = (2/r) int_0^r kappa r' dr' by 60-digit quadrature of the projected profile (the
+    # closed form cancels badly near x = 1 in FP64, so the reference runs in mpmath); and the
+    # profile integrates to unit mass, int_0^inf kappa_hat x dx = 1
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp
+    mp.dps = 60
+
+    def kh(x):
+        x = mp.mpf(x)
+        if abs(x * x - 1) < mp.mpf(10) ** -20:   # the limit; the next term is 8/35 (x^2 - 1)
+            return mp.mpf(4) / 15
+        F = mp.acosh(1 / x) / mp.sqrt(1 - x * x) if x < 1 else mp.acos(1 / x) / mp.sqrt(x * x - 1)
+        return ((2 + x * x) * F - 3) / (x * x - 1) ** 2
+
+    sigma0, Rs = 0.6, 0.4
+    r = np.array([0.01, 0.1, 0.39, 0.4, 0.41, 1.0, 3.0, 10.0])
+    ax, ay = oracle.alpha("HERNQUIST_ELLIPSE_CSE", [sigma0, Rs, 0.0, 0.0, 0.0, 0.0], r, np.zeros_like(r))
+    ref = []
+    for v in r:
+        pts = [0, min(v, Rs), v] if v > Rs else [0, v]
+        ref.append(float(2 * sigma0 * mp.quad(lambda t: kh(t / Rs) * t, pts) / v))
+    np.testing.assert_allclose(ax, ref, rtol=1e-11)
+    assert np.abs(ay).max() < 1e-15
+    assert abs(mp.quad(lambda t: kh(t) * t, [0, 1, 10, mp.inf]) - 1) < 1e-12
