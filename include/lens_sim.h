@@ -74,9 +74,16 @@ typedef enum {
                          * kappa = r_E a_m cos(m (phi - phi_m)) / (2 r); potential
                          * r_E a_m r cos(m dphi) / (1 - m^2), or (r_E a_1 / 2) r ln(r/r_E) cos(dphi)
                          * for m = 1                                                           */
-  LENS_EPL_MULTIPOLE_M1M3M4 = 10 /* theta_E, gamma, e1, e2, cx, cy, a_1, dphi_1, a_3, dphi_3, a_4,
+  LENS_EPL_MULTIPOLE_M1M3M4 = 10, /* theta_E, gamma, e1, e2, cx, cy, a_1, dphi_1, a_3, dphi_3, a_4,
                          * dphi_4: EPL_E1E2 plus the m = 1, 3, 4 multipoles about its centre with
                          * r_E = theta_E and phi_m = phi + dphi_m (phi = the EPL position angle) */
+  LENS_CSE = 11,        /* A, s, e1, e2, cx, cy               cored steep ellipsoid (Oguri 2021),
+                         * kappa = A / (2 (s^2 + x'^2 + y'^2/q^2)^(3/2)), s > 0              */
+  LENS_NFW_ELLIPSE_CSE = 12, /* Rs, alpha_Rs, e1, e2, cx, cy   NFW convergence on ellipses
+                         * xi^2 = q x'^2 + y'^2/q, evaluated as a sum of 44 CSEs (deflection
+                         * within 1e-7 of the exact profile's maximum on 1e-3 < xi/Rs < 1e3) */
+  LENS_HERNQUIST_ELLIPSE_CSE = 13 /* sigma0, Rs, e1, e2, cx, cy  kappa = sigma0 ((2 + x^2) F(x) - 3)
+                         * / (x^2 - 1)^2, x = xi/Rs (Hernquist 1990 projection), 44 CSEs     */
 } lens_profile_type;
 
 /* Source light profile types (light table rows). I = amp exp(-b_n [(R/R_s)^(1/n) - 1]),

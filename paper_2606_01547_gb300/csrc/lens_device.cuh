@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include "lens_sim.h"
+#include "cse_fits.h"
 
 namespace ls {
 
@@ -573,6 +574,55 @@ __device__ __forceinline__ void alpha_multipole(float x, float y, int m, float a
   ay = ar * s1 + at * c1;
 }
 
+// Cored steep ellipsoid, kappa = A / (2 (s^2 + x'^2 + y'^2/q^2)^(3/2)) in the frame of phi.
+// Closed form: kappa is -(A/s) d/ds of the softened isothermal ellipsoid's 1/(2 sqrt(s^2 + xi^2)),
+// so alpha is -(A/s) d/ds of its deflection; with psi = sqrt(q^2 (s^2 + x'^2) + y'^2) and
+// D = (1 + q^2) s^2 + 2 s psi + x'^2 + y'^2 (all terms positive, no cancellation):
+//   alpha'_x = A q x' (psi + q^2 s) / (s psi D),  alpha'_y = A q y' (psi + s) / (s psi D).
+__device__ __forceinline__ void alpha_cse(float x, float y, float A, float s, float q, float phi, float cx, float cy,
+                                          float& ax, float& ay) {
+  float sp, cp;
+  sincosf(phi, &sp, &cp);
+  const float dx = x - cx, dy = y - cy;
+  const float xp = cp * dx + sp * dy, yp = -sp * dx + cp * dy;
+  const float q2 = q * q;
+  const float psi = sqrtf(q2 * (s * s + xp * xp) + yp * yp);
+  const float D = (1.f + q2) * s * s + 2.f * s * psi + xp * xp + yp * yp;
+  const float f = A * q / (s * psi * D);
+  const float axp = f * xp * (psi + q2 * s), ayp = f * yp * (psi + s);
+  ax = cp * axp - sp * ayp;
+  ay = sp * axp + cp * ayp;
+}
+
+// Elliptical profile given as a sum of CSEs in units of Rs (tables of cse_fits.h):
+//   kappa = norm sum_i a_i / (2 (sigma_i^2 + xi^2/Rs^2)^(3/2)),  xi^2 = q x'^2 + y'^2/q.
+// In the CSE frame xi_c^2 = xi^2/q each term is a CSE with s_i = sigma_i Rs/sqrt(q) and
+// A_i = norm a_i Rs^3 q^(-3/2), hence A_i q / s_i = norm a_i Rs^2 / sigma_i.  All terms add with
+// the same sign (a_i >= 0), so the FP32 sum has no cancellation.
+__device__ __forceinline__ void alpha_cse_sum(const float* sig, const float* amp, float norm, float Rs, float q,
+                                              float phi, float cx, float cy, float x, float y, float& ax,
+                                              float& ay) {
+  float sp, cp;
+  sincosf(phi, &sp, &cp);
+  const float dx = x - cx, dy = y - cy;
+  const float xp = cp * dx + sp * dy, yp = -sp * dx + cp * dy;
+  const float q2 = q * q, isq = rsqrtf(q), xx = xp * xp, yy = yp * yp, r2 = xx + yy;
+  const float nR2 = norm * Rs * Rs;
+  float axp = 0.f, ayp = 0.f;
+  for (int i = 0; i < kCseTerms; ++i) {
+    const float s = sig[i] * Rs * isq;
+    const float psi = sqrtf(q2 * (s * s + xx) + yy);
+    const float D = (1.f + q2) * s * s + 2.f * s * psi + r2;
+    const float f = nR2 * amp[i] / (sig[i] * psi * D);
+    axp = fmaf(f, psi + q2 * s, axp);
+    ayp = fmaf(f, psi + s, ayp);
+  }
+  axp *= xp;
+  ayp *= yp;
+  ax = cp * axp - sp * ayp;
+  ay = sp * axp + cp * ayp;
+}
+
 static __device__ __noinline__ void alpha_profile(const DevProfile& P, float x, float y, float& ax, float& ay) {
   const float* p = P.p;
   switch (P.type) {
@@ -593,6 +643,25 @@ static __device__ __noinline__ void alpha_profile(const DevProfile& P, float x, 
       float q, phi;
       e1e2_to_qphi(p[1], p[2], q, phi);
       alpha_sie(x, y, p[0], q, phi, p[3], p[4], ax, ay);
+      return;
+    }
+    case LENS_CSE: {
+      float q, phi;
+      e1e2_to_qphi(p[2], p[3], q, phi);
+      alpha_cse(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay);
+      return;
+    }
+    case LENS_NFW_ELLIPSE_CSE: {
+      float q, phi;
+      e1e2_to_qphi(p[2], p[3], q, phi);
+      alpha_cse_sum(kCseNfwSigma, kCseNfwAmp, p[1] / (kOneMinusLn2 * 4.f * p[0]), p[0], q, phi, p[4], p[5], x, y, ax,
+                    ay);
+      return;
+    }
+    case LENS_HERNQUIST_ELLIPSE_CSE: {
+      float q, phi;
+      e1e2_to_qphi(p[2], p[3], q, phi);
+      alpha_cse_sum(kCseHernquistSigma, kCseHernquistAmp, p[0], p[1], q, phi, p[4], p[5], x, y, ax, ay);
       return;
     }
     case LENS_MULTIPOLE: alpha_multipole(x, y, __float2int_rn(p[0]), p[1], p[2], p[3], p[4], p[5], ax, ay); return;

@@ -114,6 +114,15 @@ int validate_profile(lens_sim* s, const lens_profile& p) {
                     LENS_MAX_MULTIPOLE_ORDER);
       if (!(p.p[5] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "multipole r_E must be > 0");
       return LENS_OK;
+    case LENS_NFW_ELLIPSE_CSE:
+    case LENS_HERNQUIST_ELLIPSE_CSE:
+      if (!(p.p[p.type == LENS_NFW_ELLIPSE_CSE ? 0 : 1] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "Rs must be > 0");
+      if (!(p.p[2] * p.p[2] + p.p[3] * p.p[3] < 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "|e| >= 1");
+      return LENS_OK;
+    case LENS_CSE:
+      if (!(p.p[1] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "CSE core s must be > 0");
+      if (!(p.p[2] * p.p[2] + p.p[3] * p.p[3] < 1.f)) return fail(s, LENS_ERR_INVALID_ARG, "CSE |e| >= 1");
+      return LENS_OK;
     case LENS_EPL_MULTIPOLE_M1M3M4:
       if (!(p.p[0] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL theta_E must be > 0");
       if (!(p.p[1] > 1.f && p.p[1] < 3.f)) return fail(s, LENS_ERR_INVALID_ARG, "EPL gamma=%g not in (1,3)", p.p[1]);

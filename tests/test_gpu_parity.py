@@ -145,7 +145,12 @@ PROFILES = [("SIS", [1.1, 0.05, -0.02]), ("SIE", [1.0, 0.8, 0.3, 0.0, 0.0]),
             ("MULTIPOLE", [1, 0.05, 0.4, 0.1, -0.1, 1.2]), ("MULTIPOLE", [2, 0.08, -0.3, 0.0, 0.0, 1.0]),
             ("MULTIPOLE", [3, 0.03, 1.1, 0.05, 0.02, 1.3]), ("MULTIPOLE", [4, 0.02, 0.2, 0.0, 0.0, 0.9]),
             ("MULTIPOLE", [7, 0.01, 2.0, 0.1, 0.1, 1.1]),
-            ("EPL_MULTIPOLE_M1M3M4", [1.1, 2.05, 0.08, -0.05, 0.0, 0.03, 0.01, 0.3, 0.02, -0.2, 0.015, 0.5])]
+            ("EPL_MULTIPOLE_M1M3M4", [1.1, 2.05, 0.08, -0.05, 0.0, 0.03, 0.01, 0.3, 0.02, -0.2, 0.015, 0.5]),
+            ("CSE", [0.5, 0.2, 0.2, -0.1, 0.1, 0.0]), ("CSE", [1.3, 0.03, 0.35, 0.2, 0.0, 0.1]),
+            ("CSE", [0.1, 1.5, -0.4, 0.1, 0.0, 0.0]),
+            ("NFW_ELLIPSE_CSE", [0.8, 0.3, 0.15, -0.2, 0.05, 0.0]), ("NFW_ELLIPSE_CSE", [3.0, 1.0, 0.05, 0.02, 0.0, 0.0]),
+            ("HERNQUIST_ELLIPSE_CSE", [0.5, 0.8, 0.1, -0.2, 0.0, 0.1]),
+            ("HERNQUIST_ELLIPSE_CSE", [1.2, 0.3, 0.25, 0.2, 0.0, 0.0])]
 
 
 @pytest.mark.parametrize("name,params", PROFILES)
