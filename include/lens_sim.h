@@ -167,8 +167,9 @@ int lens_sim_deflection(lens_sim* sim, const lens_system* sys, const float* x, c
 int lens_sim_convolve(lens_sim* sim, const float* in, int n_img, int ny, int nx, int psf_id, float* out,
                       void* stream);
 
-/* Launch variants of the fused trace kernel (one CTA per work unit; the same capped at 80
- * registers; thread-block clusters of 2, 4 or 8 CTAs per unit).  Every variant gives
+/* Launch variants of the fused trace kernel (0: one CTA of 8 warps per work unit; 1: one CTA of
+ * 4 warps that sums the unit's 8 subhalo slices in two passes; 2-4: thread-block clusters of
+ * 2, 4 or 8 CTAs per unit).  Every variant gives
  * bitwise-identical images; only the speed differs.  lens_sim_autotune times each variant
  * on `sample` (reps launches each, CUDA events on `stream`, synchronising it), makes the
  * fastest the handle's default for single-system calls, and reports the index and the mean

@@ -92,7 +92,7 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
 }
 
 // Partial subhalo deflections of one unit: warp w of this CTA sums slice (slice0 + w) of the
-// kTraceWarps-way split of the subhalo list and writes its 288 partials to wa[w].part.
+// kTraceWarps-way split of the subhalo list and writes its 288 partials to wa[area0 + w].part.
 //
 // A lane's first 2 kPackedPairs samples run as packed pairs (FP32x2 instructions, two samples
 // per issue slot), the rest as scalars; the two kinds run on different FP32 pipes.  The packed
@@ -100,7 +100,7 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
 // deflection is the same whichever kind it is.
 template <int NWC>
 __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGeom& g, int slice0,
-                                              TraceSmem<NWC>& sm) {
+                                              TraceSmem<NWC>& sm, int area0 = 0) {
   constexpr int kP = kPackedPairs;
   constexpr int kS = kUnitPts - 2 * kP;
   static_assert(kS >= 0, "more packed samples than samples");
@@ -113,7 +113,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   const int hi = (int)(((long long)n * (slice + 1)) / kTraceWarps);
   const float4* __restrict__ tab = sys.sub;
   const float4* __restrict__ mid_tab = sys.sub + (size_t)kSubStride * n;
-  auto& area = sm.wa[w];
+  auto& area = sm.wa[area0 + w];
 
   float2 px2[kPa], py2[kPa], ax2[kPa], ay2[kPa];
   float pxs[kSa], pys[kSa], axs[kSa], ays[kSa];
@@ -338,6 +338,26 @@ __global__ void __launch_bounds__(32 * kTraceWarps, MINB) trace_image_kernel(con
   trace_unit(sys, blockIdx.x, sm);
 }
 
+// Two-pass form: a CTA of kTraceWarps/2 warps sums the 8 slices in two passes (warp w takes
+// slices w and w + 4) into the same per-slice areas, then reduces them in slice order like the
+// one-CTA form, so its images are bitwise the same; the smaller CTA fits three per SM.
+constexpr int kHalfWarps = kTraceWarps / 2;
+__device__ __forceinline__ void trace_unit_2pass(const DevSystem& sys, int blk, TraceSmem<kTraceWarps>& sm) {
+  const UnitGeom g = unit_geom(sys, blk);
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) unit_partials<kTraceWarps>(sys, g, pass * kHalfWarps, sm, pass * kHalfWarps);
+  __syncthreads();
+  unit_finalize(sys, g, sm.I, 32 * kHalfWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; });
+  __syncthreads();
+  unit_bin_down(sys, g, sm.I, 32 * kHalfWarps);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(32 * kHalfWarps) trace_image_2pass_kernel(const __grid_constant__ DevSystem sys) {
+  __shared__ TraceSmem<kTraceWarps> sm;
+  trace_unit_2pass(sys, blockIdx.x, sm);
+}
+
 // Cluster form: CL CTAs of kTraceWarps/CL warps share one unit.  CTA r computes slices
 // [r*NWC, (r+1)*NWC) of the same split; the leader reads every CTA's partials through
 // distributed shared memory in slice order, so the image is bitwise that of the one-CTA form,
@@ -367,7 +387,7 @@ trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
 // Persistent form: CTAs pull unit tickets from the header's counter; ticket u belongs to the
 // system whose prefix range [unit_prefix[i], unit_prefix[i+1]) contains it.  Systems arrive
 // ordered by per-unit cost (largest first), so the queue hands out the longest units first.
-__global__ void __launch_bounds__(32 * kTraceWarps) trace_batch_kernel(BatchMeta* __restrict__ meta) {
+__global__ void __launch_bounds__(32 * kHalfWarps) trace_batch_kernel(BatchMeta* __restrict__ meta) {
   __shared__ TraceSmem<kTraceWarps> sm;
   __shared__ int s_ticket;
   const int n_sys = meta->n_sys;
@@ -385,7 +405,7 @@ __global__ void __launch_bounds__(32 * kTraceWarps) trace_batch_kernel(BatchMeta
       const int mid = (lo + hi) >> 1;
       if (unit_prefix[mid] <= u) lo = mid; else hi = mid;
     }
-    trace_unit(systems[lo], u - unit_prefix[lo], sm);
+    trace_unit_2pass(systems[lo], u - unit_prefix[lo], sm);
   }
 }
 
@@ -402,7 +422,7 @@ TraceShape choose_trace_shape(int nx, int ny, int s, int n_sub, int sm_count) {
 const char* trace_variant_name(int v) {
   switch (v) {
     case 0: return "cta8";
-    case 1: return "cta8_minblocks3";
+    case 1: return "cta4x2pass";
     case 2: return "cluster2x4";
     case 3: return "cluster4x2";
     case 4: return "cluster8x1";
@@ -413,7 +433,7 @@ const char* trace_variant_name(int v) {
 cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t st) {
   const int units = unit_count(sys.nx, sys.ny, sys.s);
   switch (variant) {
-    case 1: trace_image_kernel<3><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
+    case 1: trace_image_2pass_kernel<<<units, 32 * kHalfWarps, 0, st>>>(sys); break;
     case 2: trace_cluster_kernel<2><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
     case 3: trace_cluster_kernel<4><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
     case 4: trace_cluster_kernel<8><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
@@ -431,7 +451,7 @@ int trace_batch_grid(int sm_count) {
   static int blocks_per_sm = 0;
   if (!blocks_per_sm) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, trace_batch_kernel,
-                                                      32 * kTraceWarps, 0) != cudaSuccess || blocks_per_sm < 1) {
+                                                      32 * kHalfWarps, 0) != cudaSuccess || blocks_per_sm < 1) {
       cudaGetLastError();
       blocks_per_sm = 1;
     }
@@ -440,7 +460,7 @@ int trace_batch_grid(int sm_count) {
 }
 
 cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int grid, cudaStream_t st) {
-  trace_batch_kernel<<<grid, 32 * kTraceWarps, 0, st>>>(const_cast<BatchMeta*>(meta));
+  trace_batch_kernel<<<grid, 32 * kHalfWarps, 0, st>>>(const_cast<BatchMeta*>(meta));
   return cudaGetLastError();
 }
 

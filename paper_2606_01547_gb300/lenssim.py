@@ -29,7 +29,7 @@ LENS_TYPES = {"SIS": 0, "SIE": 1, "EPL": 2, "SHEAR": 3, "POINT_MASS": 4, "NFW": 
               "NFW_ELLIPSE_CSE": 12, "HERNQUIST_ELLIPSE_CSE": 13}
 LIGHT_TYPES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2, "SHAPELETS": 3}
 MAX_DEFLECTORS = 8
-TRACE_VARIANTS = ("cta8", "cta8_minblocks3", "cluster2x4", "cluster4x2", "cluster8x1")
+TRACE_VARIANTS = ("cta8", "cta4x2pass", "cluster2x4", "cluster4x2", "cluster8x1")
 _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
