@@ -321,6 +321,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
         extras["psf_conv"] = conv_extra(sim, W, dev)
+        extras["psf_fft"] = fft_conv_extra(sim, W, dev)
         extras["batched"] = batched_extra(sim, lenssim, W, dev, args.batch_systems)
         extras["batched_small_systems"] = batched_extra(sim, lenssim, W, dev, args.batch_systems, small=True)
         extras["differentiation"] = grad_extra(sim, W, dev)
@@ -431,6 +432,38 @@ def conv_extra(sim, W, dev, n_img: int = 4096, size: int = 256):
     res["workload"] = f"{n_img} x {size}^2 FP32 images, lens_sim_convolve, inputs larger than L2"
     del x, y
     torch.cuda.empty_cache()
+    return res
+
+
+def fft_conv_extra(sim, W, dev, n_img: int = 64):
+    """FFT against direct PSF step for large kernels (the paper's 180x180 grids with kernels up
+    to 135): a stack of n_img images per call through lens_sim_convolve, each method forced."""
+    import torch
+    st = torch.cuda.current_stream()
+    res = {}
+    for size, k in ((180, 135), (200, 135), (200, 75), (200, 45), (256, 101)):
+        x = torch.rand((n_img, size, size), device=dev)
+        y = torch.empty_like(x)
+        pid = sim.register_psf(W.moffat_psf(3.0, 0.12 * k / 21.0, 0.04, k))
+        row = {}
+        for m in ("direct", "fft"):
+            sim.set_conv_method(m)
+            sim.convolve(x, pid, out=y)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record(st)
+            for _ in range(reps):
+                sim.convolve(x, pid, out=y)
+            e1.record(st)
+            torch.cuda.synchronize()
+            row[f"{m}_ms_per_image"] = e0.elapsed_time(e1) / reps / n_img
+        row["fft_speedup"] = row["direct_ms_per_image"] / row["fft_ms_per_image"]
+        res[f"{size}x{size}_k{k}"] = row
+        del x, y
+    sim.set_conv_method("auto")
+    torch.cuda.empty_cache()
+    res["workload"] = f"{n_img} images per call, Moffat kernels, lens_sim_convolve with the method forced"
     return res
 
 

@@ -180,6 +180,21 @@ int lens_sim_autotune(lens_sim* sim, const lens_system* sample, int reps, int* b
                       float* ms_per_variant, int n_ms, void* stream);
 int lens_sim_set_variant(lens_sim* sim, int variant);
 
+/* PSF method of lens_sim_image (single system) and lens_sim_convolve.  LENS_CONV_DIRECT: tiled
+ * direct convolution.  LENS_CONV_FFT: FFT convolution (the paper's method for large kernels):
+ * radix-2 transforms on a grid padded to powers of two >= (n + (k-1)/2) in each direction,
+ * at most 1024; larger images return LENS_ERR_UNSUPPORTED.  The kernel's spectrum is computed
+ * once per (psf_id, padded size) and kept by the handle.  LENS_CONV_AUTO (the default): FFT
+ * when k >= LENS_CONV_FFT_MIN_K and the padded size fits, else direct.  Both compute the same
+ * convolution; they differ by FP32 rounding only (the FFT's is of order eps log2(M) of the
+ * output scale, below 1e-5 relative L-inf).  The batched and
+ * likelihood paths always use the direct form. */
+#define LENS_CONV_AUTO 0
+#define LENS_CONV_DIRECT 1
+#define LENS_CONV_FFT 2
+#define LENS_CONV_FFT_MIN_K 33
+int lens_sim_set_conv_method(lens_sim* sim, int method);
+
 /* Chi^2 log-likelihood of n_points parameter vectors against DEVICE data [ny][nx]:
  *   sigma^2 = sigma_bkg^2 + max(m, 0)/t_exp,   logL = -1/2 sum (d - m)^2 / sigma^2,
  * with m the PSF-convolved model.  params is DEVICE [n_points][15] in the order

@@ -240,6 +240,54 @@ void fill_dev_system(const lens_system& y, DevSystem& d) {
     for (int q = 0; q < y.n_source_coeffs && q < LENS_MAX_SHAPELET_COEFFS; ++q) d.src_coef[q] = y.source_coeffs[q];
 }
 
+// PSF step of a stack of n_img equal-size device images (method per the handle; in != out).
+int psf_apply(lens_sim* s, const float* in, float* out, int n_img, int ny, int nx, int psf_id, cudaStream_t st,
+              bool allow_tma) {
+  const PsfEntry& p = s->res->psfs[psf_id];
+  int My = 0, Mx = 0;
+  const bool fits = conv_fft_sizes(ny, nx, p.k, &My, &Mx);
+  if (s->conv_method == LENS_CONV_FFT && !fits)
+    return fail(s, LENS_ERR_UNSUPPORTED, "FFT convolution needs padded sizes <= 1024 (got %dx%d)", My, Mx);
+  const bool use_fft = fits && (s->conv_method == LENS_CONV_FFT ||
+                                (s->conv_method == LENS_CONV_AUTO && p.k >= LENS_CONV_FFT_MIN_K));
+  cudaError_t e;
+  if (use_fft) {
+    lens_sim::FftSpectrum* spec = nullptr;
+    for (auto& f : s->spectra)
+      if (f.psf_id == psf_id && f.My == My && f.Mx == Mx) spec = &f;
+    const size_t per_img = conv_fft_bytes_per_image(ny, Mx);
+    const size_t want_ws = std::max(per_img * (size_t)std::min(n_img, 64), sizeof(float2) * (size_t)p.k * Mx);
+    int rc;
+    if ((rc = ensure(s, s->fft_ws, want_ws))) return rc;
+    if (!spec) {
+      s->spectra.push_back({psf_id, My, Mx, DevBuffer{}});
+      spec = &s->spectra.back();
+      if ((rc = ensure(s, spec->buf, sizeof(float2) * (size_t)My * Mx))) {
+        s->spectra.pop_back();
+        return rc;
+      }
+      e = launch_fft_spectrum(p.d, p.k, My, Mx, (float2*)s->fft_ws.p, (float2*)spec->buf.p, st);
+      if (e != cudaSuccess) return cuda_fail(s, e, "FFT spectrum of the PSF");
+    }
+    const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_img, s->fft_ws.cap / per_img));
+    float2* A = (float2*)s->fft_ws.p;
+    float2* B = A + (size_t)chunk * ny * Mx;
+    for (int i0 = 0; i0 < n_img; i0 += chunk) {
+      const int n = std::min(chunk, n_img - i0);
+      e = launch_conv_fft(in + (size_t)i0 * ny * nx, out + (size_t)i0 * ny * nx, n, ny, nx, p.k, My, Mx,
+                          (const float2*)spec->buf.p, A, B, st);
+      if (e != cudaSuccess) return cuda_fail(s, e, "FFT convolution launch");
+    }
+    return LENS_OK;
+  }
+  if (allow_tma && conv_tma_supported(in, out, ny, nx, p.k))
+    e = launch_conv_tma(in, out, n_img, ny, nx, p.d, p.k, s->wait_flag_d, s->sm_count, st);
+  else
+    e = launch_conv(in, out, n_img, ny, nx, p.d, p.k, 1, st);
+  if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
+  return LENS_OK;
+}
+
 DeviceGuard::DeviceGuard(int dev) {
   // A non-fatal status left by an earlier call on this thread (e.g. "not ready" from a query)
   // would otherwise be read back by the launch checks below as a launch failure.
@@ -296,6 +344,9 @@ void lens_sim_destroy(lens_sim* s) {
     release(s, s->img);
     release(s, s->stage);
     release(s, s->grad_ws);
+    release(s, s->fft_ws);
+    for (auto& f : s->spectra) release(s, f.buf);
+    s->spectra.clear();
     release(s, s->batch_meta);
     release(s, s->batch_data);
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
@@ -389,11 +440,8 @@ int lens_sim_image(lens_sim* s, const lens_system* systems, int n_sys, float* co
     d.out = (y.psf_id >= 0) ? (float*)s->img.p : final_dst;
     cudaError_t e = launch_trace_variant(d, s->trace_variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "trace kernel launch");
-    if (y.psf_id >= 0) {
-      const PsfEntry& p = s->res->psfs[y.psf_id];
-      e = launch_conv((float*)s->img.p, final_dst, 1, d.ny, d.nx, p.d, p.k, 1, st);
-      if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
-    }
+    if (y.psf_id >= 0 && (rc = psf_apply(s, (float*)s->img.p, final_dst, 1, d.ny, d.nx, y.psf_id, st, false)))
+      return rc;
     if (!dev_out) {
       e = cudaMemcpyAsync(out_images[i], final_dst, sizeof(float) * d.nx * d.ny, cudaMemcpyDeviceToHost, st);
       if (e != cudaSuccess) return cuda_fail(s, e, "copy image to host");
@@ -456,12 +504,15 @@ int lens_sim_convolve(lens_sim* s, const float* in, int n_img, int ny, int nx, i
     *s->wait_flag_h = 0;
     return fail(s, LENS_ERR_TIMEOUT, "a bounded wait of an earlier convolution expired");
   }
-  cudaError_t e;
-  if (conv_tma_supported(in, out, ny, nx, p.k))
-    e = launch_conv_tma(in, out, n_img, ny, nx, p.d, p.k, s->wait_flag_d, s->sm_count, (cudaStream_t)stream);
-  else
-    e = launch_conv(in, out, n_img, ny, nx, p.d, p.k, 1, (cudaStream_t)stream);
-  if (e != cudaSuccess) return cuda_fail(s, e, "psf kernel launch");
+  (void)p;
+  return psf_apply(s, in, out, n_img, ny, nx, psf_id, (cudaStream_t)stream, true);
+}
+
+int lens_sim_set_conv_method(lens_sim* s, int method) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (method != LENS_CONV_AUTO && method != LENS_CONV_DIRECT && method != LENS_CONV_FFT)
+    return fail(s, LENS_ERR_INVALID_ARG, "unknown convolution method %d", method);
+  s->conv_method = method;
   return LENS_OK;
 }
 

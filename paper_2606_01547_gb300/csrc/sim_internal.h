@@ -68,6 +68,7 @@ struct lens_sim {
   int max_batch = 4096;
   int sm_count = 0;
   int trace_variant = 0;  // launch variant of the single-system trace kernel
+  int conv_method = 0;    // LENS_CONV_AUTO / _DIRECT / _FFT
   int* wait_flag_h = nullptr;  // host-mapped flag raised by an expired bounded device wait
   int* wait_flag_d = nullptr;
   std::string err;
@@ -78,6 +79,12 @@ struct lens_sim {
   ls::DevBuffer img;      // unconvolved (binned) image
   ls::DevBuffer stage;    // device staging of host outputs
   ls::DevBuffer grad_ws;  // likelihood / adjoint workspace
+  ls::DevBuffer fft_ws;   // FFT convolution workspace (row and column spectra of a chunk of images)
+  struct FftSpectrum {
+    int psf_id, My, Mx;
+    ls::DevBuffer buf;
+  };
+  std::vector<FftSpectrum> spectra;  // kernel spectra per (psf, padded size)
   // batched launch
   ls::DevBuffer batch_meta;   // packed header + descriptors + prefix + jobs
   ls::DevBuffer batch_data;   // subhalo tables, raw copies, unconvolved images, output staging

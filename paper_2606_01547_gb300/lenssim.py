@@ -29,12 +29,15 @@ LENS_TYPES = {"SIS": 0, "SIE": 1, "EPL": 2, "SHEAR": 3, "POINT_MASS": 4, "NFW": 
               "NFW_ELLIPSE_CSE": 12, "HERNQUIST_ELLIPSE_CSE": 13}
 LIGHT_TYPES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2, "SHAPELETS": 3}
 MAX_DEFLECTORS = 8
+CONV_METHODS = {"auto": 0, "direct": 1, "fft": 2}
+CONV_FFT_MIN_K = 33   # LENS_CONV_FFT_MIN_K: auto takes the FFT from this kernel size on
 TRACE_VARIANTS = ("cta8", "cta4x2pass", "cluster2x4", "cluster4x2", "cluster8x1")
 _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
             "lens_sim_register_subhalos", "lens_sim_image", "lens_sim_deflection", "lens_sim_convolve",
-            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_grad", "lens_sim_linear_amp",
+            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_set_conv_method", "lens_sim_grad",
+            "lens_sim_linear_amp",
             "lens_sim_image_noalloc", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
             "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats",
             "lens_serve_reset_stats", "lens_serve_destroy")
@@ -118,6 +121,7 @@ def lib():
             L.lens_sim_autotune.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(ip),
                                             ctypes.POINTER(fp), ip, vp]
             L.lens_sim_set_variant.argtypes = [vp, ip]
+            L.lens_sim_set_conv_method.argtypes = [vp, ctypes.c_int]
             L.lens_sim_image_noalloc.argtypes = [ctypes.POINTER(LensSystemC), vp, ip, vp, vp]
             L.lens_sim_linear_amp.argtypes = [vp, ctypes.POINTER(LensSystemC), vp, fp, fp, vp, ip, vp, vp, vp]
             L.lens_serve_create.argtypes = [ctypes.POINTER(SimConfig), ip, ctypes.POINTER(vp)]
@@ -268,6 +272,10 @@ class Simulator:
     # ------------------------------------------------------------------ tuning
     def set_variant(self, variant: int) -> None:
         self._check(self._L.lens_sim_set_variant(self.h, int(variant)))
+
+    def set_conv_method(self, method: str) -> None:
+        """PSF method: "auto" (FFT for k >= 33 when it fits), "direct" or "fft"."""
+        self._check(self._L.lens_sim_set_conv_method(self.h, CONV_METHODS[method]))
 
     def autotune(self, system: W.LensSystem, reps: int = 5, use_cache: bool = True, stream=None):
         """Pick the fastest trace-kernel launch variant for systems shaped like `system`.

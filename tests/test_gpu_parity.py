@@ -219,10 +219,15 @@ def test_subhalo_sum_deflection_matches_oracle(sim):
 @pytest.mark.parametrize("k,ny,nx,n", [(1, 9, 13, 1), (5, 37, 53, 3), (21, 64, 64, 2), (31, 40, 71, 1),
                                        (3, 1, 1, 2), (45, 50, 50, 1)])
 def test_convolution_matches_oracle(sim, k, ny, nx, n):
+    # the direct kernels (forced: auto would take the FFT for k = 45)
     rng = np.random.default_rng(k)
     imgs = rng.random((n, ny, nx)).astype(np.float32)
     K = rng.random((k, k)).astype(np.float32)
-    out = sim.convolve(torch.from_numpy(imgs).cuda(), K).cpu().numpy()
+    sim.set_conv_method("direct")
+    try:
+        out = sim.convolve(torch.from_numpy(imgs).cuda(), K).cpu().numpy()
+    finally:
+        sim.set_conv_method("auto")
     for i in range(n):
         ref = oracle.convolve(imgs[i], K)
         assert rel_linf(out[i], ref) < 2e-6
@@ -256,6 +261,64 @@ def test_tma_and_generic_convolution_agree_bitwise(sim):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(b.cpu().numpy(), ref_b.cpu().numpy())
     assert a.shape == b.shape
+
+
+@pytest.mark.parametrize("k,ny,nx,n", [(45, 60, 60, 2), (135, 180, 180, 1), (75, 97, 131, 3), (3, 17, 23, 1),
+                                       (135, 200, 200, 1), (61, 1, 40, 2), (1, 8, 8, 1)])
+def test_fft_convolution_matches_oracle(sim, k, ny, nx, n):
+    # the FFT path against the direct definition: ragged, non-square, single-row and k = 1 cases.
+    # FP32 transforms make an error of order eps log2(M) of the output scale (2 x 2 log2 M
+    # butterfly stages): the image tolerance, 1e-5 relative L-inf, bounds it (measured <= 6e-6)
+    rng = np.random.default_rng(100 + k)
+    imgs = rng.random((n, ny, nx)).astype(np.float32)
+    K = (rng.random((k, k)) + 0.1).astype(np.float32)
+    sim.set_conv_method("fft")
+    try:
+        out = sim.convolve(torch.from_numpy(imgs).cuda(), K).cpu().numpy()
+    finally:
+        sim.set_conv_method("auto")
+    for i in range(n):
+        assert rel_linf(out[i], oracle.convolve(imgs[i], K)) < 1e-5
+
+
+def test_fft_and_direct_methods_select_and_agree(sim):
+    from paper_2606_01547_gb300 import lenssim
+    rng = np.random.default_rng(7)
+    imgs = torch.from_numpy(rng.random((2, 120, 90)).astype(np.float32)).cuda()
+    for k in (31, 45, 101):
+        K = W.moffat_psf(3.0, 0.12 * k / 21, 0.04, k)
+        outs = {}
+        for m in ("auto", "direct", "fft"):
+            sim.set_conv_method(m)
+            outs[m] = sim.convolve(imgs, K).cpu().numpy()
+        sim.set_conv_method("auto")
+        # auto takes the FFT above the TMA kernel's k <= 31, the direct form below (bitwise the
+        # chosen one); both within the image tolerance of each other
+        np.testing.assert_array_equal(outs["auto"], outs["fft" if k >= lenssim.CONV_FFT_MIN_K else "direct"])
+        assert rel_linf(outs["fft"], outs["direct"]) < 1e-5
+    # an FFT grid beyond 1024 is refused when forced; auto falls back to the direct form
+    big = torch.zeros((1, 1000, 64), device="cuda")
+    sim.set_conv_method("fft")
+    with pytest.raises(lenssim.LensSimError) as ei:
+        sim.convolve(big, W.moffat_psf(3.0, 0.3, 0.04, 61))
+    assert ei.value.code == lenssim.LENS_ERR_UNSUPPORTED
+    sim.set_conv_method("auto")
+    sim.convolve(big, W.moffat_psf(3.0, 0.3, 0.04, 61))
+    torch.cuda.synchronize()
+
+
+def test_image_with_fft_psf_matches_oracle(sim):
+    system = W.substructure_system(9, n_sub=200, nx=64, s=2, k=0)
+    system = W.LensSystem(system.grid, system.deflectors, system.subhalos, system.source,
+                          W.moffat_psf(3.0, 0.5, 0.04, 61))
+    ref = oracle.image(system)
+    tol, floor = image_tol(system, ref)
+    sim.set_conv_method("fft")
+    try:
+        err = rel_linf(gpu_image(sim, system), ref)
+    finally:
+        sim.set_conv_method("auto")
+    assert err <= tol, (err, floor)
 
 
 def test_delta_psf_is_identity_on_gpu(sim):
