@@ -252,38 +252,38 @@ __device__ __forceinline__ float tnfw_g_far(float x2, float tau, float t2, float
 
 
 // ---------------------------------------------------------------------------- subhalo table
-// Far field (x >= 4 max(tau, 1)): G(x) is analytic in y = 1/x for |y| < min(1, 1/tau), and
+// Far field (x >= 5 max(tau, 1)): G(x) is analytic in y = 1/x for |y| < min(1, 1/tau), and
 //   G = sum_k c_k y^k,  c_0 = C - (tau^2 + 1),  c_1 = 0,
 //   c_(2n+1) = pi [ (tau^2-1) a_n / 2 + a_(n+1) - s_(n+1) tau^(2n+2) ],
 //   c_(2n)   = -(tau^2-1) b_(n-1) - 2 b_n - (tau^2-1) tau^(2n) sum_(i+j=n) s_i h_j,
 // from the Taylor series of (1-y^2)^(-1/2) = sum a_j y^2j, asin(y)/sqrt(1-y^2) = sum b_j y^(2j+1),
 // sqrt(1+u) = sum s_j u^j and asinh(z) = sum h_j z^(2j+1) substituted into the defining formula
-// (the 1/y terms cancel exactly).  Truncated after c_10 the relative error is below 1e-7 for
-// tau >= 0.6 (below 1e-8 for tau >= 2) on that range, and Horner in FP32 is well conditioned
-// (sum |c_k y^k| / |G| < 1.1).
-constexpr int kFarTerms = 10;
+// (the 1/y terms cancel exactly).  Truncated after c_8 and used from x >= kFarRadius max(tau, 1)
+// = 5 max(tau, 1) on, the relative error is below 2.7e-7 for all tau, and Horner in FP32 is well
+// conditioned (sum |c_k y^k| / |G| < 1.1).
+constexpr int kFarTerms = 8;
+constexpr float kFarRadius = 5.f;  // the series' range: r >= kFarRadius max(tau, 1) Rs
 constexpr int kSubStride = 8;   // float4 per subhalo record (staged through shared memory)
 constexpr int kMidTerms = 12;   // coefficients of the annulus polynomial
 constexpr int kMidStride = 3;   // float4 per subhalo in the annulus block
 constexpr int kTableStride = kSubStride + kMidStride;  // float4 per subhalo in a whole table
-// Largest tau whose annulus 4 <= x < 4 tau the 12-term polynomial covers to 1e-7 (relative, in
-// FP64 arithmetic); beyond it the annulus takes the closed form.
-constexpr float kMidTauMax = 9.5f;
+// Largest tau whose annulus 4 <= x < 5 max(tau, 1) the 12-term polynomial covers to 1e-7
+// (relative, in FP64 arithmetic); beyond it the annulus takes the closed form.
+constexpr float kMidTauMax = 9.f;
 
 // A subhalo table of n subhalos is n records of kSubStride float4 followed by n annulus blocks of
 // kMidStride float4.  The record (128 B) is laid out for packed FP32x2 arithmetic (two samples
 // per instruction): centres negated and every series coefficient stored as a duplicated pair,
-//   t0 = (-cx, -cx, -cy, -cy),           t1 = (r_far^2 = 16 max(tau,1)^2 Rs^2, 1/Rs^2, tau, A),
+//   t0 = (-cx, -cx, -cy, -cy),           t1 = (r_far^2 = 25 max(tau,1)^2 Rs^2, 1/Rs^2, tau, A),
 //   t2 = (d_0, d_0, d_2, d_2),  t3 = (d_3, d_3, d_4, d_4),  t4 = (d_5, d_5, d_6, d_6),
-//   t5 = (d_7, d_7, d_8, d_8),  t6 = (d_9, d_9, d_10, d_10), t7 = (a_t, b_t, r_in^2, C),
+//   t5 = (d_7, d_7, d_8, d_8),  t6 = (a_t, b_t, r_in^2, C),  t7 = 0,
 // with A = alpha_Rs tau^2 / ((1 - ln 2) Rs (tau^2+1)^2), so that alpha = A g(x^2) (dx, dy), and
 // d_k = A c_k Rs^(k+2): the series then runs in u = 1/r with no per-pair scaling by 1/Rs^2.
 // C = tau pi + (tau^2-1) ln tau.  The annulus block holds the 12 coefficients e_0..e_11 of
 //   A g = u^2 sum_j e_j t^j,  t = a_t u + b_t,
 // the polynomial in t in [-1, 1] that interpolates A Rs^2 G at the 12 Chebyshev nodes of
-// y = Rs u in [1/(4 tau), 1/4], i.e. on the annulus r_in = 4 Rs <= r < r_far.  When the annulus
-// is empty (tau <= 1) or too wide for 12 terms (tau > kMidTauMax), r_in^2 = r_far^2 and the
-// block is zero.
+// y = Rs u in [1/(5 max(tau, 1)), 1/4], i.e. on the annulus r_in = 4 Rs <= r < r_far.  When the
+// annulus is too wide for 12 terms (tau > kMidTauMax), r_in^2 = r_far^2 and the block is zero.
 __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, float alphaRs, float rt, float4* t) {
   const float tau = rt / Rs;
   const float t2 = tau * tau, t2m1 = t2 - 1.f, t2p1 = t2 + 1.f;
@@ -315,10 +315,10 @@ __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, flo
     rp *= Rs;
   }
   const float tm = fmaxf(tau, 1.f);
-  const float r_far2 = 16.f * tm * tm * Rs * Rs;
-  const bool annulus = tau > 1.f && tau <= kMidTauMax;
-  // t = (2y - (ylo + yhi)) / (yhi - ylo) with y = Rs u, ylo = 1/(4 tau), yhi = 1/4
-  const float ylo = 0.25f / tau, yhi = 0.25f;
+  const float r_far2 = kFarRadius * kFarRadius * tm * tm * Rs * Rs;
+  const bool annulus = tau <= kMidTauMax;
+  // t = (2y - (ylo + yhi)) / (yhi - ylo) with y = Rs u, ylo = 1/(5 max(tau, 1)), yhi = 1/4
+  const float ylo = 1.f / (kFarRadius * tm), yhi = 0.25f;
   const float at = annulus ? 2.f * Rs / (yhi - ylo) : 0.f;
   const float bt = annulus ? -(ylo + yhi) / (yhi - ylo) : 0.f;
   t[0] = make_float4(-cx, -cx, -cy, -cy);
@@ -327,12 +327,12 @@ __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, flo
   t[3] = make_float4(d[3], d[3], d[4], d[4]);
   t[4] = make_float4(d[5], d[5], d[6], d[6]);
   t[5] = make_float4(d[7], d[7], d[8], d[8]);
-  t[6] = make_float4(d[9], d[9], d[10], d[10]);
-  t[7] = make_float4(at, bt, annulus ? 16.f * Rs * Rs : r_far2, C);
+  t[6] = make_float4(at, bt, annulus ? 16.f * Rs * Rs : r_far2, C);
+  t[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Annulus block of a subhalo from its record t (Rs = its scale radius): G at the 12 Chebyshev
-// nodes of y in [1/(4 tau), 1/4] by the x >= 4 closed form, Chebyshev coefficients by the
+// nodes of y in [1/(5 max(tau, 1)), 1/4] by the x >= 4 closed form, Chebyshev coefficients by the
 // discrete cosine sum, then the monomial coefficients in t (T_j expanded by its recurrence,
 // whose integer coefficients are exact in FP32; the monomial form's FP32 condition number on
 // [-1, 1] is below 2 for tau <= kMidTauMax), scaled by A Rs^2.
@@ -340,10 +340,10 @@ __device__ __forceinline__ void tnfw_mid_constants(float Rs, const float4* t, fl
   float e[kMidTerms];
 #pragma unroll
   for (int j = 0; j < kMidTerms; ++j) e[j] = 0.f;
-  if (t[7].z < t[1].x) {
-    const float tau = t[1].z, A = t[1].w, C = t[7].w;
+  if (t[6].z < t[1].x) {
+    const float tau = t[1].z, A = t[1].w, C = t[6].w;
     const float t2 = tau * tau, t2m1 = t2 - 1.f;
-    const float ylo = 0.25f / tau, yhi = 0.25f;
+    const float ylo = 1.f / (kFarRadius * fmaxf(tau, 1.f)), yhi = 0.25f;
     float ch[kMidTerms];
 #pragma unroll
     for (int j = 0; j < kMidTerms; ++j) ch[j] = 0.f;
@@ -402,12 +402,10 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
   return r;
 }
 
-// Far-field series: A g = u^2 (d_0 + u^2 (d_2 + d_3 u + ... + d_10 u^8)), u = 1/r, u2 = u^2,
+// Far-field series: A g = u^2 (d_0 + u^2 (d_2 + d_3 u + ... + d_8 u^6)), u = 1/r, u2 = u^2,
 // the same as A y^2 sum_k c_k y^k with y = Rs/r.  Scalar form (one sample).
 __device__ __forceinline__ float tnfw_series_u(float u, float u2, const float4* t) {
-  float p = fmaf(t[6].z, u, t[6].x);
-  p = fmaf(p, u, t[5].z);
-  p = fmaf(p, u, t[5].x);
+  float p = fmaf(t[5].z, u, t[5].x);
   p = fmaf(p, u, t[4].z);
   p = fmaf(p, u, t[4].x);
   p = fmaf(p, u, t[3].z);
@@ -425,9 +423,7 @@ __device__ __forceinline__ float tnfw_series(float r2, const float4* t) {
 // Packed forms (two samples per instruction): element-wise the same operations, hence the same
 // rounding, as the scalar forms.
 __device__ __forceinline__ float2 tnfw_series2_u(float2 u, float2 u2, const float4* t) {
-  float2 p = __ffma2_rn(make_float2(t[6].z, t[6].w), u, make_float2(t[6].x, t[6].y));
-  p = __ffma2_rn(p, u, make_float2(t[5].z, t[5].w));
-  p = __ffma2_rn(p, u, make_float2(t[5].x, t[5].y));
+  float2 p = __ffma2_rn(make_float2(t[5].z, t[5].w), u, make_float2(t[5].x, t[5].y));
   p = __ffma2_rn(p, u, make_float2(t[4].z, t[4].w));
   p = __ffma2_rn(p, u, make_float2(t[4].x, t[4].y));
   p = __ffma2_rn(p, u, make_float2(t[3].z, t[3].w));
@@ -444,7 +440,7 @@ __device__ __forceinline__ float2 tnfw_series2(float2 r2, const float4* t) {
 
 // Annulus polynomial: A g = u^2 sum_j e_j t^j, t = a_t u + b_t (Horner in t).
 __device__ __forceinline__ float tnfw_mid_u(float u, float u2, const float4* t, const float4* m) {
-  const float x = fmaf(t[7].x, u, t[7].y);
+  const float x = fmaf(t[6].x, u, t[6].y);
   float p = fmaf(m[2].w, x, m[2].z);
   p = fmaf(p, x, m[2].y);
   p = fmaf(p, x, m[2].x);
@@ -461,7 +457,7 @@ __device__ __forceinline__ float tnfw_mid_u(float u, float u2, const float4* t, 
 
 __device__ __forceinline__ float2 tnfw_mid2_u(float2 u, float2 u2, const float4* t, const float4* m) {
   auto d = [](float v) { return make_float2(v, v); };
-  const float2 x = __ffma2_rn(d(t[7].x), u, d(t[7].y));
+  const float2 x = __ffma2_rn(d(t[6].x), u, d(t[6].y));
   float2 p = __ffma2_rn(d(m[2].w), x, d(m[2].z));
   p = __ffma2_rn(p, x, d(m[2].y));
   p = __ffma2_rn(p, x, d(m[2].x));
@@ -488,11 +484,11 @@ static __device__ __noinline__ float tnfw_g_inner(float x2, float tau, float A, 
 // polynomial on [r_in, r_far) when the annulus block m is given, the closed forms inside.
 __device__ __forceinline__ float tnfw_ag(float r2, const float4* t, const float4* m) {
   if (r2 >= t[1].x) return tnfw_series(r2, t);
-  if (m != nullptr && r2 >= t[7].z) {
+  if (m != nullptr && r2 >= t[6].z) {
     const float u = rsqrt_ftz(r2);
     return tnfw_mid_u(u, u * u, t, m);
   }
-  return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[7].w);
+  return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[6].w);
 }
 
 // One point-subhalo pair accumulated into (ax, ay); t is the subhalo's record, m its annulus

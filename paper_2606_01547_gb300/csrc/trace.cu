@@ -205,11 +205,11 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     // inside r_in call the closed forms
     auto near_pairs = [&](const float4* t, const float4* m) {
       const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
-      const float r_far2 = t[1].x, r_in2 = t[7].z;
+      const float r_far2 = t[1].x, r_in2 = t[6].z;
       auto pick = [&](float r2, float gs, float gm) {
         if (r2 >= r_far2) return gs;
         if (r2 >= r_in2) return gm;
-        return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[7].w);
+        return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[6].w);
       };
 #pragma unroll
       for (int i = 0; i < kP; ++i) {
@@ -258,7 +258,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
 #pragma unroll
           for (int f = 0; f < kFuseSubhalos; ++f)
 #pragma unroll
-            for (int c = 0; c < kSubStride - 1; ++c) tg[f][c] = area.sub[q + f][c];
+            for (int c = 0; c < 6; ++c) tg[f][c] = area.sub[q + f][c];  // t0..t5: centre and series
 #pragma unroll
           for (int f = 0; f < kFuseSubhalos; ++f) far_pairs(tg[f]);
         } else {

@@ -40,37 +40,48 @@ def lbfgs_fit(sim: lenssim.Simulator, system: W.LensSystem, data: torch.Tensor, 
     The n problems are independent; their negative log-likelihoods are summed so that one
     batched lens_sim_grad call serves all of them at every function evaluation.  L-BFGS runs on
     parameters divided by `scale` (default: the prior widths), which evens out the very different
-    sensitivities of the 15 parameters, and is restarted with a fresh history (up to `restarts`
-    times, `iters` iterations each) until a restart no longer improves the summed likelihood."""
+    sensitivities of the 15 parameters, and is restarted with a fresh history from the best point
+    seen (up to `restarts` times, `iters` iterations each) until a restart no longer improves the
+    summed likelihood.  Points outside the profiles' domain (non-finite likelihood) count as a
+    very large loss, so the line search backs off from them; the best finite point is returned."""
     sc = torch.tensor(np.asarray(PRIOR_HI - PRIOR_LO if scale is None else scale, np.float32), device=data.device)
     Z = (torch.tensor(np.asarray(starts, np.float32), device=data.device) / sc).requires_grad_(True)
     history = []
     evals = [0]
+    best = {"total": -float("inf"), "P": (Z * sc).detach().clone()}
 
     def closure_for(opt):
         def closure():
             opt.zero_grad()
             L = lenssim.LensLogLike.apply(Z * sc, sim, system, data, sigma_bkg, t_exp, subhalo_table)
             evals[0] += Z.shape[0]
+            if not bool(torch.isfinite(L).all()):
+                # outside the profiles' domain (|e| >= 1, n <= 0, ...): a large loss with zero
+                # gradient, so that the line search backs off
+                loss = (Z * 0.0).sum() + 1e30
+                loss.backward()
+                return loss
+            total = float(L.sum())
+            if total > best["total"]:
+                best["total"] = total
+                best["P"] = (Z * sc).detach().clone()
             loss = -L.sum()
             loss.backward()
             history.append(float(L.max()))
             return loss
         return closure
 
-    best = -float("inf")
+    prev = -float("inf")
     for _ in range(max(1, restarts)):
         opt = torch.optim.LBFGS([Z], lr=lr, max_iter=iters, history_size=20, line_search_fn="strong_wolfe",
                                 tolerance_grad=1e-12, tolerance_change=1e-14)
         opt.step(closure_for(opt))
         with torch.no_grad():
-            L = sim.grad(system, data, sigma_bkg, t_exp, (Z * sc).detach(), want_grad=False,
-                         subhalo_table=subhalo_table)
-        total = float(L.sum())
-        if total <= best + 1e-7 * abs(best):
+            Z.copy_(best["P"] / sc)   # restart from the best point seen
+        if best["total"] <= prev + 1e-7 * abs(prev):
             break
-        best = total
-    P = (Z * sc).detach()
+        prev = best["total"]
+    P = best["P"]
     with torch.no_grad():
         L = sim.grad(system, data, sigma_bkg, t_exp, P, want_grad=False, subhalo_table=subhalo_table)
     return FitResult(P.cpu().numpy(), L.cpu().numpy(), history, evals[0] + P.shape[0])
