@@ -39,9 +39,9 @@ WORKLOAD = ("substructure image: 200x200 grid at 0.04\", supersampling 3 (360,00
 N_SYSTEMS = 8            # distinct seeded systems cycled through the steps
 # Algorithmic work of one point-subhalo pair, frozen from the far-field series pair formula that
 # almost every pair takes: dx, dy (2 FADD); r^2 = dx^2 + dy^2 (FMUL, FFMA); u = rsqrt(r^2)
-# (1 MUFU); u^2 (FMUL); Horner over the 8 coefficients (7 FFMA); g = p u^2 (FMUL);
-# alpha += g (dx, dy) (2 FFMA)  ->  10 FFMA + 3 FMUL + 2 FADD = 25 FP32 flops (FMA = 2), 1 MUFU.
-FLOPS_PER_PAIR = 25
+# (1 MUFU); u^2 (FMUL); Horner over the 6 coefficients (5 FFMA); g = p u^2 (FMUL);
+# alpha += g (dx, dy) (2 FFMA)  ->  8 FFMA + 3 FMUL + 2 FADD = 21 FP32 flops (FMA = 2), 1 MUFU.
+FLOPS_PER_PAIR = 21
 KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh",
                   "paper_2606_01547_gb300/csrc/kernels.h")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trace_kernel_substructure_200x200_traffic.txt")

@@ -252,37 +252,38 @@ __device__ __forceinline__ float tnfw_g_far(float x2, float tau, float t2, float
 
 
 // ---------------------------------------------------------------------------- subhalo table
-// Far field (x >= 5 max(tau, 1)): G(x) is analytic in y = 1/x for |y| < min(1, 1/tau), and
+// Far field (x >= 7 max(tau, 1)): G(x) is analytic in y = 1/x for |y| < min(1, 1/tau), and
 //   G = sum_k c_k y^k,  c_0 = C - (tau^2 + 1),  c_1 = 0,
 //   c_(2n+1) = pi [ (tau^2-1) a_n / 2 + a_(n+1) - s_(n+1) tau^(2n+2) ],
 //   c_(2n)   = -(tau^2-1) b_(n-1) - 2 b_n - (tau^2-1) tau^(2n) sum_(i+j=n) s_i h_j,
 // from the Taylor series of (1-y^2)^(-1/2) = sum a_j y^2j, asin(y)/sqrt(1-y^2) = sum b_j y^(2j+1),
 // sqrt(1+u) = sum s_j u^j and asinh(z) = sum h_j z^(2j+1) substituted into the defining formula
-// (the 1/y terms cancel exactly).  Truncated after c_8 and used from x >= kFarRadius max(tau, 1)
-// = 5 max(tau, 1) on, the relative error is below 2.7e-7 for all tau, and Horner in FP32 is well
-// conditioned (sum |c_k y^k| / |G| < 1.1).
-constexpr int kFarTerms = 8;
-constexpr float kFarRadius = 5.f;  // the series' range: r >= kFarRadius max(tau, 1) Rs
+// (the 1/y terms cancel exactly).  Truncated after c_6 and used from x >= kFarRadius max(tau, 1)
+// = 7 max(tau, 1) on, the relative error is below 1e-6 for all tau (FP32 closed forms reach
+// 3e-6), and Horner in FP32 is well conditioned (sum |c_k y^k| / |G| < 1.1).
+constexpr int kFarTerms = 6;
+constexpr float kFarRadius = 7.f;  // the series' range: r >= kFarRadius max(tau, 1) Rs
+static_assert(kFarTerms >= 3 && kFarTerms <= 8, "the record holds d_0, d_2 .. d_8 in t2..t5");
 constexpr int kSubStride = 8;   // float4 per subhalo record (staged through shared memory)
 constexpr int kMidTerms = 12;   // coefficients of the annulus polynomial
 constexpr int kMidStride = 3;   // float4 per subhalo in the annulus block
 constexpr int kTableStride = kSubStride + kMidStride;  // float4 per subhalo in a whole table
-// Largest tau whose annulus 4 <= x < 5 max(tau, 1) the 12-term polynomial covers to 1e-7
+// Largest tau whose annulus 4 <= x < 7 max(tau, 1) the 12-term polynomial covers to 1e-7
 // (relative, in FP64 arithmetic); beyond it the annulus takes the closed form.
-constexpr float kMidTauMax = 9.f;
+constexpr float kMidTauMax = 8.5f;
 
 // A subhalo table of n subhalos is n records of kSubStride float4 followed by n annulus blocks of
 // kMidStride float4.  The record (128 B) is laid out for packed FP32x2 arithmetic (two samples
 // per instruction): centres negated and every series coefficient stored as a duplicated pair,
-//   t0 = (-cx, -cx, -cy, -cy),           t1 = (r_far^2 = 25 max(tau,1)^2 Rs^2, 1/Rs^2, tau, A),
+//   t0 = (-cx, -cx, -cy, -cy),           t1 = (r_far^2 = 49 max(tau,1)^2 Rs^2, 1/Rs^2, tau, A),
 //   t2 = (d_0, d_0, d_2, d_2),  t3 = (d_3, d_3, d_4, d_4),  t4 = (d_5, d_5, d_6, d_6),
-//   t5 = (d_7, d_7, d_8, d_8),  t6 = (a_t, b_t, r_in^2, C),  t7 = 0,
+//   t5 = 0 (room for d_7, d_8),  t6 = (a_t, b_t, r_in^2, C),  t7 = 0,
 // with A = alpha_Rs tau^2 / ((1 - ln 2) Rs (tau^2+1)^2), so that alpha = A g(x^2) (dx, dy), and
 // d_k = A c_k Rs^(k+2): the series then runs in u = 1/r with no per-pair scaling by 1/Rs^2.
 // C = tau pi + (tau^2-1) ln tau.  The annulus block holds the 12 coefficients e_0..e_11 of
 //   A g = u^2 sum_j e_j t^j,  t = a_t u + b_t,
 // the polynomial in t in [-1, 1] that interpolates A Rs^2 G at the 12 Chebyshev nodes of
-// y = Rs u in [1/(5 max(tau, 1)), 1/4], i.e. on the annulus r_in = 4 Rs <= r < r_far.  When the
+// y = Rs u in [1/(7 max(tau, 1)), 1/4], i.e. on the annulus r_in = 4 Rs <= r < r_far.  When the
 // annulus is too wide for 12 terms (tau > kMidTauMax), r_in^2 = r_far^2 and the block is zero.
 __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, float alphaRs, float rt, float4* t) {
   const float tau = rt / Rs;
@@ -317,22 +318,22 @@ __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, flo
   const float tm = fmaxf(tau, 1.f);
   const float r_far2 = kFarRadius * kFarRadius * tm * tm * Rs * Rs;
   const bool annulus = tau <= kMidTauMax;
-  // t = (2y - (ylo + yhi)) / (yhi - ylo) with y = Rs u, ylo = 1/(5 max(tau, 1)), yhi = 1/4
+  // t = (2y - (ylo + yhi)) / (yhi - ylo) with y = Rs u, ylo = 1/(7 max(tau, 1)), yhi = 1/4
   const float ylo = 1.f / (kFarRadius * tm), yhi = 0.25f;
   const float at = annulus ? 2.f * Rs / (yhi - ylo) : 0.f;
   const float bt = annulus ? -(ylo + yhi) / (yhi - ylo) : 0.f;
   t[0] = make_float4(-cx, -cx, -cy, -cy);
   t[1] = make_float4(r_far2, 1.f / (Rs * Rs), tau, A);
-  t[2] = make_float4(d[0], d[0], d[2], d[2]);
-  t[3] = make_float4(d[3], d[3], d[4], d[4]);
-  t[4] = make_float4(d[5], d[5], d[6], d[6]);
-  t[5] = make_float4(d[7], d[7], d[8], d[8]);
+  float seq[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // d_0, d_2, ..., d_kFarTerms
+  seq[0] = d[0];
+  for (int k = 2; k <= kFarTerms; ++k) seq[k - 1] = d[k];
+  for (int j = 0; j < 4; ++j) t[2 + j] = make_float4(seq[2 * j], seq[2 * j], seq[2 * j + 1], seq[2 * j + 1]);
   t[6] = make_float4(at, bt, annulus ? 16.f * Rs * Rs : r_far2, C);
   t[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Annulus block of a subhalo from its record t (Rs = its scale radius): G at the 12 Chebyshev
-// nodes of y in [1/(5 max(tau, 1)), 1/4] by the x >= 4 closed form, Chebyshev coefficients by the
+// nodes of y in [1/(7 max(tau, 1)), 1/4] by the x >= 4 closed form, Chebyshev coefficients by the
 // discrete cosine sum, then the monomial coefficients in t (T_j expanded by its recurrence,
 // whose integer coefficients are exact in FP32; the monomial form's FP32 condition number on
 // [-1, 1] is below 2 for tau <= kMidTauMax), scaled by A Rs^2.
@@ -402,16 +403,26 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
   return r;
 }
 
-// Far-field series: A g = u^2 (d_0 + u^2 (d_2 + d_3 u + ... + d_8 u^6)), u = 1/r, u2 = u^2,
+// Series coefficient d_k of a record (k = 0 or 2..kFarTerms): the sequence d_0, d_2, d_3, ...
+// fills t2, t3, ... two per float4, each as a duplicated pair (x, y) or (z, w).
+__device__ __forceinline__ int tnfw_coef_slot(int k) { return k == 0 ? 0 : k - 1; }
+__device__ __forceinline__ float tnfw_coef(const float4* t, int k) {
+  const int e = tnfw_coef_slot(k);
+  return (e & 1) ? t[2 + e / 2].z : t[2 + e / 2].x;
+}
+__device__ __forceinline__ float2 tnfw_coef2(const float4* t, int k) {
+  const int e = tnfw_coef_slot(k);
+  const float4 v = t[2 + e / 2];
+  return (e & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+}
+
+// Far-field series: A g = u^2 (d_0 + u^2 (d_2 + d_3 u + ... + d_6 u^4)), u = 1/r, u2 = u^2,
 // the same as A y^2 sum_k c_k y^k with y = Rs/r.  Scalar form (one sample).
 __device__ __forceinline__ float tnfw_series_u(float u, float u2, const float4* t) {
-  float p = fmaf(t[5].z, u, t[5].x);
-  p = fmaf(p, u, t[4].z);
-  p = fmaf(p, u, t[4].x);
-  p = fmaf(p, u, t[3].z);
-  p = fmaf(p, u, t[3].x);
-  p = fmaf(p, u, t[2].z);
-  p = fmaf(p, u2, t[2].x);
+  float p = fmaf(tnfw_coef(t, kFarTerms), u, tnfw_coef(t, kFarTerms - 1));
+#pragma unroll
+  for (int k = kFarTerms - 2; k >= 2; --k) p = fmaf(p, u, tnfw_coef(t, k));
+  p = fmaf(p, u2, tnfw_coef(t, 0));
   return p * u2;
 }
 
@@ -423,13 +434,10 @@ __device__ __forceinline__ float tnfw_series(float r2, const float4* t) {
 // Packed forms (two samples per instruction): element-wise the same operations, hence the same
 // rounding, as the scalar forms.
 __device__ __forceinline__ float2 tnfw_series2_u(float2 u, float2 u2, const float4* t) {
-  float2 p = __ffma2_rn(make_float2(t[5].z, t[5].w), u, make_float2(t[5].x, t[5].y));
-  p = __ffma2_rn(p, u, make_float2(t[4].z, t[4].w));
-  p = __ffma2_rn(p, u, make_float2(t[4].x, t[4].y));
-  p = __ffma2_rn(p, u, make_float2(t[3].z, t[3].w));
-  p = __ffma2_rn(p, u, make_float2(t[3].x, t[3].y));
-  p = __ffma2_rn(p, u, make_float2(t[2].z, t[2].w));
-  p = __ffma2_rn(p, u2, make_float2(t[2].x, t[2].y));
+  float2 p = __ffma2_rn(tnfw_coef2(t, kFarTerms), u, tnfw_coef2(t, kFarTerms - 1));
+#pragma unroll
+  for (int k = kFarTerms - 2; k >= 2; --k) p = __ffma2_rn(p, u, tnfw_coef2(t, k));
+  p = __ffma2_rn(p, u2, tnfw_coef2(t, 0));
   return __fmul2_rn(p, u2);
 }
 

@@ -358,12 +358,13 @@ __global__ void __launch_bounds__(32 * kHalfWarps) trace_image_2pass_kernel(cons
   trace_unit_2pass(sys, blockIdx.x, sm);
 }
 
-// Cluster form: CL CTAs of kTraceWarps/CL warps share one unit.  CTA r computes slices
+// Cluster form: CL CTAs of kTraceWarps/CL warps share one unit (register budget for 16 warps
+// per SM: measured faster than fewer warps with no spills).  CTA r computes slices
 // [r*NWC, (r+1)*NWC) of the same split; the leader reads every CTA's partials through
 // distributed shared memory in slice order, so the image is bitwise that of the one-CTA form,
 // while the finer CTAs balance the tail of the grid across the SMs.
 template <int CL>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(32 * (kTraceWarps / CL))
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(32 * (kTraceWarps / CL), 4 * CL / 2)
 trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
   constexpr int NWC = kTraceWarps / CL;
   __shared__ TraceSmem<NWC> sm;
