@@ -353,7 +353,7 @@ __device__ __forceinline__ void trace_unit_2pass(const DevSystem& sys, int blk, 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(32 * kHalfWarps) trace_image_2pass_kernel(const __grid_constant__ DevSystem sys) {
+__global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_image_2pass_kernel(const __grid_constant__ DevSystem sys) {
   __shared__ TraceSmem<kTraceWarps> sm;
   trace_unit_2pass(sys, blockIdx.x, sm);
 }
@@ -388,7 +388,7 @@ trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
 // Persistent form: CTAs pull unit tickets from the header's counter; ticket u belongs to the
 // system whose prefix range [unit_prefix[i], unit_prefix[i+1]) contains it.  Systems arrive
 // ordered by per-unit cost (largest first), so the queue hands out the longest units first.
-__global__ void __launch_bounds__(32 * kHalfWarps) trace_batch_kernel(BatchMeta* __restrict__ meta) {
+__global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_batch_kernel(BatchMeta* __restrict__ meta) {
   __shared__ TraceSmem<kTraceWarps> sm;
   __shared__ int s_ticket;
   const int n_sys = meta->n_sys;
@@ -438,7 +438,7 @@ cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t
     case 2: trace_cluster_kernel<2><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
     case 3: trace_cluster_kernel<4><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
     case 4: trace_cluster_kernel<8><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
-    default: trace_image_kernel<1><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
+    default: trace_image_kernel<2><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
   }
   return cudaGetLastError();
 }
