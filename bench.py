@@ -284,7 +284,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 "frac_at_median_clock": (achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
                                          if clocks["sm_mhz"] else None),
                 "pairs_per_s": pairs / avg_trace_s, "flops_per_pair": FLOPS_PER_PAIR,
-                "trace_ms": avg_trace_s * 1e3}
+                "trace_ms": avg_trace_s * 1e3,
+                # SFU: one MUFU.RSQ per pair against 16 MUFU results per clock per SM
+                "sfu": {"mufu_per_s": pairs / avg_trace_s, "peak_per_s": sms * 16 * max_mhz * 1e6,
+                        "frac": pairs / avg_trace_s / (sms * 16 * max_mhz * 1e6)}}
 
     # e2e: the public call with HOST buffers (pinned), copies inside the timed region
     e2e = None
@@ -402,6 +405,16 @@ def batched_extra(sim, lenssim, W, dev, n_sys: int, small: bool = False):
                         + "; one graph launch vs per-image calls with a sync each"}
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json), else the
+    recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def conv_extra(sim, W, dev, n_img: int = 4096, size: int = 256):
     """PSF step alone on a batch larger than L2: n_img x size^2 FP32 images through
     lens_sim_convolve.  k = 5 is HBM-bound (algorithmic 8 B per pixel: one read, one write);
@@ -427,8 +440,11 @@ def conv_extra(sim, W, dev, n_img: int = 4096, size: int = 256):
         px = n_img * size * size
         res[f"k{k}"] = {"ms": t * 1e3, "gbs_algorithmic": 8.0 * px / t / 1e9,
                         "tflops": 2.0 * k * k * px / t / 1e12}
-    res["hbm_peak_gbs_measured"] = 6780.0
-    res["k5_frac_of_measured_hbm"] = res["k5"]["gbs_algorithmic"] / 6780.0
+    peak, basis = measured_hbm_gbs()
+    res["hbm_peak_gbs"] = peak
+    res["hbm_peak_basis"] = basis
+    res["k5_frac_of_measured_hbm"] = res["k5"]["gbs_algorithmic"] / peak
+    res["k5_frac_of_nominal_hbm_7900"] = res["k5"]["gbs_algorithmic"] / 7900.0
     res["workload"] = f"{n_img} x {size}^2 FP32 images, lens_sim_convolve, inputs larger than L2"
     del x, y
     torch.cuda.empty_cache()
