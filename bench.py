@@ -598,6 +598,8 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=8.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, gradient and serving lines")
     ap.add_argument("--variant", type=int, default=-1, help="fixed trace launch variant instead of autotuning")
+    ap.add_argument("--fft-only", type=int, default=0, metavar="N_IMG",
+                    help="profiling mode: only the FFT-versus-direct PSF measurement (N_IMG images per call)")
     ap.add_argument("--psf-only", type=int, default=0, metavar="N_IMG",
                     help="only the standalone PSF measurement on N_IMG 256^2 images (profiling runs)")
     ap.add_argument("--batch-systems", type=int, default=4096)
@@ -611,6 +613,14 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.fft_only:
+        import torch
+        from paper_2606_01547_gb300 import lenssim
+        from paper_2606_01547_gb300 import workloads as W
+        sim = lenssim.Simulator(device=0)
+        print(json.dumps({"psf_fft": fft_conv_extra(sim, W, torch.device("cuda", 0), n_img=args.fft_only)}), flush=True)
+        sim.close()
         return
     if args.psf_only:
         import torch
