@@ -327,6 +327,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     if rank == 0 and world == 1 and not args.no_extras:
         extras["psf_conv"] = conv_extra(sim, W, dev)
         extras["psf_fft"] = fft_conv_extra(sim, W, dev)
+        extras["subhalo_scaling"] = subhalo_scaling_extra(sim, W, dev)
         extras["batched"] = batched_extra(sim, lenssim, W, dev, args.batch_systems)
         extras["batched_small_systems"] = batched_extra(sim, lenssim, W, dev, args.batch_systems, small=True)
         extras["differentiation"] = grad_extra(sim, W, dev)
@@ -483,6 +484,38 @@ def fft_conv_extra(sim, W, dev, n_img: int = 64):
     torch.cuda.empty_cache()
     res["workload"] = f"{n_img} images per call, Moffat kernels, lens_sim_convolve with the method forced"
     return res
+
+
+def subhalo_scaling_extra(sim, W, dev):
+    """Trace-kernel throughput against the subhalo count on the benchmark grid (200x200, s = 3):
+    the pair sum should stay at a flat pairs/s once the subhalos fill the GPU."""
+    import ctypes
+    import torch
+    from paper_2606_01547_gb300 import lenssim
+    L = lenssim.lib()
+    st = torch.cuda.current_stream()
+    out = torch.empty((200, 200), device=dev)
+    ptrs = (ctypes.c_void_p * 1)(out.data_ptr())
+    res = []
+    for n_sub in (1000, 3000, 10000, 30000, 100000):
+        system = W.substructure_system(2000 + n_sub, n_sub=n_sub, k=0)
+        keep = []
+        c = sim.system_struct(system, keep, subhalos=torch.from_numpy(system.subhalos).to(dev), use_psf=False)
+        reps = 3 if n_sub >= 30000 else 10
+        for _ in range(2):
+            L.lens_sim_image(sim.h, ctypes.byref(c), 1, ptrs, int(st.cuda_stream))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            rc = L.lens_sim_image(sim.h, ctypes.byref(c), 1, ptrs, int(st.cuda_stream))
+            if rc:
+                raise lenssim.LensSimError(rc, sim.last_error())
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res.append({"n_subhalos": n_sub, "ms_per_image": ms, "pairs_per_s": system.pairs() / (ms / 1e3)})
+    return {"points": res, "workload": "200x200, s = 3, no PSF, seeded TNFW populations of each size"}
 
 
 def grad_extra(sim, W, dev):

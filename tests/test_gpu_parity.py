@@ -353,6 +353,22 @@ def test_batch_of_uneven_systems_matches_single_calls(sim):
         np.testing.assert_array_equal(o.cpu().numpy(), gpu_image(sim, s_))
 
 
+def test_batched_largest_system_matches_oracle_rows(sim):
+    # the batched configuration's largest system (256x256, s = 3, 20,000 subhalos) inside an
+    # uneven batch, through the persistent batched launch the benchmark times: sampled
+    # unconvolved rows against the oracle, and bitwise equality with the single-image path
+    big = W.substructure_system(13, n_sub=20000, nx=256, s=3, k=0)
+    others = W.batched_systems(14, count=3, max_sub=2000, grids=(64, 100))
+    outs = sim.image([big] + others)
+    torch.cuda.synchronize()
+    got = outs[0].cpu().numpy()
+    np.testing.assert_array_equal(got, gpu_image(sim, big))
+    for row in (31, 180):
+        ref = oracle.image_rows(big, row, row + 1)
+        fl = np.abs(oracle.image_rows(big, row, row + 1, fp32=True) - ref).max() / np.abs(ref).max()
+        assert np.abs(got[row] - ref[0]).max() / np.abs(ref).max() <= max(1e-5, 2 * fl)
+
+
 def test_invalid_arguments_are_rejected(sim):
     from paper_2606_01547_gb300 import lenssim
     base = W.plain_system()
