@@ -91,6 +91,46 @@ def test_shapelet_source_needs_its_amplitudes(sim):
         sim.image(bad_m)
 
 
+@pytest.mark.parametrize("nx,ny,s,nsub,k", [(13, 9, 6, 60, 3), (11, 7, 7, 40, 5), (9, 10, 8, 25, 1),
+                                              (1, 37, 3, 80, 5), (41, 1, 2, 80, 3), (1, 1, 8, 10, 1)])
+def test_edge_grids_match_oracle(sim, nx, ny, s, nsub, k):
+    # the largest supersampling factors (their own unit shapes), single-row / single-column /
+    # single-pixel grids, and odd, non-square sizes
+    base = W.substructure_system(60 + s, n_sub=nsub, nx=8, s=s, k=k)
+    system = W.LensSystem(W.Grid(nx, ny, s, base.grid.dpix), base.deflectors, base.subhalos, base.source, base.psf)
+    ref = oracle.image(system)
+    tol, floor = image_tol(system, ref)
+    err = rel_linf(gpu_image(sim, system), ref)
+    assert err <= tol, (err, floor)
+
+
+def test_degenerate_inputs_match_oracle(sim):
+    # a subhalo centred exactly on a traced sample (x floored at 1e-6: alpha -> 0 there), round
+    # (e = 0) EPL and CSE lenses, and no lens at all
+    g = W.Grid(12, 12, 1, 0.1)
+    x0 = W.f32(0.05 + 0.1)   # centre of pixel column 7 (x = (7 - 5.5) * 0.1)
+    sub = np.array([[x0], [W.f32(0.05)], [0.02], [0.005], [0.1]], np.float32)
+    src = ("SERSIC_ELLIPSE_Q_PHI", [10.0, 0.3, 1.5, 0.8, 0.4, 0.02, -0.03])
+    cases = [W.LensSystem(g, [("EPL_E1E2", [1.0, 2.1, 0.0, 0.0, 0.0, 0.0])], sub, src, None),
+             W.LensSystem(g, [("CSE", [0.4, 0.1, 0.0, 0.0, 0.0, 0.0])], sub, src, None),
+             W.LensSystem(g, [], np.zeros((5, 0), np.float32), src, None)]
+    for system in cases:
+        ref = oracle.image(system)
+        tol, floor = image_tol(system, ref)
+        err = rel_linf(gpu_image(sim, system), ref)
+        assert err <= tol, (system.deflectors, err, floor)
+
+
+def test_image_path_with_largest_psf_matches_oracle(sim):
+    # k = 135 (the paper's largest kernel) through the single-image path; auto takes the FFT
+    base = W.substructure_system(70, n_sub=100, nx=60, s=1, k=0)
+    system = W.LensSystem(base.grid, base.deflectors, base.subhalos, base.source, W.moffat_psf(3.0, 1.0, 0.04, 135))
+    ref = oracle.image(system)
+    tol, floor = image_tol(system, ref)
+    err = rel_linf(gpu_image(sim, system), ref)
+    assert err <= tol, (err, floor)
+
+
 def test_unconvolved_image_and_no_subhalos(sim):
     system = W.substructure_system(5, n_sub=0, nx=40, s=2, k=0)
     ref = oracle.image(system)
