@@ -636,6 +636,9 @@ def main():
                     help="reference arm: seconds of oracle work for the whole run, split over its steps")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, gradient and serving lines")
     ap.add_argument("--variant", type=int, default=-1, help="fixed trace launch variant instead of autotuning")
+    ap.add_argument("--extra-only", default="", choices=["", "differentiation", "batched", "batched_small_systems",
+                                                          "fitting", "scaling"],
+                    help="profiling mode: only this one extra measurement")
     ap.add_argument("--fft-only", type=int, default=0, metavar="N_IMG",
                     help="profiling mode: only the FFT-versus-direct PSF measurement (N_IMG images per call)")
     ap.add_argument("--psf-only", type=int, default=0, metavar="N_IMG",
@@ -651,6 +654,20 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.extra_only:
+        import torch
+        from paper_2606_01547_gb300 import lenssim
+        from paper_2606_01547_gb300 import workloads as W
+        dev = torch.device("cuda", 0)
+        sim = lenssim.Simulator(device=0)
+        fn = {"differentiation": lambda: grad_extra(sim, W, dev),
+              "batched": lambda: batched_extra(sim, lenssim, W, dev, args.batch_systems),
+              "batched_small_systems": lambda: batched_extra(sim, lenssim, W, dev, args.batch_systems, small=True),
+              "fitting": lambda: fitting_extra(sim, W, dev),
+              "scaling": lambda: subhalo_scaling_extra(sim, W, dev)}[args.extra_only]
+        print(json.dumps({args.extra_only: fn()}), flush=True)
+        sim.close()
         return
     if args.fft_only:
         import torch

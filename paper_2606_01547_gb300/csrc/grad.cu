@@ -314,6 +314,40 @@ __global__ void __launch_bounds__(kGradThreads) residual_chi2_kernel(const float
 
 using namespace ls;
 
+namespace ls {
+// The fixed subhalo field of a likelihood call: cached per handle for registered tables (their
+// contents never change), recomputed into `scratch` otherwise.
+static int subhalo_field(lens_sim* s, const lens_system& y, const DevSystem& d, long long n_samples,
+                         float2* scratch, cudaStream_t st, float2** out) {
+  if (y.subhalo_table < 0) {
+    subhalo_field_kernel<<<(unsigned)((n_samples + 255) / 256), 256, 0, st>>>(d, scratch, n_samples);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "subhalo field");
+    *out = scratch;
+    return LENS_OK;
+  }
+  lens_sim::FieldKey key;
+  key.table = y.subhalo_table;
+  key.nx = y.grid.nx;
+  key.ny = y.grid.ny;
+  key.s = y.grid.supersample;
+  key.dpix = y.grid.pixel_scale;
+  key.x0 = y.grid.x0;
+  key.y0 = y.grid.y0;
+  void* before = s->sub_field.p;
+  int rc = ensure(s, s->sub_field, sizeof(float2) * (size_t)n_samples);
+  if (rc) return rc;
+  if (s->sub_field.p != before) s->field_key = lens_sim::FieldKey{};  // reallocated: contents gone
+  *out = (float2*)s->sub_field.p;
+  if (s->field_key == key) return LENS_OK;
+  subhalo_field_kernel<<<(unsigned)((n_samples + 255) / 256), 256, 0, st>>>(d, *out, n_samples);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(s, e, "subhalo field");
+  s->field_key = key;
+  return LENS_OK;
+}
+}  // namespace ls
+
 extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* data, float sigma_bkg, float t_exp,
                              const float* params, int n_points, float* out_logL, float* out_grad, void* stream) {
   if (!s) return LENS_ERR_INVALID_ARG;
@@ -358,7 +392,8 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
   d.n_defl = 0;
   if ((rc = prepare_subhalos(s, y, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
   char* base = (char*)s->grad_ws.p;
-  float2* asub = (float2*)base;
+  float2* asub = nullptr;
+  if ((rc = subhalo_field(s, y, d, n_samples, (float2*)base, st, &asub))) return rc;
   base += sub_bytes;
   float* m0 = (float*)base;
   float* m = m0 + (size_t)chunk * npix;
@@ -366,9 +401,7 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
   float* gm0 = gm + (size_t)chunk * npix;
   float* pl = gm0 + (size_t)chunk * npix;
   float* pg = pl + (size_t)chunk * nblk_l;
-  subhalo_field_kernel<<<(unsigned)((n_samples + 255) / 256), 256, 0, st>>>(d, asub, n_samples);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(s, e, "subhalo field");
+  cudaError_t e;
   const PsfEntry* psf = y.psf_id >= 0 ? &s->res->psfs[y.psf_id] : nullptr;
   for (int p0 = 0; p0 < n_points; p0 += chunk) {
     const int np = std::min(chunk, n_points - p0);
@@ -434,15 +467,14 @@ extern "C" int lens_sim_linear_amp(lens_sim* s, const lens_system* sys, const fl
   d.n_defl = 0;
   if ((rc = prepare_subhalos(s, y, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
   char* base = (char*)s->grad_ws.p;
-  float2* asub = (float2*)base;
+  float2* asub = nullptr;
+  if ((rc = subhalo_field(s, y, d, n_samples, (float2*)base, st, &asub))) return rc;
   base += sub_bytes;
   float* m0 = (float*)base;
   float* m1 = m0 + (size_t)chunk * npix;
   float* part = m1 + (size_t)chunk * npix;
   float* sums = part + (size_t)chunk * nblk * 3;
-  subhalo_field_kernel<<<(unsigned)((n_samples + 255) / 256), 256, 0, st>>>(d, asub, n_samples);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(s, e, "subhalo field");
+  cudaError_t e;
   const PsfEntry* psf = y.psf_id >= 0 ? &s->res->psfs[y.psf_id] : nullptr;
   for (int p0 = 0; p0 < n_points; p0 += chunk) {
     const int np = std::min(chunk, n_points - p0);

@@ -345,6 +345,7 @@ void lens_sim_destroy(lens_sim* s) {
     release(s, s->stage);
     release(s, s->grad_ws);
     release(s, s->fft_ws);
+    release(s, s->sub_field);
     for (auto& f : s->spectra) release(s, f.buf);
     s->spectra.clear();
     release(s, s->batch_meta);

@@ -80,6 +80,16 @@ struct lens_sim {
   ls::DevBuffer stage;    // device staging of host outputs
   ls::DevBuffer grad_ws;  // likelihood / adjoint workspace
   ls::DevBuffer fft_ws;   // FFT convolution workspace (row and column spectra of a chunk of images)
+  // Subhalo deflection field at every sample of a grid, for a registered (immutable) subhalo
+  // table: computed once per (table, grid) and reused by the likelihood calls that follow.
+  ls::DevBuffer sub_field;
+  struct FieldKey {
+    int table = -1, nx = 0, ny = 0, s = 0;
+    float dpix = 0.f, x0 = 0.f, y0 = 0.f;
+    bool operator==(const FieldKey& o) const {
+      return table == o.table && nx == o.nx && ny == o.ny && s == o.s && dpix == o.dpix && x0 == o.x0 && y0 == o.y0;
+    }
+  } field_key;
   struct FftSpectrum {
     int psf_id, My, Mx;
     ls::DevBuffer buf;

@@ -118,3 +118,24 @@ def test_linear_amplitude_solver_matches_oracle(sim, nx, s, k, nsub):
     np.testing.assert_allclose(amp.cpu().numpy(), ar, rtol=2e-5)
     np.testing.assert_allclose(L.cpu().numpy(), Lr, rtol=2e-5)
     assert abs(amp[0].item() - pb.truth[8]) < 0.05 * pb.truth[8]  # the truth point recovers its amplitude
+
+
+def test_cached_subhalo_field_of_registered_tables(sim):
+    # a registered table's subhalo field is computed once per (table, grid) and reused: the
+    # likelihood and gradient equal, bitwise, those of the same subhalos passed as raw arrays,
+    # on repeated calls and after switching to another grid and back
+    pb = W.diff_problem(31, n_points=4, n_sub=300, nx=40, dpix=0.08, k=5)
+    data = torch.from_numpy(W.observe(oracle.model_image(pb.system, pb.truth), pb.sigma_bkg, pb.t_exp, 31)).cuda()
+    P = torch.from_numpy(pb.points).cuda()
+    tid = sim.register_subhalos(pb.system.subhalos)
+    raw = [t.cpu().numpy() for t in sim.grad(pb.system, data, pb.sigma_bkg, pb.t_exp, P, want_grad=True)]
+    other = W.LensSystem(W.Grid(24, 24, 1, 0.1), pb.system.deflectors, pb.system.subhalos, pb.system.source,
+                         pb.system.psf)
+    data_o = torch.zeros((24, 24), device="cuda") + 0.01
+    for i in range(3):
+        got = [t.cpu().numpy() for t in sim.grad(pb.system, data, pb.sigma_bkg, pb.t_exp, P, want_grad=True,
+                                                   subhalo_table=tid)]
+        for a, b in zip(got, raw):
+            np.testing.assert_array_equal(a, b)
+        if i == 1:
+            sim.grad(other, data_o, pb.sigma_bkg, pb.t_exp, P, want_grad=False, subhalo_table=tid)
