@@ -348,6 +348,19 @@ static int subhalo_field(lens_sim* s, const lens_system& y, const DevSystem& d, 
 }
 }  // namespace ls
 
+namespace ls {
+// PSF step of the likelihood path on np images: the convolution (adjoint = 0) or its adjoint,
+// the correlation (adjoint = 1, a convolution with the kernel turned by 180 degrees); the TMA
+// kernel where it applies, else the generic one.
+static cudaError_t psf_step(lens_sim* s, const float* in, float* out, int np, int ny, int nx, const PsfEntry* psf,
+                            int adjoint, cudaStream_t st) {
+  if (s->wait_flag_d && conv_tma_supported(in, out, ny, nx, psf->k))
+    return launch_conv_tma(in, out, np, ny, nx, adjoint ? psf->dflip : psf->d, psf->k, s->wait_flag_d, s->sm_count,
+                           st);
+  return launch_conv(in, out, np, ny, nx, psf->d, psf->k, adjoint ? 0 : 1, st);
+}
+}  // namespace ls
+
 extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* data, float sigma_bkg, float t_exp,
                              const float* params, int n_points, float* out_logL, float* out_grad, void* stream) {
   if (!s) return LENS_ERR_INVALID_ARG;
@@ -357,6 +370,7 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
   if (!(sigma_bkg > 0.f) || !(t_exp > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "sigma_bkg and t_exp must be > 0");
   if (n_points == 0) return LENS_OK;
   DeviceGuard guard(s->device);
+  if (int rw = ensure_wait_flag(s)) return rw;
   lens_system y = *sys;
   y.n_deflectors = 0;   // the free parameters replace the deflector list and source
   y.source.type = LIGHT_SERSIC;
@@ -407,14 +421,14 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
     const int np = std::min(chunk, n_points - p0);
     const float* P = params + (size_t)p0 * LENS_N_FREE_PARAMS;
     forward_model_kernel<<<dim3((npix + kGradThreads - 1) / kGradThreads, np), kGradThreads, 0, st>>>(d, P, asub, m0, 0);
-    if (psf) e = launch_conv(m0, m, np, ny, nx, psf->d, psf->k, 1, st);
+    if (psf) e = psf_step(s, m0, m, np, ny, nx, psf, 0, st);
     else e = cudaMemcpyAsync(m, m0, sizeof(float) * (size_t)np * npix, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "model convolution");
     likelihood_kernel<<<dim3(nblk_l, np), kGradThreads, 0, st>>>(m, data, npix, sigma_bkg * sigma_bkg, 1.f / t_exp,
                                                                   out_grad ? gm : nullptr, pl, nblk_l);
     reduce_partials_kernel<<<(np + 127) / 128, 128, 0, st>>>(pl, nblk_l, 1, -0.5f, out_logL + p0, np);
     if (out_grad) {
-      if (psf) e = launch_conv(gm, gm0, np, ny, nx, psf->d, psf->k, 0, st);
+      if (psf) e = psf_step(s, gm, gm0, np, ny, nx, psf, 1, st);
       else e = cudaMemcpyAsync(gm0, gm, sizeof(float) * (size_t)np * npix, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return cuda_fail(s, e, "adjoint convolution");
       backward_kernel<<<dim3(nblk_b, np), kGradThreads, 0, st>>>(d, P, asub, gm0, pg, nblk_b);
@@ -437,6 +451,7 @@ extern "C" int lens_sim_linear_amp(lens_sim* s, const lens_system* sys, const fl
   if (!(sigma_bkg > 0.f) || !(t_exp > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "sigma_bkg and t_exp must be > 0");
   if (n_points == 0) return LENS_OK;
   DeviceGuard guard(s->device);
+  if (int rw = ensure_wait_flag(s)) return rw;
   lens_system y = *sys;
   y.n_deflectors = 0;
   y.source.type = LIGHT_SERSIC;
@@ -480,7 +495,7 @@ extern "C" int lens_sim_linear_amp(lens_sim* s, const lens_system* sys, const fl
     const int np = std::min(chunk, n_points - p0);
     const float* P = params + (size_t)p0 * LENS_N_FREE_PARAMS;
     forward_model_kernel<<<dim3(nblk, np), kGradThreads, 0, st>>>(d, P, asub, m0, 1);
-    if (psf) e = launch_conv(m0, m1, np, ny, nx, psf->d, psf->k, 1, st);
+    if (psf) e = psf_step(s, m0, m1, np, ny, nx, psf, 0, st);
     else e = cudaMemcpyAsync(m1, m0, sizeof(float) * (size_t)np * npix, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "model convolution");
     normal_eq_kernel<<<dim3(nblk, np), kGradThreads, 0, st>>>(m1, data, npix, sigma_bkg * sigma_bkg, 1.f / t_exp,

@@ -288,6 +288,24 @@ int psf_apply(lens_sim* s, const float* in, float* out, int n_img, int ny, int n
   return LENS_OK;
 }
 
+int ensure_wait_flag(lens_sim* s) {
+  if (!s->wait_flag_h) {
+    if (cudaHostAlloc((void**)&s->wait_flag_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&s->wait_flag_d, s->wait_flag_h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (s->wait_flag_h) cudaFreeHost(s->wait_flag_h);
+      s->wait_flag_h = nullptr;
+      return fail(s, LENS_ERR_OOM, "host-mapped wait flag");
+    }
+    *s->wait_flag_h = 0;
+  }
+  if (*(volatile int*)s->wait_flag_h) {
+    *s->wait_flag_h = 0;
+    return fail(s, LENS_ERR_TIMEOUT, "a bounded wait of an earlier convolution expired");
+  }
+  return LENS_OK;
+}
+
 DeviceGuard::DeviceGuard(int dev) {
   // A non-fatal status left by an earlier call on this thread (e.g. "not ready" from a query)
   // would otherwise be read back by the launch checks below as a launch failure.
@@ -367,14 +385,21 @@ int lens_sim_register_psf(lens_sim* s, const float* kernel, int k, int* psf_id) 
   if (k < 1 || k > LENS_MAX_PSF || (k % 2) == 0) return fail(s, LENS_ERR_INVALID_ARG, "PSF size %d must be odd in [1, %d]", k, LENS_MAX_PSF);
   DeviceGuard g(s->device);
   size_t bytes = sizeof(float) * (size_t)k * k;
-  if (s->budget && s->allocated + bytes > s->budget) return fail(s, LENS_ERR_OOM, "PSF exceeds the memory budget");
+  if (s->budget && s->allocated + 2 * bytes > s->budget) return fail(s, LENS_ERR_OOM, "PSF exceeds the memory budget");
+  std::vector<float> h((size_t)k * k), hf((size_t)k * k);
+  cudaError_t e = cudaMemcpy(h.data(), kernel, bytes, is_device_ptr(kernel) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+  if (e != cudaSuccess) return cuda_fail(s, e, "read PSF");
+  for (size_t t = 0; t < h.size(); ++t) hf[t] = h[h.size() - 1 - t];
   float* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, bytes);
+  float* df = nullptr;
+  e = cudaMalloc(&d, 2 * bytes);
   if (e != cudaSuccess) { cudaGetLastError(); return fail(s, LENS_ERR_OOM, "cudaMalloc PSF: %s", cudaGetErrorString(e)); }
-  e = cudaMemcpy(d, kernel, bytes, is_device_ptr(kernel) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  df = d + (size_t)k * k;
+  e = cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(df, hf.data(), bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(d); return cuda_fail(s, e, "copy PSF"); }
-  s->allocated += bytes;
-  s->res->psfs.push_back({d, k});
+  s->allocated += 2 * bytes;
+  s->res->psfs.push_back({d, k, df});
   *psf_id = (int)s->res->psfs.size() - 1;
   return LENS_OK;
 }
@@ -490,22 +515,8 @@ int lens_sim_convolve(lens_sim* s, const float* in, int n_img, int ny, int nx, i
   if (!in || !out || in == out) return fail(s, LENS_ERR_INVALID_ARG, "NULL or aliased buffers");
   DeviceGuard g(s->device);
   if (!is_device_ptr(in) || !is_device_ptr(out)) return fail(s, LENS_ERR_INVALID_ARG, "images must be device memory");
-  const PsfEntry& p = s->res->psfs[psf_id];
-  if (!s->wait_flag_h) {
-    if (cudaHostAlloc((void**)&s->wait_flag_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostGetDevicePointer((void**)&s->wait_flag_d, s->wait_flag_h, 0) != cudaSuccess) {
-      cudaGetLastError();
-      if (s->wait_flag_h) cudaFreeHost(s->wait_flag_h);
-      s->wait_flag_h = nullptr;
-      return fail(s, LENS_ERR_OOM, "host-mapped wait flag");
-    }
-    *s->wait_flag_h = 0;
-  }
-  if (*(volatile int*)s->wait_flag_h) {
-    *s->wait_flag_h = 0;
-    return fail(s, LENS_ERR_TIMEOUT, "a bounded wait of an earlier convolution expired");
-  }
-  (void)p;
+  const int rc = ensure_wait_flag(s);
+  if (rc) return rc;
   return psf_apply(s, in, out, n_img, ny, nx, psf_id, (cudaStream_t)stream, true);
 }
 

@@ -21,6 +21,7 @@ struct DevBuffer {
 struct PsfEntry {
   float* d = nullptr;
   int k = 0;
+  float* dflip = nullptr;  // the kernel turned by 180 degrees: correlation as a convolution
 };
 
 struct SubTable {
@@ -44,6 +45,9 @@ bool is_device_ptr(const void* p);
 int ensure(lens_sim* s, DevBuffer& b, size_t bytes);
 void release(lens_sim* s, DevBuffer& b);
 int validate_system(lens_sim* s, const lens_system& y, bool need_grid);
+// Host-mapped flag of the TMA convolution's bounded waits: allocated on first use; returns
+// LENS_ERR_TIMEOUT (and clears it) if an earlier wait expired.
+int ensure_wait_flag(lens_sim* s);
 int sub_count(lens_sim* s, const lens_system& y);
 int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* raw_buf, const float4** out_tab,
                      int* out_n, cudaStream_t st);
