@@ -604,9 +604,12 @@ def serving_extra(lenssim, W, rates, seconds: float):
         codes = collections.Counter(srv.wait(t, 600000) for t in tickets)
         st = srv.stats()
         n_img = sum(1 for rq in reqs if rq.kind == 0)
-        out.append({"rate_req_per_s": rate, "seconds": dur, "requests": len(reqs), "images": n_img,
-                    "completed_ok": codes.get(0, 0), "failed": {str(k): v for k, v in codes.items() if k != 0},
-                    "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "served_req_per_s": st["requests_per_s"]})
+        rec = {"rate_req_per_s": rate, "seconds": dur, "requests": len(reqs), "images": n_img,
+               "completed_ok": codes.get(0, 0), "failed": {str(k): v for k, v in codes.items() if k != 0},
+               "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "served_req_per_s": st["requests_per_s"]}
+        if rec["failed"]:
+            rec["last_error"] = srv.last_error()
+        out.append(rec)
         srv.close()
         if plain is None:
             sim = lenssim.Simulator(device=0)

@@ -263,8 +263,12 @@ typedef struct {
 
 int lens_serve_create(const lens_sim_config* config, int max_inflight, lens_server** out);
 /* The server's own handle, for lens_sim_register_psf / lens_sim_register_subhalos before
- * submitting requests that use them (do not call them while requests are in flight). */
+ * submitting requests that use them (registration is safe while other requests run: the
+ * registry is shared under a lock and read as copies). */
 lens_sim* lens_serve_sim(lens_server* srv);
+/* Text of the server's most recent failed request ("" if none); the calling thread's copy,
+ * valid until its next call. */
+const char* lens_serve_last_error(lens_server* srv);
 /* Enqueue a request; LENS_ERR_BUSY when max_inflight requests are already queued or running. */
 int lens_serve_submit(lens_server* srv, const lens_request* req, unsigned long long* ticket);
 /* Wait up to timeout_ms (>= 0) for a ticket: LENS_OK, LENS_ERR_TIMEOUT, LENS_ERR_CANCELLED,

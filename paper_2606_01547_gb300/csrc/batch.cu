@@ -88,7 +88,8 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
     const size_t npix = (size_t)y.grid.nx * y.grid.ny;
     if (y.psf_id >= 0) {
       pix_total += align256(npix * sizeof(float));
-      kmax = std::max(kmax, s->res->psfs[y.psf_id].k);
+      PsfEntry pe;
+      if (s->res->psf(y.psf_id, &pe)) kmax = std::max(kmax, pe.k);
       ++n_conv;
     }
     if (!dev_out[i]) stage_total += align256(npix * sizeof(float));
@@ -98,7 +99,7 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
       ++n_prep;
     }
   }
-  for (const auto& p : s->res->psfs) kmax = std::max(kmax, p.k);  // graph smem covers every registered PSF
+  kmax = std::max(kmax, s->res->kmax());  // graph smem covers every registered PSF
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
 
@@ -190,8 +191,10 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
     DevSystem& d = hsys[r];
     fill_dev_system(y, d);
     if (y.subhalo_table >= 0) {
-      d.sub = s->res->tables[y.subhalo_table].d;
-      d.n_sub = s->res->tables[y.subhalo_table].n;
+      SubTable t;
+      s->res->table(y.subhalo_table, &t);
+      d.sub = t.d;
+      d.n_sub = t.n;
     } else {
       d.sub = tabs[i];
       d.n_sub = nsub[i];
@@ -202,7 +205,8 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
     hpre[r] = u;
     u += units[i];
     if (y.psf_id >= 0) {
-      const PsfEntry& p = s->res->psfs[y.psf_id];
+      PsfEntry p;
+      s->res->psf(y.psf_id, &p);
       hconv[ic++] = ConvJob{raw_img[i], final_dst, p.d, y.grid.ny, y.grid.nx, p.k, tiles};
       tiles += ((y.grid.nx + 31) / 32) * ((y.grid.ny + 31) / 32);
     }

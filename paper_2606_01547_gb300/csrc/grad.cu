@@ -416,7 +416,8 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
   float* pl = gm0 + (size_t)chunk * npix;
   float* pg = pl + (size_t)chunk * nblk_l;
   cudaError_t e;
-  const PsfEntry* psf = y.psf_id >= 0 ? &s->res->psfs[y.psf_id] : nullptr;
+  PsfEntry psf_copy;
+  const PsfEntry* psf = (y.psf_id >= 0 && s->res->psf(y.psf_id, &psf_copy)) ? &psf_copy : nullptr;
   for (int p0 = 0; p0 < n_points; p0 += chunk) {
     const int np = std::min(chunk, n_points - p0);
     const float* P = params + (size_t)p0 * LENS_N_FREE_PARAMS;
@@ -490,7 +491,8 @@ extern "C" int lens_sim_linear_amp(lens_sim* s, const lens_system* sys, const fl
   float* part = m1 + (size_t)chunk * npix;
   float* sums = part + (size_t)chunk * nblk * 3;
   cudaError_t e;
-  const PsfEntry* psf = y.psf_id >= 0 ? &s->res->psfs[y.psf_id] : nullptr;
+  PsfEntry psf_copy;
+  const PsfEntry* psf = (y.psf_id >= 0 && s->res->psf(y.psf_id, &psf_copy)) ? &psf_copy : nullptr;
   for (int p0 = 0; p0 < n_points; p0 += chunk) {
     const int np = std::min(chunk, n_points - p0);
     const float* P = params + (size_t)p0 * LENS_N_FREE_PARAMS;

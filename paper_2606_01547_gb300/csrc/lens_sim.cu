@@ -172,7 +172,8 @@ int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
       return fail(s, LENS_ERR_INVALID_ARG, "bad pixel scale or grid centre");
     int rc = validate_light(s, y.source, y.source_coeffs, y.n_source_coeffs);
     if (rc) return rc;
-    if (y.psf_id < -1 || y.psf_id >= (int)s->res->psfs.size() || (y.psf_id >= 0 && !s->res->psfs[y.psf_id].d))
+    PsfEntry pe;
+    if (y.psf_id < -1 || (y.psf_id >= 0 && (!s->res->psf(y.psf_id, &pe) || !pe.d)))
       return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", y.psf_id);
   }
   if (y.n_deflectors < 0 || y.n_deflectors > LENS_MAX_DEFLECTORS)
@@ -183,7 +184,8 @@ int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
     if (rc) return rc;
   }
   if (y.subhalo_table >= 0) {
-    if (y.subhalo_table >= (int)s->res->tables.size() || (!s->res->tables[y.subhalo_table].d && s->res->tables[y.subhalo_table].n))
+    SubTable t;
+    if (!s->res->table(y.subhalo_table, &t) || (!t.d && t.n))
       return fail(s, LENS_ERR_INVALID_ARG, "unknown subhalo_table %d", y.subhalo_table);
   } else {
     if (y.subhalo_table != -1) return fail(s, LENS_ERR_INVALID_ARG, "subhalo_table must be -1 or a table id");
@@ -194,7 +196,9 @@ int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
 }
 
 int sub_count(lens_sim* s, const lens_system& y) {
-  return y.subhalo_table >= 0 ? s->res->tables[y.subhalo_table].n : y.n_subhalos;
+  if (y.subhalo_table < 0) return y.n_subhalos;
+  SubTable t;
+  return s->res->table(y.subhalo_table, &t) ? t.n : 0;
 }
 
 // Resolve the subhalo table of a system into device constants (kTableStride float4 per subhalo).
@@ -202,8 +206,10 @@ int sub_count(lens_sim* s, const lens_system& y) {
 int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* raw_buf,
                      const float4** out_tab, int* out_n, cudaStream_t st) {
   if (y.subhalo_table >= 0) {
-    *out_tab = s->res->tables[y.subhalo_table].d;
-    *out_n = s->res->tables[y.subhalo_table].n;
+    SubTable t;
+    if (!s->res->table(y.subhalo_table, &t)) return fail(s, LENS_ERR_INVALID_ARG, "unknown subhalo_table %d", y.subhalo_table);
+    *out_tab = t.d;
+    *out_n = t.n;
     return LENS_OK;
   }
   const int n = y.n_subhalos;
@@ -243,7 +249,8 @@ void fill_dev_system(const lens_system& y, DevSystem& d) {
 // PSF step of a stack of n_img equal-size device images (method per the handle; in != out).
 int psf_apply(lens_sim* s, const float* in, float* out, int n_img, int ny, int nx, int psf_id, cudaStream_t st,
               bool allow_tma) {
-  const PsfEntry& p = s->res->psfs[psf_id];
+  PsfEntry p;
+  if (!s->res->psf(psf_id, &p)) return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", psf_id);
   int My = 0, Mx = 0;
   const bool fits = conv_fft_sizes(ny, nx, p.k, &My, &Mx);
   if (s->conv_method == LENS_CONV_FFT && !fits)
@@ -352,6 +359,7 @@ void lens_sim_destroy(lens_sim* s) {
     DeviceGuard g(s->device);
     cudaDeviceSynchronize();
     if (s->owns_resident) {
+      std::lock_guard<std::mutex> lk(s->res->mu);
       for (auto& p : s->res->psfs) if (p.d) cudaFree(p.d);
       for (auto& t : s->res->tables) if (t.d) cudaFree(t.d);
       s->res->psfs.clear();
@@ -399,8 +407,7 @@ int lens_sim_register_psf(lens_sim* s, const float* kernel, int k, int* psf_id) 
   if (e == cudaSuccess) e = cudaMemcpy(df, hf.data(), bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(d); return cuda_fail(s, e, "copy PSF"); }
   s->allocated += 2 * bytes;
-  s->res->psfs.push_back({d, k, df});
-  *psf_id = (int)s->res->psfs.size() - 1;
+  *psf_id = s->res->add_psf({d, k, df});
   return LENS_OK;
 }
 
@@ -427,8 +434,7 @@ int lens_sim_register_subhalos(lens_sim* s, const float* soa, int n, int* table_
     if (e != cudaSuccess) { cudaFree(t.d); return cuda_fail(s, e, "subhalo table"); }
     s->allocated += bytes;
   }
-  s->res->tables.push_back(t);
-  *table_id = (int)s->res->tables.size() - 1;
+  *table_id = s->res->add_table(t);
   return LENS_OK;
 }
 
@@ -510,7 +516,8 @@ int lens_sim_deflection(lens_sim* s, const lens_system* sys, const float* x, con
 int lens_sim_convolve(lens_sim* s, const float* in, int n_img, int ny, int nx, int psf_id, float* out, void* stream) {
   if (!s) return LENS_ERR_INVALID_ARG;
   if (n_img < 0 || ny < 1 || nx < 1 || ny > 16384 || nx > 16384) return fail(s, LENS_ERR_INVALID_ARG, "bad image sizes");
-  if (psf_id < 0 || psf_id >= (int)s->res->psfs.size()) return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", psf_id);
+  PsfEntry pe;
+  if (!s->res->psf(psf_id, &pe)) return fail(s, LENS_ERR_INVALID_ARG, "unknown psf_id %d", psf_id);
   if (n_img == 0) return LENS_OK;
   if (!in || !out || in == out) return fail(s, LENS_ERR_INVALID_ARG, "NULL or aliased buffers");
   DeviceGuard g(s->device);

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -88,9 +89,16 @@ struct lens_server {
   std::vector<double> lat_ms;
   Clock::time_point t_first, t_last;
   bool have_first = false;
+  std::mutex err_mu;
+  std::string last_err;  // text of the most recent failed request
 };
 
 namespace {
+
+void note_error(lens_server* srv, const char* what) {
+  std::lock_guard<std::mutex> lk(srv->err_mu);
+  srv->last_err = what ? what : "unknown error";
+}
 
 // Estimated device bytes of one request while it runs.
 size_t estimate_bytes(lens_server* srv, const lens_request& r) {
@@ -163,6 +171,7 @@ void issue(lens_server* srv, Slot* sl, CbArg* cb) {
   }
   if (rc != LENS_OK) {
     for (Req* q : sl->batch) q->status = rc;
+    note_error(srv, "staging the batch's inputs failed");
   } else {
     // images: one (batched) call
     std::vector<lens_system> sys;
@@ -182,8 +191,10 @@ void issue(lens_server* srv, Slot* sl, CbArg* cb) {
       int st = lens_sim_image(sl->sim, sys.data(), (int)sys.size(), outs.data(), sl->stream);
       if (st != LENS_OK) {
         // re-issue one by one so that one bad request does not fail the others
-        for (size_t k = 0; k < img.size(); ++k)
+        for (size_t k = 0; k < img.size(); ++k) {
           img[k]->status = lens_sim_image(sl->sim, &sys[k], 1, &outs[k], sl->stream);
+          if (img[k]->status != LENS_OK) note_error(srv, lens_sim_last_error(sl->sim));
+        }
       }
       for (Req* q : img)
         if (q->status == LENS_OK)
@@ -206,6 +217,7 @@ void issue(lens_server* srv, Slot* sl, CbArg* cb) {
       float* dout = sl->d_out + q->out_off;
       q->status = lens_sim_grad(sl->sim, &y, din, q->r.sigma_bkg, q->r.t_exp, din + npix, 1, dout,
                                 q->r.out_grad ? dout + 1 : nullptr, sl->stream);
+      if (q->status != LENS_OK) note_error(srv, lens_sim_last_error(sl->sim));
       if (q->status == LENS_OK)
         cudaMemcpyAsync(sl->h_out + q->out_off, dout, 16 * sizeof(float), cudaMemcpyDeviceToHost, sl->stream);
     }
@@ -236,6 +248,7 @@ void finish(lens_server* srv, Slot* sl) {
     e = cudaSuccess;
   }
   const auto now = Clock::now();
+  if (e != cudaSuccess) note_error(srv, cudaGetErrorString(e));
   for (Req* q : sl->batch) {
     if (q->status == LENS_OK && e != cudaSuccess) q->status = LENS_ERR_CUDA;
     if (q->status == LENS_OK) {
@@ -347,6 +360,14 @@ int lens_serve_create(const lens_sim_config* config, int max_inflight, lens_serv
 }
 
 lens_sim* lens_serve_sim(lens_server* srv) { return srv ? srv->main : nullptr; }
+
+const char* lens_serve_last_error(lens_server* srv) {
+  static thread_local std::string copy;
+  if (!srv) return "null server";
+  std::lock_guard<std::mutex> lk(srv->err_mu);
+  copy = srv->last_err;
+  return copy.c_str();
+}
 
 int lens_serve_pause(lens_server* srv, int paused) {
   if (!srv) return LENS_ERR_INVALID_ARG;

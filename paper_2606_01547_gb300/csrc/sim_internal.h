@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -59,9 +60,42 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
 namespace ls {
 // Resident state (registered PSFs and subhalo tables).  A server's slot handles share their
 // parent's resident state; only the owner frees it.
+// Registered PSFs and subhalo tables, shared by a server's slot handles.  Registration may
+// append from another thread while requests run, so entries are read as copies under the lock
+// (a reference into the vectors would dangle when they grow).
 struct Resident {
+  mutable std::mutex mu;
   std::vector<PsfEntry> psfs;
   std::vector<SubTable> tables;
+
+  bool psf(int id, PsfEntry* out) const {
+    std::lock_guard<std::mutex> lk(mu);
+    if (id < 0 || id >= (int)psfs.size()) return false;
+    *out = psfs[id];
+    return true;
+  }
+  bool table(int id, SubTable* out) const {
+    std::lock_guard<std::mutex> lk(mu);
+    if (id < 0 || id >= (int)tables.size()) return false;
+    *out = tables[id];
+    return true;
+  }
+  int kmax() const {
+    std::lock_guard<std::mutex> lk(mu);
+    int k = 0;
+    for (const auto& p : psfs) k = p.k > k ? p.k : k;
+    return k;
+  }
+  int add_psf(const PsfEntry& e) {
+    std::lock_guard<std::mutex> lk(mu);
+    psfs.push_back(e);
+    return (int)psfs.size() - 1;
+  }
+  int add_table(const SubTable& t) {
+    std::lock_guard<std::mutex> lk(mu);
+    tables.push_back(t);
+    return (int)tables.size() - 1;
+  }
 };
 }  // namespace ls
 

@@ -39,7 +39,7 @@ EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_
             "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_set_conv_method", "lens_sim_grad",
             "lens_sim_linear_amp",
             "lens_sim_image_noalloc", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
-            "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats",
+            "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats", "lens_serve_last_error",
             "lens_serve_reset_stats", "lens_serve_destroy")
 
 
@@ -136,6 +136,8 @@ def lib():
             L.lens_serve_pause.argtypes = [vp, ip]
             L.lens_serve_reset_stats.argtypes = [vp]
             L.lens_serve_destroy.argtypes = [vp]
+            L.lens_serve_last_error.argtypes = [vp]
+            L.lens_serve_last_error.restype = ctypes.c_char_p
             L.lens_serve_destroy.restype = None
             _lib = L
     return _lib
@@ -467,6 +469,10 @@ class Server:
         keep.append(req)
         self._keep[t.value] = keep
         return t.value
+
+    def last_error(self) -> str:
+        """Text of the server's most recent failed request ("" if none)."""
+        return (self._L.lens_serve_last_error(self.h) or b"").decode()
 
     def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
         rc = self._L.lens_serve_wait(self.h, ticket, int(timeout_ms))

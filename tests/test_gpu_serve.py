@@ -139,3 +139,31 @@ def test_budget_refusal_and_a_bad_request_fails_alone(lenssim):
     assert srv.wait(t3) == lenssim.LENS_OK
     np.testing.assert_array_equal(o1, o3)
     srv.close()
+
+
+def test_psf_registration_while_requests_run(lenssim):
+    # the binding registers each new PSF on the server's handle at submit time, while the worker
+    # runs earlier requests: the worker's registry reads must not race the registrations
+    srv = lenssim.Server(device=0)
+    rng = np.random.default_rng(5)
+    tickets, keep = [], []
+    for i in range(240):
+        k = int(W.BATCH_PSF[i % len(W.BATCH_PSF)])
+        nx = 64 if i % 2 else 48
+        base = W.LensSystem(W.Grid(nx, nx, 1, W.f32(0.04)), [], W.subhalo_population(rng, 50),
+                            ("SERSIC_ELLIPSE", [0.0] * 7), W.moffat_psf(3.0, 0.1 + 0.01 * (i % 7), 0.04, k))
+        p = W._draw_free(rng)
+        system = W.system_from_free(base, p)
+        if i % 3:
+            o = np.empty((nx, nx), np.float32)
+            keep.append(o)
+            tickets.append(srv.submit_image(system, o))
+        else:
+            d = np.zeros((nx, nx), np.float32)
+            pp = np.array(p, np.float32)
+            o, g = np.empty(1, np.float32), np.empty(15, np.float32)
+            keep += [d, pp, o, g]
+            tickets.append(srv.submit_loglike(system, d, 0.01, 1000.0, pp, o, g))
+    codes = [srv.wait(t, 120000) for t in tickets]
+    assert all(c == lenssim.LENS_OK for c in codes), (codes, srv.last_error())
+    srv.close()
