@@ -340,6 +340,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{rows} unconvolved rows of one 200x200 s=3 image (10k subhalos) + one full "
                          f"21x21 convolution, extrapolated to whole images"}
+        # the same oracle on one core (a short sample: a few rows)
+        import oracle
+        oracle.set_threads(1)
+        v1, rows1, _ = oracle_sample(systems[0], max(2.0, args.cpu_budget_s / 4), 200)
+        oracle.set_threads(cores)
+        cpu["one_core"] = {"value": v1, "rows": rows1}
 
     if rank == 0:
         res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -568,6 +574,85 @@ def fitting_extra(sim, W, dev):
     return {"pso": out, "workload": "100x100, 13x13 PSF, 1000 fixed TNFW, 15 free parameters"}
 
 
+def serving_full_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_sets: int = 2):
+    """The long serving sweep: open-loop Poisson arrivals at each rate for `seconds`, drawn from a
+    pool of `pool_size` pre-generated requests (the serving mix) that is cycled.  Each pool entry
+    has `out_sets` sets of output buffers used in turn, so a buffer set is reused only
+    pool_size * out_sets arrivals later, after its previous request finished (a reuse that had to
+    wait for it is counted in `blocked_reuses`); a submit refused with LENS_ERR_BUSY (more than
+    max_inflight = 4096 requests admitted) counts as rejected.  p50/p99 are the server's own
+    submit-to-result latencies of the admitted requests."""
+    import collections
+    import numpy as np
+    pool = W.serving_stream(7, rate=1.0, duration=1.3 * pool_size)[:pool_size]
+    inputs, outs = [], []
+    for rq in pool:
+        g = rq.system.grid
+        if rq.kind == 0:
+            inputs.append(())
+            outs.append([(np.empty((g.ny, g.nx), np.float32),) for _ in range(out_sets)])
+        else:
+            p = np.array([*rq.system.deflectors[0][1], *rq.system.deflectors[1][1], *rq.system.source[1]],
+                         np.float32)
+            inputs.append((np.zeros((g.ny, g.nx), np.float32), p))
+            outs.append([(np.empty(1, np.float32), np.empty(15, np.float32)) for _ in range(out_sets)])
+    out = []
+    for rate in rates:
+        rng = np.random.default_rng(int(rate))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds * 1.2) + 16))
+        arrivals = arrivals[arrivals < seconds]
+        srv = lenssim.Server(device=0)
+        # the PSFs are registered up front, as a deployment would
+        for rq in pool:
+            srv.sim.register_psf(rq.system.psf)
+        codes = collections.Counter()
+        pending = {}
+        rejected = blocked = 0
+        late = 0.0
+        t0 = time.perf_counter()
+        for i, ta in enumerate(arrivals):
+            delay = ta - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            else:
+                late = max(late, -delay)
+            j = i % len(pool)
+            c = (i // len(pool)) % out_sets
+            prev = pending.pop((j, c), None)
+            if prev is not None:
+                rc = srv.poll(prev)
+                if rc == lenssim.LENS_ERR_BUSY:
+                    blocked += 1
+                    rc = srv.wait(prev, 600000)
+                codes[rc] += 1
+            rq, b, o = pool[j], inputs[j], outs[j][c]
+            try:
+                if rq.kind == 0:
+                    pending[(j, c)] = srv.submit_image(rq.system, o[0])
+                else:
+                    pending[(j, c)] = srv.submit_loglike(rq.system, b[0], 0.01, 1000.0, b[1], o[0], o[1])
+            except lenssim.LensSimError as e:
+                if e.code != lenssim.LENS_ERR_BUSY:
+                    raise
+                rejected += 1
+        t_submit = time.perf_counter() - t0
+        for t in pending.values():
+            codes[srv.wait(t, 600000)] += 1
+        t_all = time.perf_counter() - t0
+        st = srv.stats()
+        rec = {"rate_req_per_s": rate, "seconds": seconds, "offered": int(len(arrivals)),
+               "submit_seconds": t_submit, "max_submit_lag_s": late, "rejected_busy": rejected,
+               "blocked_reuses": blocked, "admitted": int(sum(codes.values())), "completed_ok": codes.get(0, 0),
+               "failed": {str(k): v for k, v in codes.items() if k != 0},
+               "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "served_req_per_s": st["requests_per_s"],
+               "completed_per_wall_s": codes.get(0, 0) / t_all}
+        if rec["failed"]:
+            rec["last_error"] = srv.last_error()
+        out.append(rec)
+        srv.close()
+    return {"rates": out, "pool": pool_size, "mix": "70% image / 30% likelihood+gradient, grids 64..256 (even), "
+                                                   "s = 1, subhalos log-uniform 0..20000, PSF 5..31"}
+
 def serving_extra(lenssim, W, rates, seconds: float):
     """Open-loop Poisson arrivals (70% image / 30% likelihood+gradient, grids 64..256, subhalos
     0..20,000, PSF 5..31) at each rate: p50/p99 latency (submit to result in host memory) and
@@ -640,7 +725,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, gradient and serving lines")
     ap.add_argument("--variant", type=int, default=-1, help="fixed trace launch variant instead of autotuning")
     ap.add_argument("--extra-only", default="", choices=["", "differentiation", "batched", "batched_small_systems",
-                                                          "fitting", "scaling"],
+                                                          "fitting", "scaling", "serving_full"],
                     help="profiling mode: only this one extra measurement")
     ap.add_argument("--fft-only", type=int, default=0, metavar="N_IMG",
                     help="profiling mode: only the FFT-versus-direct PSF measurement (N_IMG images per call)")
@@ -649,6 +734,9 @@ def main():
     ap.add_argument("--batch-systems", type=int, default=4096)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[300.0, 3000.0, 12000.0])
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-full-rates", type=float, nargs="*",
+                    default=[100.0, 300.0, 1000.0, 3000.0, 10000.0, 20000.0],
+                    help="rates of --extra-only serving_full (10 s each)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -668,7 +756,8 @@ def main():
               "batched": lambda: batched_extra(sim, lenssim, W, dev, args.batch_systems),
               "batched_small_systems": lambda: batched_extra(sim, lenssim, W, dev, args.batch_systems, small=True),
               "fitting": lambda: fitting_extra(sim, W, dev),
-              "scaling": lambda: subhalo_scaling_extra(sim, W, dev)}[args.extra_only]
+              "scaling": lambda: subhalo_scaling_extra(sim, W, dev),
+              "serving_full": lambda: serving_full_extra(lenssim, W, args.serve_full_rates, 10.0)}[args.extra_only]
         print(json.dumps({args.extra_only: fn()}), flush=True)
         sim.close()
         return

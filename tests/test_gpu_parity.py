@@ -170,6 +170,31 @@ def test_substructure_full_size_sampled_rows(sim):
     assert np.abs(got_raw[row2] - raw2[0]).max() / np.abs(raw2).max() <= max(1e-5, 2 * fl2)
 
 
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_substructure_full_size_whole_images(sim, seed):
+    # whole 200x200, s = 3, 10,000-subhalo images with the 21x21 Moffat PSF, the benchmark's
+    # workload and launch configuration, element by element against the oracle
+    system = W.substructure_system(seed)
+    ref = oracle.image(system)
+    tol, floor = image_tol(system, ref)
+    err = rel_linf(gpu_image(sim, system), ref)
+    assert err <= tol, (err, floor)
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5, 6, 7])
+def test_substructure_full_size_row_subsets(sim, seed):
+    # more seeds of the same workload on three unconvolved rows each (top, middle, bottom band);
+    # errors relative to the image's maximum, as for whole images
+    system = W.substructure_system(seed)
+    got = gpu_image(sim, system, use_psf=False)
+    scale = float(np.abs(got).max())
+    for row in (seed, 100 + seed, 199 - seed):
+        ref = oracle.image_rows(system, row, row + 1)
+        fl = float(np.abs(oracle.image_rows(system, row, row + 1, fp32=True) - ref).max()) / scale
+        err = float(np.abs(got[row:row + 1] - ref).max()) / scale
+        assert err <= max(1e-5, 2 * fl), (row, err, fl)
+
 # ----------------------------------------------------------------------------- deflections
 def _points(n, seed, lo=-3.0, hi=3.0):
     rng = np.random.default_rng(seed)
