@@ -11,11 +11,11 @@
 //   g_I  = g_m0 dpix^2/s^2 at each sample of the pixel                 (bin-down spread)
 //   dlogL/dp_src  = sum g_I dI/dp_src
 //   dlogL/dp_lens = sum g_I (-dI/dbeta . dalpha/dp_lens)               (lens equation)
-// The per-sample local Jacobians dalpha_EPL/dp and dI/d(p_src, beta) come from a forward-mode
-// dual type; every reduction is a fixed-order two-stage tree (deterministic).
+// The per-sample local Jacobians dalpha_EPL/dp and dI/d(p_src, beta) are closed forms (the EPL's
+// q and t derivatives as tangent recurrences beside its series); every reduction is a
+// fixed-order two-stage tree (deterministic).
 #include <algorithm>
 
-#include "dual.cuh"
 #include "kernels.h"
 #include "lens_sim.h"
 #include "sim_internal.h"
@@ -23,7 +23,32 @@
 namespace ls {
 
 constexpr int kGradThreads = 256;
-using D6 = Dn<6>;
+// A value and its derivatives along 6 parameters (the per-sample local Jacobians).
+struct Jac6 {
+  float v;
+  float d[6];
+};
+
+__device__ __forceinline__ Jac6 jac_const(float v) {
+  Jac6 r;
+  r.v = v;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) r.d[i] = 0.f;
+  return r;
+}
+
+// Per parameter point, the EPL series coefficients c_n (the division alpha_epl makes) and
+// dc_n/dt = 4n/(2n + 2 - t)^2 for n = 1..kEplTab: t = gamma - 1 is the same for every sample of
+// a point, so each block fills the table once in shared memory instead of dividing per term and
+// sample.  kEplTab covers the longest series (epl_terms <= 200, plus 4 for the tangents).
+constexpr int kEplTab = 256;
+__device__ __forceinline__ void fill_epl_table(const float* P, float2* tab) {
+  const float t = P[1] - 1.f;
+  for (int n = threadIdx.x + 1; n <= kEplTab; n += blockDim.x) {
+    const float inv = 1.f / ((2.f * n + 2.f) - t);
+    tab[n - 1] = make_float2(epl_coef(n, t), 4.f * n * inv * inv);
+  }
+}
 
 // ---------------------------------------------------------------------------- sample geometry
 __device__ __forceinline__ void sample_coords(const DevSystem& g, long long idx, float& x, float& y, int& pix) {
@@ -68,12 +93,13 @@ __global__ void __launch_bounds__(256) subhalo_field_kernel(const __grid_constan
 }
 
 // ---------------------------------------------------------------------------- forward model
-__device__ __forceinline__ float model_sample(float x, float y, float2 asub, const float* __restrict__ P) {
+__device__ __forceinline__ float model_sample(float x, float y, float2 asub, const float* __restrict__ P,
+                                              const float2* __restrict__ tab) {
   float ex, ey;
   {
     float q, phi;
     e1e2_to_qphi(P[2], P[3], q, phi);
-    alpha_epl(x, y, P[0], P[1], q, phi, P[4], P[5], ex, ey);
+    alpha_epl_series(x, y, P[0], P[1], q, phi, P[4], P[5], [tab](int n) { return tab[n - 1].x; }, ex, ey);
   }
   const float bx = x - ex - (P[6] * x + P[7] * y) - asub.x;
   const float by = y - ey - (P[7] * x - P[6] * y) - asub.y;
@@ -87,9 +113,12 @@ __global__ void __launch_bounds__(kGradThreads) forward_model_kernel(const __gri
                                                                      const float2* __restrict__ asub,
                                                                      float* __restrict__ m0, int unit_amp) {
   __shared__ float P[LENS_N_FREE_PARAMS];
+  __shared__ float2 tab[kEplTab];
   const int p = blockIdx.y;
   if (threadIdx.x < LENS_N_FREE_PARAMS) P[threadIdx.x] = params[p * LENS_N_FREE_PARAMS + threadIdx.x];
   if (unit_amp && threadIdx.x == 8) P[8] = 1.f;  // linear solve: the model per unit source amplitude
+  __syncthreads();
+  fill_epl_table(P, tab);
   __syncthreads();
   const int npix = g.nx * g.ny;
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,7 +130,7 @@ __global__ void __launch_bounds__(kGradThreads) forward_model_kernel(const __gri
     float x, y;
     int pp;
     sample_coords(g, idx, x, y, pp);
-    acc += model_sample(x, y, asub[idx], P);
+    acc += model_sample(x, y, asub[idx], P, tab);
   }
   m0[(size_t)p * npix + pix] = acc * (g.dpix * g.dpix / (float)s2);
 }
@@ -160,63 +189,140 @@ __global__ void reduce_partials_kernel(const float* __restrict__ partial, int nb
 }
 
 // ---------------------------------------------------------------------------- local Jacobians
-__device__ __forceinline__ void e1e2_to_qphi_d(const D6& e1, const D6& e2, D6& q, D6& phi) {
-  phi = datan2(e2, e1) * 0.5f;
-  const D6 c = dsqrt(e1 * e1 + e2 * e2);
-  q = (1.f - c) / (1.f + c);
-}
-
-// EPL deflection with tangents along (theta_E, gamma, e1, e2, cx, cy) at a fixed point.
-__device__ __noinline__ void epl_alpha_jac(float x, float y, const float* __restrict__ P, D6& ax, D6& ay) {
-  const D6 thetaE = dvar<6>(P[0], 0), gamma = dvar<6>(P[1], 1);
-  const D6 e1 = dvar<6>(P[2], 2), e2 = dvar<6>(P[3], 3);
-  const D6 cx = dvar<6>(P[4], 4), cy = dvar<6>(P[5], 5);
-  D6 q, phi;
-  e1e2_to_qphi_d(e1, e2, q, phi);
-  const D6 cp = dcos(phi), sp = dsin(phi);
-  const D6 dx = x - cx, dy = y - cy;
-  const D6 xp = cp * dx + sp * dy, yp = sp * (-1.f) * dx + cp * dy;
-  const D6 R = dsqrt(q * q * xp * xp + yp * yp);
-  if (R.v < 1e-12f) { ax = dconst<6>(0.f); ay = dconst<6>(0.f); return; }
-  const D6 t = gamma - 1.f;
-  const D6 b = thetaE * dsqrt(q);
-  const D6 iR = inv(R);
-  const D6 er = q * xp * iR, ei = yp * iR;
-  const D6 f = (1.f - q) / (1.f + q);
-  const D6 zr = -f * (er * er - ei * ei), zi = -f * (2.f * er * ei);
-  D6 omr = er, omi = ei, sr = er, si = ei;
-  const int nt = epl_terms(f.v) + 4;  // tangents converge like n f^(n-1)
+// EPL deflection with tangents along (theta_E, gamma, e1, e2, cx, cy) at a fixed point.  The
+// value is the series of alpha_epl (Tessore & Metcalf 2015); of the tangents only d/dq and d/dt
+// run through the series (two complex tangent recurrences beside it), the rest are closed forms:
+//   theta_E: alpha is proportional to b^t with b = theta_E sqrt(q), so d alpha = t alpha / theta_E;
+//   cx, cy:  minus the Hessian A of the potential; its trace is 2 kappa with
+//            kappa = (2 - t)/2 (b/R)^t, and its shear follows from Euler's relation
+//            x'.grad alpha' = (1 - t) alpha' of a deflection homogeneous of degree 1 - t;
+//   phi:     the frame rotation, d alpha'/dphi = J alpha' - A J x' with J the quarter turn;
+//   e1, e2:  chain rule through q = (1 - c)/(1 + c), c = |e|, phi = atan2(e2, e1)/2.
+__device__ __noinline__ void epl_alpha_jac(float x, float y, const float* __restrict__ P,
+                                          const float2* __restrict__ tab, Jac6& ax, Jac6& ay) {
+  const float thetaE = P[0], t = P[1] - 1.f, e1 = P[2], e2 = P[3];
+  const float c = sqrtf(e1 * e1 + e2 * e2);
+  const float q = (1.f - c) / (1.f + c), phi = 0.5f * atan2f(e2, e1);
+  float sp, cp;
+  sincosf(phi, &sp, &cp);
+  const float dx = x - P[4], dy = y - P[5];
+  const float xp = cp * dx + sp * dy, yp = -sp * dx + cp * dy;
+  const float R = sqrtf(q * q * xp * xp + yp * yp);
+  if (R < 1e-12f) { ax = jac_const(0.f); ay = jac_const(0.f); return; }
+  const float iR = 1.f / R;
+  const float b = thetaE * sqrtf(q);
+  const float er = q * xp * iR, ei = yp * iR;        // e = (q x' + i y') / R
+  const float f = (1.f - q) / (1.f + q);
+  const float e2r = er * er - ei * ei, e2i = 2.f * er * ei;
+  const float zr = -f * e2r, zi = -f * e2i;          // Z = -f e^2
+  const float Rq = q * xp * xp * iR;                 // dR/dq
+  const float eqr = (xp - er * Rq) * iR, eqi = -ei * Rq * iR;  // de/dq
+  const float gq = 2.f / ((1.f + q) * (1.f + q));    // -df/dq
+  const float zqr = gq * e2r - 2.f * f * (er * eqr - ei * eqi);  // dZ/dq = gq e^2 - 2 f e de/dq
+  const float zqi = gq * e2i - 2.f * f * (er * eqi + ei * eqr);
+  float omr = er, omi = ei, sr = er, si = ei;        // Omega_n and its sum
+  float otr = 0.f, oti = 0.f, str = 0.f, sti = 0.f;  // d/dt
+  float oqr = eqr, oqi = eqi, sqr = eqr, sqi = eqi;  // d/dq
+  const int nt = epl_terms(f) + 4;  // tangents converge like n f^(n-1)
   for (int n = 1; n <= nt; ++n) {
-    const D6 coef = ((2.f * n - 2.f) + t) / ((2.f * n + 2.f) - t);
-    const D6 nr = coef * (omr * zr - omi * zi);
-    const D6 ni = coef * (omr * zi + omi * zr);
-    omr = nr;
-    omi = ni;
-    sr = sr + omr;
-    si = si + omi;
+    const float2 cc = tab[n - 1];
+    const float cn = cc.x, cnt = cc.y;  // c_n, dc_n/dt
+    const float zor = omr * zr - omi * zi, zoi = omr * zi + omi * zr;          // Z Omega_{n-1}
+    const float nqr = cn * ((zqr * omr - zqi * omi) + (zr * oqr - zi * oqi));
+    const float nqi = cn * ((zqr * omi + zqi * omr) + (zr * oqi + zi * oqr));
+    const float ntr = cnt * zor + cn * (zr * otr - zi * oti);
+    const float nti = cnt * zoi + cn * (zr * oti + zi * otr);
+    omr = cn * zor;
+    omi = cn * zoi;
+    otr = ntr;
+    oti = nti;
+    oqr = nqr;
+    oqi = nqi;
+    sr += omr;
+    si += omi;
+    str += otr;
+    sti += oti;
+    sqr += oqr;
+    sqi += oqi;
   }
-  const D6 pref = (2.f * b / (1.f + q)) * dexp((t - 1.f) * dlog(b * iR));
-  const D6 apx = pref * sr, apy = pref * si;
-  ax = cp * apx - sp * apy;
-  ay = sp * apx + cp * apy;
+  const float bR = b * iR, lbR = log2f(bR);
+  const float pw = exp2f((t - 1.f) * lbR);           // (b/R)^(t-1)
+  const float pref = 2.f * b / (1.f + q) * pw;
+  const float apx = pref * sr, apy = pref * si;      // alpha' in the lens frame
+  const float ln_bR = lbR * 0.693147180559945f;
+  const float atx = apx * ln_bR + pref * str, aty = apy * ln_bR + pref * sti;
+  const float dlnP = t / (2.f * q) + (1.f - t) * Rq * iR - 1.f / (1.f + q);
+  const float aqx = pref * (dlnP * sr + sqr), aqy = pref * (dlnP * si + sqi);
+  const float kap = 0.5f * (2.f - t) * pw * bR;
+  const float U = (1.f - t) * apx - kap * xp, V = (1.f - t) * apy - kap * yp;
+  const float ir2 = 1.f / (xp * xp + yp * yp);
+  const float g1 = (U * xp - V * yp) * ir2, g2 = (U * yp + V * xp) * ir2;
+  const float a11 = kap + g1, a22 = kap - g1, a12 = g2;
+  const float afx = -apy - (a12 * xp - a11 * yp);    // J alpha' - A J x', J x' = (-y', x')
+  const float afy = apx - (a22 * xp - a12 * yp);
+  auto rot_x = [&](float vx, float vy) { return cp * vx - sp * vy; };
+  auto rot_y = [&](float vx, float vy) { return sp * vx + cp * vy; };
+  ax.v = rot_x(apx, apy);
+  ay.v = rot_y(apx, apy);
+  const float dT = t / thetaE;
+  ax.d[0] = dT * ax.v;
+  ay.d[0] = dT * ay.v;
+  ax.d[1] = rot_x(atx, aty);
+  ay.d[1] = rot_y(atx, aty);
+  const float qx = rot_x(aqx, aqy), qy = rot_y(aqx, aqy), fx = rot_x(afx, afy), fy = rot_y(afx, afy);
+  const float qc = -2.f / ((1.f + c) * (1.f + c)) / c, pc = 0.5f / (c * c);  // dq/dc / c, dphi scale
+  ax.d[2] = qx * qc * e1 - fx * pc * e2;
+  ay.d[2] = qy * qc * e1 - fy * pc * e2;
+  ax.d[3] = qx * qc * e2 + fx * pc * e1;
+  ay.d[3] = qy * qc * e2 + fy * pc * e1;
+  // Hessian in the image frame: columns Rot A Rot^T e_x and Rot A Rot^T e_y; d/dc = -column
+  const float hx1 = a11 * cp - a12 * sp, hx2 = a12 * cp - a22 * sp;   // A Rot^T e_x, Rot^T e_x = (cp, -sp)
+  const float hy1 = a11 * sp + a12 * cp, hy2 = a12 * sp + a22 * cp;   // A Rot^T e_y, Rot^T e_y = (sp, cp)
+  ax.d[4] = -rot_x(hx1, hx2);
+  ay.d[4] = -rot_y(hx1, hx2);
+  ax.d[5] = -rot_x(hy1, hy2);
+  ay.d[5] = -rot_y(hy1, hy2);
 }
 
-// Sersic with tangents along (R_s, n, e1, e2, beta_x, beta_y); dI/damp = I/amp and
+// Sersic with tangents along (R_s, n, e1, e2, beta_x, beta_y), in closed form: with
+// rho = R/R_s, w = rho^(1/n) and ln I = ln amp - b_n (w - 1),
+//   d ln I/dR_s = b_n w / (n R_s),  d ln I/dn = -b_n' (w - 1) + b_n w ln(rho) / n^2,
+//   d ln I/dR = -b_n w / (n R),
+// and R = sqrt(q x'^2 + y'^2/q) differentiated along q, phi (dx'/dphi = y', dy'/dphi = -x'),
+// beta_x and beta_y; e1, e2 -> (q, phi) by the chain rule.  dI/damp = I/amp and
 // dI/dc = -dI/dbeta follow without tangents.
-__device__ __noinline__ D6 sersic_jac(float bx, float by, const float* __restrict__ P) {
-  const D6 Rs = dvar<6>(P[9], 0), n = dvar<6>(P[10], 1);
-  const D6 e1 = dvar<6>(P[11], 2), e2 = dvar<6>(P[12], 3);
-  const D6 Bx = dvar<6>(bx, 4), By = dvar<6>(by, 5);
-  D6 q, phi;
-  e1e2_to_qphi_d(e1, e2, q, phi);
-  const D6 cp = dcos(phi), sp = dsin(phi);
-  const D6 dx = Bx - P[13], dy = By - P[14];
-  const D6 xp = cp * dx + sp * dy, yp = sp * (-1.f) * dx + cp * dy;
-  const D6 R = dsqrt(q * xp * xp + yp * yp / q);
-  const D6 bn = 1.9992f * n - 0.3271f;
-  if (R.v <= 0.f) return dexp(bn) * P[8];
-  const D6 pw = dexp(dlog(R / Rs) / n);
-  return dexp(-bn * (pw - 1.f)) * P[8];
+__device__ __noinline__ Jac6 sersic_jac(float bx, float by, const float* __restrict__ P) {
+  const float Rs = P[9], n = P[10], e1 = P[11], e2 = P[12];
+  const float c = sqrtf(e1 * e1 + e2 * e2);
+  const float q = (1.f - c) / (1.f + c), phi = 0.5f * atan2f(e2, e1);
+  float sp, cp;
+  sincosf(phi, &sp, &cp);
+  const float dx = bx - P[13], dy = by - P[14];
+  const float xp = cp * dx + sp * dy, yp = -sp * dx + cp * dy;
+  const float R = sqrtf(q * xp * xp + yp * yp / q);
+  const float bn = 1.9992f * n - 0.3271f;
+  Jac6 I;
+  if (R <= 0.f) {  // rho^(1/n) = 0: I = amp e^(b_n), which depends on n only
+    I = jac_const(P[8] * expf(bn));
+    I.d[1] = 1.9992f * I.v;
+    return I;
+  }
+  const float in = 1.f / n, lr = log2f(R / Rs);
+  const float w = exp2f(lr * in);
+  I.v = P[8] * expf(-bn * (w - 1.f));
+  const float bw = bn * w * in;
+  const float dR = -bw / R;  // d ln I / dR
+  I.d[0] = I.v * bw / Rs;
+  I.d[1] = I.v * (bw * lr * 0.693147180559945f * in - 1.9992f * (w - 1.f));
+  const float Rx = q * xp / R, Ry = yp / (q * R);          // dR/dx', dR/dy'
+  const float Rq = (xp * xp - yp * yp / (q * q)) / (2.f * R);
+  const float Rphi = Rx * yp - Ry * xp;
+  const float qc = -2.f / ((1.f + c) * (1.f + c)) / c, pc = 0.5f / (c * c);
+  I.d[2] = I.v * dR * (Rq * qc * e1 - Rphi * pc * e2);
+  I.d[3] = I.v * dR * (Rq * qc * e2 + Rphi * pc * e1);
+  I.d[4] = I.v * dR * (Rx * cp - Ry * sp);
+  I.d[5] = I.v * dR * (Rx * sp + Ry * cp);
+  return I;
 }
 
 __global__ void __launch_bounds__(kGradThreads) backward_kernel(const __grid_constant__ DevSystem g,
@@ -225,8 +331,11 @@ __global__ void __launch_bounds__(kGradThreads) backward_kernel(const __grid_con
                                                                 const float* __restrict__ gm0,
                                                                 float* __restrict__ partial, int nblk) {
   __shared__ float P[LENS_N_FREE_PARAMS];
+  __shared__ float2 tab[kEplTab];
   const int p = blockIdx.y;
   if (threadIdx.x < LENS_N_FREE_PARAMS) P[threadIdx.x] = params[p * LENS_N_FREE_PARAMS + threadIdx.x];
+  __syncthreads();
+  fill_epl_table(P, tab);
   __syncthreads();
   const int npix = g.nx * g.ny;
   const int s2 = g.s * g.s;
@@ -241,12 +350,12 @@ __global__ void __launch_bounds__(kGradThreads) backward_kernel(const __grid_con
     int pix;
     sample_coords(g, idx, x, y, pix);
     const float gI = gm0[(size_t)p * npix + pix] * w;
-    D6 ax, ay;
-    epl_alpha_jac(x, y, P, ax, ay);
+    Jac6 ax, ay;
+    epl_alpha_jac(x, y, P, tab, ax, ay);
     const float2 as = asub[idx];
     const float bx = x - ax.v - (P[6] * x + P[7] * y) - as.x;
     const float by = y - ay.v - (P[7] * x - P[6] * y) - as.y;
-    const D6 I = sersic_jac(bx, by, P);
+    const Jac6 I = sersic_jac(bx, by, P);
     const float dIdbx = I.d[4], dIdby = I.d[5];
     // lens parameters: beta = theta - alpha  ->  dI/dp = -(dI/dbx dax/dp + dI/dby day/dp)
 #pragma unroll

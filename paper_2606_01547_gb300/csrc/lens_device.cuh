@@ -110,8 +110,11 @@ __device__ __forceinline__ int epl_terms(float f) {
   return n < 1 ? 1 : (n > 200 ? 200 : n);
 }
 
-static __device__ __noinline__ void alpha_epl(float x, float y, float thetaE, float gamma, float q, float phi,
-                                       float cx, float cy, float& ax, float& ay) {
+// The EPL series with its coefficients c_n = (2n - 2 + t)/(2n + 2 - t) taken from `coef(n)`:
+// computed in place here, read from a per-point table by the likelihood kernels.
+template <class Coef>
+__device__ __forceinline__ void alpha_epl_series(float x, float y, float thetaE, float gamma, float q, float phi,
+                                                 float cx, float cy, Coef coef, float& ax, float& ay) {
   float sp, cp;
   sincosf(phi, &sp, &cp);
   float dx = x - cx, dy = y - cy, xp, yp;
@@ -127,9 +130,9 @@ static __device__ __noinline__ void alpha_epl(float x, float y, float thetaE, fl
   float omr = er, omi = ei, sr = er, si = ei;
   const int nt = epl_terms(f);
   for (int n = 1; n <= nt; ++n) {
-    float coef = (2.f * n - 2.f + t) / (2.f * n + 2.f - t);
-    float nr = coef * (omr * zr - omi * zi);
-    float ni = coef * (omr * zi + omi * zr);
+    const float c = coef(n);
+    float nr = c * (omr * zr - omi * zi);
+    float ni = c * (omr * zi + omi * zr);
     omr = nr; omi = ni;
     sr += omr; si += omi;
   }
@@ -137,6 +140,14 @@ static __device__ __noinline__ void alpha_epl(float x, float y, float thetaE, fl
   float apx = pref * sr, apy = pref * si;
   ax = cp * apx - sp * apy;
   ay = sp * apx + cp * apy;
+}
+
+__device__ __forceinline__ float epl_coef(int n, float t) { return (2.f * n - 2.f + t) / (2.f * n + 2.f - t); }
+
+static __device__ __noinline__ void alpha_epl(float x, float y, float thetaE, float gamma, float q, float phi,
+                                       float cx, float cy, float& ax, float& ay) {
+  const float t = gamma - 1.f;
+  alpha_epl_series(x, y, thetaE, gamma, q, phi, cx, cy, [t](int n) { return epl_coef(n, t); }, ax, ay);
 }
 
 // ---------------------------------------------------------------------------- NFW / TNFW
