@@ -23,6 +23,13 @@
 namespace ls {
 
 constexpr int kGradThreads = 256;
+// Samples (pixels in the forward model) per thread of the per-point kernels: each block fills
+// its EPL table and reduces its partial sums once, so a few samples per thread amortise that.
+constexpr int kWorkPerThread = 4;
+inline int blocks_per_point(long long n_work) {
+  return (int)std::max<long long>(1, std::min<long long>((n_work + kGradThreads * kWorkPerThread - 1) /
+                                                            (kGradThreads * kWorkPerThread), 64));
+}
 // A value and its derivatives along 6 parameters (the per-sample local Jacobians).
 struct Jac6 {
   float v;
@@ -121,18 +128,18 @@ __global__ void __launch_bounds__(kGradThreads) forward_model_kernel(const __gri
   fill_epl_table(P, tab);
   __syncthreads();
   const int npix = g.nx * g.ny;
-  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pix >= npix) return;
   const int s2 = g.s * g.s;
-  float acc = 0.f;
-  for (int k = 0; k < s2; ++k) {
-    const long long idx = (long long)pix * s2 + k;
-    float x, y;
-    int pp;
-    sample_coords(g, idx, x, y, pp);
-    acc += model_sample(x, y, asub[idx], P, tab);
+  for (int pix = blockIdx.x * blockDim.x + threadIdx.x; pix < npix; pix += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int k = 0; k < s2; ++k) {
+      const long long idx = (long long)pix * s2 + k;
+      float x, y;
+      int pp;
+      sample_coords(g, idx, x, y, pp);
+      acc += model_sample(x, y, asub[idx], P, tab);
+    }
+    m0[(size_t)p * npix + pix] = acc * (g.dpix * g.dpix / (float)s2);
   }
-  m0[(size_t)p * npix + pix] = acc * (g.dpix * g.dpix / (float)s2);
 }
 
 // ---------------------------------------------------------------------------- block reduction
@@ -495,7 +502,7 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
   const int npix = nx * ny;
   const long long n_samples = (long long)npix * ss * ss;
   const int nblk_l = (npix + kGradThreads - 1) / kGradThreads;
-  const int nblk_b = (int)std::min<long long>((n_samples + kGradThreads - 1) / kGradThreads, 64);
+  const int nblk_b = blocks_per_point(n_samples);
   // workspace: alpha_sub | m0 | m | g_m | g_m0 | partials (per point chunk)
   const size_t sub_bytes = ((size_t)n_samples * sizeof(float2) + 255) & ~(size_t)255;
   const size_t per_point = 4 * (size_t)npix * sizeof(float) +
@@ -530,7 +537,7 @@ extern "C" int lens_sim_grad(lens_sim* s, const lens_system* sys, const float* d
   for (int p0 = 0; p0 < n_points; p0 += chunk) {
     const int np = std::min(chunk, n_points - p0);
     const float* P = params + (size_t)p0 * LENS_N_FREE_PARAMS;
-    forward_model_kernel<<<dim3((npix + kGradThreads - 1) / kGradThreads, np), kGradThreads, 0, st>>>(d, P, asub, m0, 0);
+    forward_model_kernel<<<dim3(blocks_per_point(npix), np), kGradThreads, 0, st>>>(d, P, asub, m0, 0);
     if (psf) e = psf_step(s, m0, m, np, ny, nx, psf, 0, st);
     else e = cudaMemcpyAsync(m, m0, sizeof(float) * (size_t)np * npix, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "model convolution");
@@ -605,7 +612,7 @@ extern "C" int lens_sim_linear_amp(lens_sim* s, const lens_system* sys, const fl
   for (int p0 = 0; p0 < n_points; p0 += chunk) {
     const int np = std::min(chunk, n_points - p0);
     const float* P = params + (size_t)p0 * LENS_N_FREE_PARAMS;
-    forward_model_kernel<<<dim3(nblk, np), kGradThreads, 0, st>>>(d, P, asub, m0, 1);
+    forward_model_kernel<<<dim3(blocks_per_point(npix), np), kGradThreads, 0, st>>>(d, P, asub, m0, 1);
     if (psf) e = psf_step(s, m0, m1, np, ny, nx, psf, 0, st);
     else e = cudaMemcpyAsync(m1, m0, sizeof(float) * (size_t)np * npix, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "model convolution");

@@ -238,9 +238,7 @@ class Simulator:
         c = LensSystemC()
         c.grid = LensGrid(int(g.nx), int(g.ny), int(g.s), float(g.dpix), float(g.x0), float(g.y0))
         nd = len(system.deflectors)
-        if nd > MAX_DEFLECTORS:
-            raise ValueError("too many deflectors")
-        arr = (LensProfile * max(nd, 1))()
+        arr = (LensProfile * max(nd, 1))()  # the library checks nd against LENS_MAX_DEFLECTORS
         for i, (name, vals) in enumerate(system.deflectors):
             arr[i] = profile_struct(name, vals)
         keep.append(arr)

@@ -121,6 +121,40 @@ def test_degenerate_inputs_match_oracle(sim):
         assert err <= tol, (system.deflectors, err, floor)
 
 
+
+def test_maximum_sizes_match_oracle(sim):
+    # the most deflectors a system takes (8, every kind of closed form at once), the widest grid
+    # (16,384 columns) and 100,000 subhalos on a small grid
+    base = W.substructure_system(80, n_sub=200, nx=40, s=2, k=7)
+    eight = [base.deflectors[0], base.deflectors[1], ("SIS", [0.1, 0.3, -0.2]), ("NFW", [0.4, 0.05, -0.3, 0.2]),
+             ("POINT_MASS", [0.05, 0.2, 0.25]), ("MULTIPOLE", [4, 0.02, 0.2, 0.0, 0.0, 0.9]),
+             ("CSE", [0.05, 0.2, 0.2, -0.1, 0.1, 0.0]), ("SIE", [0.1, 0.8, 0.3, -0.25, 0.1])]
+    wide_src = W.substructure_system(81, n_sub=30, nx=8, s=1, k=5)
+    many_src = W.substructure_system(82, n_sub=100000, nx=8, s=1, k=3)
+    cases = [W.LensSystem(base.grid, eight, base.subhalos, base.source, base.psf),
+             W.LensSystem(W.Grid(16384, 2, 1, W.f32(0.0005)), wide_src.deflectors, wide_src.subhalos,
+                          wide_src.source, wide_src.psf),
+             W.LensSystem(W.Grid(16, 16, 1, W.f32(0.25)), many_src.deflectors, many_src.subhalos,
+                          many_src.source, many_src.psf)]
+    for system in cases:
+        ref = oracle.image(system)
+        tol, floor = image_tol(system, ref)
+        err = rel_linf(gpu_image(sim, system), ref)
+        assert err <= tol, (system.grid, len(system.deflectors), system.n_sub, err, floor)
+
+
+def test_sizes_beyond_the_limits_are_rejected(sim):
+    from paper_2606_01547_gb300 import lenssim
+    base = W.plain_system()
+    nine = base.deflectors + [("SIS", [0.01, 0.0, 0.0])] * 7
+    bad = [W.LensSystem(base.grid, nine, base.subhalos, base.source, base.psf),
+           W.LensSystem(W.Grid(16385, 2, 1, 0.05), base.deflectors, base.subhalos, base.source, base.psf),
+           W.LensSystem(base.grid, base.deflectors, base.subhalos, base.source, W.gaussian_psf(0.1, 0.05, 137))]
+    for b in bad:
+        with pytest.raises(lenssim.LensSimError) as ei:
+            sim.image(b)
+        assert ei.value.code == lenssim.LENS_ERR_INVALID_ARG
+
 def test_image_path_with_largest_psf_matches_oracle(sim):
     # k = 135 (the paper's largest kernel) through the single-image path; auto takes the FFT
     base = W.substructure_system(70, n_sub=100, nx=60, s=1, k=0)
