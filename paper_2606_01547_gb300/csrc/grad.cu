@@ -71,34 +71,6 @@ __device__ __forceinline__ void sample_coords(const DevSystem& g, long long idx,
   pix = i * g.nx + j;
 }
 
-// Fixed subhalo deflection at every sample (sample order: row, column, sub-row, sub-column).
-__global__ void __launch_bounds__(256) subhalo_field_kernel(const __grid_constant__ DevSystem sys,
-                                                            float2* __restrict__ out, long long n_samples) {
-  __shared__ float4 s_sub[8][32][kSubStride];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long first = (long long)blockIdx.x * blockDim.x + w * 32;
-  if (first >= n_samples) return;
-  const long long idx = first + lane;
-  float px = 0.f, py = 0.f;
-  int pix;
-  if (idx < n_samples) sample_coords(sys, idx, px, py, pix);
-  float ax = 0.f, ay = 0.f;
-  const float4* __restrict__ mid_tab = sys.sub + (size_t)kSubStride * sys.n_sub;
-  for (int base = 0; base < sys.n_sub; base += 32) {
-    const int t = base + lane;
-    if (t < sys.n_sub) {
-#pragma unroll
-      for (int c = 0; c < kSubStride; ++c) s_sub[w][lane][c] = __ldg(sys.sub + (size_t)kSubStride * t + c);
-    }
-    __syncwarp();
-    const int cnt = min(32, sys.n_sub - base);
-    for (int q = 0; q < cnt; ++q)
-      tnfw_pair(px, py, s_sub[w][q], mid_tab + (size_t)kMidStride * (base + q), ax, ay);
-    __syncwarp();
-  }
-  if (idx < n_samples) out[idx] = make_float2(ax, ay);
-}
-
 // ---------------------------------------------------------------------------- forward model
 __device__ __forceinline__ float model_sample(float x, float y, float2 asub, const float* __restrict__ P,
                                               const float2* __restrict__ tab) {
@@ -205,7 +177,7 @@ __global__ void reduce_partials_kernel(const float* __restrict__ partial, int nb
 //            x'.grad alpha' = (1 - t) alpha' of a deflection homogeneous of degree 1 - t;
 //   phi:     the frame rotation, d alpha'/dphi = J alpha' - A J x' with J the quarter turn;
 //   e1, e2:  chain rule through q = (1 - c)/(1 + c), c = |e|, phi = atan2(e2, e1)/2.
-__device__ __noinline__ void epl_alpha_jac(float x, float y, const float* __restrict__ P,
+__device__ __forceinline__ void epl_alpha_jac(float x, float y, const float* __restrict__ P,
                                           const float2* __restrict__ tab, Jac6& ax, Jac6& ay) {
   const float thetaE = P[0], t = P[1] - 1.f, e1 = P[2], e2 = P[3];
   const float c = sqrtf(e1 * e1 + e2 * e2);
@@ -298,7 +270,7 @@ __device__ __noinline__ void epl_alpha_jac(float x, float y, const float* __rest
 // and R = sqrt(q x'^2 + y'^2/q) differentiated along q, phi (dx'/dphi = y', dy'/dphi = -x'),
 // beta_x and beta_y; e1, e2 -> (q, phi) by the chain rule.  dI/damp = I/amp and
 // dI/dc = -dI/dbeta follow without tangents.
-__device__ __noinline__ Jac6 sersic_jac(float bx, float by, const float* __restrict__ P) {
+__device__ __forceinline__ Jac6 sersic_jac(float bx, float by, const float* __restrict__ P) {
   const float Rs = P[9], n = P[10], e1 = P[11], e2 = P[12];
   const float c = sqrtf(e1 * e1 + e2 * e2);
   const float q = (1.f - c) / (1.f + c), phi = 0.5f * atan2f(e2, e1);
@@ -332,7 +304,9 @@ __device__ __noinline__ Jac6 sersic_jac(float bx, float by, const float* __restr
   return I;
 }
 
-__global__ void __launch_bounds__(kGradThreads) backward_kernel(const __grid_constant__ DevSystem g,
+// Three blocks per SM (24 warps): the series recurrences are latency-bound chains, and the
+// extra warps hide more of that latency than the few spilled registers cost.
+__global__ void __launch_bounds__(kGradThreads, 3) backward_kernel(const __grid_constant__ DevSystem g,
                                                                 const float* __restrict__ params,
                                                                 const float2* __restrict__ asub,
                                                                 const float* __restrict__ gm0,
@@ -436,8 +410,7 @@ namespace ls {
 static int subhalo_field(lens_sim* s, const lens_system& y, const DevSystem& d, long long n_samples,
                          float2* scratch, cudaStream_t st, float2** out) {
   if (y.subhalo_table < 0) {
-    subhalo_field_kernel<<<(unsigned)((n_samples + 255) / 256), 256, 0, st>>>(d, scratch, n_samples);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_subhalo_field(d, scratch, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "subhalo field");
     *out = scratch;
     return LENS_OK;
@@ -456,8 +429,7 @@ static int subhalo_field(lens_sim* s, const lens_system& y, const DevSystem& d, 
   if (s->sub_field.p != before) s->field_key = lens_sim::FieldKey{};  // reallocated: contents gone
   *out = (float2*)s->sub_field.p;
   if (s->field_key == key) return LENS_OK;
-  subhalo_field_kernel<<<(unsigned)((n_samples + 255) / 256), 256, 0, st>>>(d, *out, n_samples);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_subhalo_field(d, *out, st);
   if (e != cudaSuccess) return cuda_fail(s, e, "subhalo field");
   s->field_key = key;
   return LENS_OK;

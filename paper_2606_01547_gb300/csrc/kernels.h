@@ -56,7 +56,7 @@ int unit_count(int nx, int ny, int s);
 // Fused ray-trace + subhalo sum + Sersic + supersample bin-down of one system into sys.out.
 cudaError_t launch_trace(const DevSystem& sys, TraceShape shape, cudaStream_t st);
 // The same with an explicit launch variant (all variants give bitwise-identical images):
-// 0 one CTA of 8 warps per unit, 1 the same capped at 80 registers (3 CTAs per SM),
+// 0 one CTA of 8 warps per unit, 1 one CTA of 4 warps summing the 8 slices in two passes,
 // 2 a cluster of 2 CTAs x 4 warps per unit, 3 a cluster of 4 CTAs x 2 warps per unit,
 // 4 a cluster of 8 single-warp CTAs per unit.
 constexpr int kTraceVariants = 5;
@@ -67,6 +67,10 @@ const char* trace_variant_name(int v);
 // ([n_sys + 1] ints) and handed out through *counter (zeroed before the launch).
 int trace_batch_grid(int sm_count);
 cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int grid, cudaStream_t st);
+
+// Summed subhalo deflection at every sample of the grid (main deflectors excluded), in the
+// order ((row * nx + column) * s + sub-row) * s + sub-column; the same sum as the image kernels.
+cudaError_t launch_subhalo_field(const DevSystem& sys, float2* out, cudaStream_t st);
 
 // Total deflection at n device points.
 cudaError_t launch_deflection(const DevSystem& sys, const float* x, const float* y, int n, float* ax,

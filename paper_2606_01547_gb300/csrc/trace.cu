@@ -338,6 +338,34 @@ __global__ void __launch_bounds__(32 * kTraceWarps, MINB) trace_image_kernel(con
   trace_unit(sys, blockIdx.x, sm);
 }
 
+// Subhalo deflection field of a grid (the likelihood's fixed field): the units, slices and
+// packed pair loop of the image kernels, then each sample's 8 slice partials summed in slice
+// order and stored at out[((i * nx + j) * s + a) * s + b] for sub-sample (a, b) of pixel (i, j).
+__global__ void __launch_bounds__(32 * kTraceWarps, 2) subhalo_field_kernel(const __grid_constant__ DevSystem sys,
+                                                                            float2* __restrict__ out) {
+  __shared__ TraceSmem<kTraceWarps> sm;
+  const UnitGeom g = unit_geom(sys, blockIdx.x);
+  unit_partials<kTraceWarps>(sys, g, 0, sm);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 32 * kUnitPts; idx += 32 * kTraceWarps) {
+    const int k = idx >> 5, l = idx & 31;
+    const int q = l * kUnitPts + k;
+    if (q >= g.nsamp) continue;
+    const int p = q / g.s2, sub = q - p * g.s2;
+    const int a = sub / g.s, b = sub - a * g.s;
+    const int i = g.by * g.bh + p / g.bw, j = g.bx * g.bw + p % g.bw;
+    if (i >= sys.ny || j >= sys.nx) continue;
+    float sx = 0.f, sy = 0.f;
+#pragma unroll
+    for (int sl = 0; sl < kTraceWarps; ++sl) {
+      const float2 v = sm.wa[sl].part[k][l];
+      sx += v.x;
+      sy += v.y;
+    }
+    out[(((size_t)i * sys.nx + j) * g.s + a) * g.s + b] = make_float2(sx, sy);
+  }
+}
+
 // Two-pass form: a CTA of kTraceWarps/2 warps sums the 8 slices in two passes (warp w takes
 // slices w and w + 4) into the same per-slice areas, then reduces them in slice order like the
 // one-CTA form, so its images are bitwise the same; the smaller CTA fits three per SM.
@@ -440,6 +468,11 @@ cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t
     case 4: trace_cluster_kernel<8><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
     default: trace_image_kernel<2><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_subhalo_field(const DevSystem& sys, float2* out, cudaStream_t st) {
+  subhalo_field_kernel<<<unit_count(sys.nx, sys.ny, sys.s), 32 * kTraceWarps, 0, st>>>(sys, out);
   return cudaGetLastError();
 }
 
