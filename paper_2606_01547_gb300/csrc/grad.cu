@@ -57,6 +57,42 @@ __device__ __forceinline__ void fill_epl_table(const float* P, float2* tab) {
   }
 }
 
+// Per parameter point: the lens and source frames and the adjoint's chain-rule factors, the
+// same for every sample of the point, so each block computes them once in shared memory.
+struct PointFrame {
+  EplFrame lens;
+  SersicFrame src;
+  float l_qc, l_pc;  // lens e1, e2 -> (q, phi): (dq/dc)/c and 1/(2 c^2), c = |e|
+  float l_gq;        // -df/dq = 2/(1 + q)^2
+  float l_dT;        // t / theta_E
+  float l_k0;        // t/(2q) - 1/(1 + q), the point-independent part of d ln(prefactor)/dq
+  float s_qc, s_pc;  // the same for the source ellipticity
+  float s_in;        // 1/n
+  int nt_adj;        // series terms of the adjoint: f^n <= 1e-7 with two more for the tangents'
+                     // n f^(n-1) (the value's own count, epl_terms, goes to 1.5e-8)
+};
+
+__device__ __forceinline__ void point_frame(const float* P, PointFrame& F) {
+  float q, phi;
+  e1e2_to_qphi(P[2], P[3], q, phi);
+  F.lens = epl_frame(P[0], P[1], q, phi);
+  const float lc = sqrtf(P[2] * P[2] + P[3] * P[3]);
+  F.l_qc = -2.f / ((1.f + lc) * (1.f + lc)) / lc;
+  F.l_pc = 0.5f / (lc * lc);
+  F.l_gq = 2.f / ((1.f + q) * (1.f + q));
+  F.l_dT = F.lens.t / P[0];
+  F.l_k0 = F.lens.t / (2.f * q) - 1.f / (1.f + q);
+  const float f = F.lens.f;
+  F.nt_adj = f < 1e-20f ? 0 : min((int)ceilf(-16.2f / logf(f)) + 2, kEplTab);
+  float qs, phis;
+  e1e2_to_qphi(P[11], P[12], qs, phis);
+  F.src = sersic_frame(P[8], P[9], P[10], qs, phis, P[13], P[14]);
+  const float sc = sqrtf(P[11] * P[11] + P[12] * P[12]);
+  F.s_qc = -2.f / ((1.f + sc) * (1.f + sc)) / sc;
+  F.s_pc = 0.5f / (sc * sc);
+  F.s_in = 1.f / P[10];
+}
+
 // ---------------------------------------------------------------------------- sample geometry
 __device__ __forceinline__ void sample_coords(const DevSystem& g, long long idx, float& x, float& y, int& pix) {
   const int s = g.s;
@@ -73,18 +109,12 @@ __device__ __forceinline__ void sample_coords(const DevSystem& g, long long idx,
 
 // ---------------------------------------------------------------------------- forward model
 __device__ __forceinline__ float model_sample(float x, float y, float2 asub, const float* __restrict__ P,
-                                              const float2* __restrict__ tab) {
+                                              const PointFrame& F, const float2* __restrict__ tab) {
   float ex, ey;
-  {
-    float q, phi;
-    e1e2_to_qphi(P[2], P[3], q, phi);
-    alpha_epl_series(x, y, P[0], P[1], q, phi, P[4], P[5], [tab](int n) { return tab[n - 1].x; }, ex, ey);
-  }
+  alpha_epl_at(x, y, F.lens, P[4], P[5], [tab](int n) { return tab[n - 1].x; }, ex, ey);
   const float bx = x - ex - (P[6] * x + P[7] * y) - asub.x;
   const float by = y - ey - (P[7] * x - P[6] * y) - asub.y;
-  float q, phi;
-  e1e2_to_qphi(P[11], P[12], q, phi);
-  return sersic(bx, by, P[8], P[9], P[10], q, phi, P[13], P[14]);
+  return sersic_at(bx, by, F.src);
 }
 
 __global__ void __launch_bounds__(kGradThreads) forward_model_kernel(const __grid_constant__ DevSystem g,
@@ -93,11 +123,13 @@ __global__ void __launch_bounds__(kGradThreads) forward_model_kernel(const __gri
                                                                      float* __restrict__ m0, int unit_amp) {
   __shared__ float P[LENS_N_FREE_PARAMS];
   __shared__ float2 tab[kEplTab];
+  __shared__ PointFrame F;
   const int p = blockIdx.y;
   if (threadIdx.x < LENS_N_FREE_PARAMS) P[threadIdx.x] = params[p * LENS_N_FREE_PARAMS + threadIdx.x];
   if (unit_amp && threadIdx.x == 8) P[8] = 1.f;  // linear solve: the model per unit source amplitude
   __syncthreads();
   fill_epl_table(P, tab);
+  if (threadIdx.x == 0) point_frame(P, F);
   __syncthreads();
   const int npix = g.nx * g.ny;
   const int s2 = g.s * g.s;
@@ -108,7 +140,7 @@ __global__ void __launch_bounds__(kGradThreads) forward_model_kernel(const __gri
       float x, y;
       int pp;
       sample_coords(g, idx, x, y, pp);
-      acc += model_sample(x, y, asub[idx], P, tab);
+      acc += model_sample(x, y, asub[idx], P, F, tab);
     }
     m0[(size_t)p * npix + pix] = acc * (g.dpix * g.dpix / (float)s2);
   }
@@ -177,32 +209,28 @@ __global__ void reduce_partials_kernel(const float* __restrict__ partial, int nb
 //            x'.grad alpha' = (1 - t) alpha' of a deflection homogeneous of degree 1 - t;
 //   phi:     the frame rotation, d alpha'/dphi = J alpha' - A J x' with J the quarter turn;
 //   e1, e2:  chain rule through q = (1 - c)/(1 + c), c = |e|, phi = atan2(e2, e1)/2.
-__device__ __forceinline__ void epl_alpha_jac(float x, float y, const float* __restrict__ P,
-                                          const float2* __restrict__ tab, Jac6& ax, Jac6& ay) {
-  const float thetaE = P[0], t = P[1] - 1.f, e1 = P[2], e2 = P[3];
-  const float c = sqrtf(e1 * e1 + e2 * e2);
-  const float q = (1.f - c) / (1.f + c), phi = 0.5f * atan2f(e2, e1);
-  float sp, cp;
-  sincosf(phi, &sp, &cp);
+__device__ __forceinline__ void epl_alpha_jac(float x, float y, const float* __restrict__ P, const PointFrame& F,
+                                              const float2* __restrict__ tab, Jac6& ax, Jac6& ay) {
+  const float t = F.lens.t, e1 = P[2], e2 = P[3];
+  const float q = F.lens.q, cp = F.lens.cp, sp = F.lens.sp;
   const float dx = x - P[4], dy = y - P[5];
   const float xp = cp * dx + sp * dy, yp = -sp * dx + cp * dy;
   const float R = sqrtf(q * q * xp * xp + yp * yp);
   if (R < 1e-12f) { ax = jac_const(0.f); ay = jac_const(0.f); return; }
   const float iR = 1.f / R;
-  const float b = thetaE * sqrtf(q);
+  const float b = F.lens.b, f = F.lens.f;
   const float er = q * xp * iR, ei = yp * iR;        // e = (q x' + i y') / R
-  const float f = (1.f - q) / (1.f + q);
   const float e2r = er * er - ei * ei, e2i = 2.f * er * ei;
   const float zr = -f * e2r, zi = -f * e2i;          // Z = -f e^2
   const float Rq = q * xp * xp * iR;                 // dR/dq
   const float eqr = (xp - er * Rq) * iR, eqi = -ei * Rq * iR;  // de/dq
-  const float gq = 2.f / ((1.f + q) * (1.f + q));    // -df/dq
+  const float gq = F.l_gq;                           // -df/dq
   const float zqr = gq * e2r - 2.f * f * (er * eqr - ei * eqi);  // dZ/dq = gq e^2 - 2 f e de/dq
   const float zqi = gq * e2i - 2.f * f * (er * eqi + ei * eqr);
   float omr = er, omi = ei, sr = er, si = ei;        // Omega_n and its sum
   float otr = 0.f, oti = 0.f, str = 0.f, sti = 0.f;  // d/dt
   float oqr = eqr, oqi = eqi, sqr = eqr, sqi = eqi;  // d/dq
-  const int nt = epl_terms(f) + 4;  // tangents converge like n f^(n-1)
+  const int nt = F.nt_adj;
   for (int n = 1; n <= nt; ++n) {
     const float2 cc = tab[n - 1];
     const float cn = cc.x, cnt = cc.y;  // c_n, dc_n/dt
@@ -226,11 +254,11 @@ __device__ __forceinline__ void epl_alpha_jac(float x, float y, const float* __r
   }
   const float bR = b * iR, lbR = log2f(bR);
   const float pw = exp2f((t - 1.f) * lbR);           // (b/R)^(t-1)
-  const float pref = 2.f * b / (1.f + q) * pw;
+  const float pref = F.lens.b2q * pw;
   const float apx = pref * sr, apy = pref * si;      // alpha' in the lens frame
   const float ln_bR = lbR * 0.693147180559945f;
   const float atx = apx * ln_bR + pref * str, aty = apy * ln_bR + pref * sti;
-  const float dlnP = t / (2.f * q) + (1.f - t) * Rq * iR - 1.f / (1.f + q);
+  const float dlnP = F.l_k0 + (1.f - t) * Rq * iR;
   const float aqx = pref * (dlnP * sr + sqr), aqy = pref * (dlnP * si + sqi);
   const float kap = 0.5f * (2.f - t) * pw * bR;
   const float U = (1.f - t) * apx - kap * xp, V = (1.f - t) * apy - kap * yp;
@@ -243,13 +271,13 @@ __device__ __forceinline__ void epl_alpha_jac(float x, float y, const float* __r
   auto rot_y = [&](float vx, float vy) { return sp * vx + cp * vy; };
   ax.v = rot_x(apx, apy);
   ay.v = rot_y(apx, apy);
-  const float dT = t / thetaE;
+  const float dT = F.l_dT;
   ax.d[0] = dT * ax.v;
   ay.d[0] = dT * ay.v;
   ax.d[1] = rot_x(atx, aty);
   ay.d[1] = rot_y(atx, aty);
   const float qx = rot_x(aqx, aqy), qy = rot_y(aqx, aqy), fx = rot_x(afx, afy), fy = rot_y(afx, afy);
-  const float qc = -2.f / ((1.f + c) * (1.f + c)) / c, pc = 0.5f / (c * c);  // dq/dc / c, dphi scale
+  const float qc = F.l_qc, pc = F.l_pc;  // (dq/dc)/c, dphi/de scale
   ax.d[2] = qx * qc * e1 - fx * pc * e2;
   ay.d[2] = qy * qc * e1 - fy * pc * e2;
   ax.d[3] = qx * qc * e2 + fx * pc * e1;
@@ -270,23 +298,20 @@ __device__ __forceinline__ void epl_alpha_jac(float x, float y, const float* __r
 // and R = sqrt(q x'^2 + y'^2/q) differentiated along q, phi (dx'/dphi = y', dy'/dphi = -x'),
 // beta_x and beta_y; e1, e2 -> (q, phi) by the chain rule.  dI/damp = I/amp and
 // dI/dc = -dI/dbeta follow without tangents.
-__device__ __forceinline__ Jac6 sersic_jac(float bx, float by, const float* __restrict__ P) {
-  const float Rs = P[9], n = P[10], e1 = P[11], e2 = P[12];
-  const float c = sqrtf(e1 * e1 + e2 * e2);
-  const float q = (1.f - c) / (1.f + c), phi = 0.5f * atan2f(e2, e1);
-  float sp, cp;
-  sincosf(phi, &sp, &cp);
+__device__ __forceinline__ Jac6 sersic_jac(float bx, float by, const float* __restrict__ P, const PointFrame& F) {
+  const float Rs = P[9], e1 = P[11], e2 = P[12];
+  const float q = F.src.q, cp = F.src.cp, sp = F.src.sp;
   const float dx = bx - P[13], dy = by - P[14];
   const float xp = cp * dx + sp * dy, yp = -sp * dx + cp * dy;
   const float R = sqrtf(q * xp * xp + yp * yp / q);
-  const float bn = 1.9992f * n - 0.3271f;
+  const float bn = F.src.bn;
   Jac6 I;
   if (R <= 0.f) {  // rho^(1/n) = 0: I = amp e^(b_n), which depends on n only
     I = jac_const(P[8] * expf(bn));
     I.d[1] = 1.9992f * I.v;
     return I;
   }
-  const float in = 1.f / n, lr = log2f(R / Rs);
+  const float in = F.s_in, lr = log2f(R / Rs);
   const float w = exp2f(lr * in);
   I.v = P[8] * expf(-bn * (w - 1.f));
   const float bw = bn * w * in;
@@ -296,7 +321,7 @@ __device__ __forceinline__ Jac6 sersic_jac(float bx, float by, const float* __re
   const float Rx = q * xp / R, Ry = yp / (q * R);          // dR/dx', dR/dy'
   const float Rq = (xp * xp - yp * yp / (q * q)) / (2.f * R);
   const float Rphi = Rx * yp - Ry * xp;
-  const float qc = -2.f / ((1.f + c) * (1.f + c)) / c, pc = 0.5f / (c * c);
+  const float qc = F.s_qc, pc = F.s_pc;
   I.d[2] = I.v * dR * (Rq * qc * e1 - Rphi * pc * e2);
   I.d[3] = I.v * dR * (Rq * qc * e2 + Rphi * pc * e1);
   I.d[4] = I.v * dR * (Rx * cp - Ry * sp);
@@ -313,10 +338,12 @@ __global__ void __launch_bounds__(kGradThreads, 3) backward_kernel(const __grid_
                                                                 float* __restrict__ partial, int nblk) {
   __shared__ float P[LENS_N_FREE_PARAMS];
   __shared__ float2 tab[kEplTab];
+  __shared__ PointFrame F;
   const int p = blockIdx.y;
   if (threadIdx.x < LENS_N_FREE_PARAMS) P[threadIdx.x] = params[p * LENS_N_FREE_PARAMS + threadIdx.x];
   __syncthreads();
   fill_epl_table(P, tab);
+  if (threadIdx.x == 0) point_frame(P, F);
   __syncthreads();
   const int npix = g.nx * g.ny;
   const int s2 = g.s * g.s;
@@ -332,11 +359,11 @@ __global__ void __launch_bounds__(kGradThreads, 3) backward_kernel(const __grid_
     sample_coords(g, idx, x, y, pix);
     const float gI = gm0[(size_t)p * npix + pix] * w;
     Jac6 ax, ay;
-    epl_alpha_jac(x, y, P, tab, ax, ay);
+    epl_alpha_jac(x, y, P, F, tab, ax, ay);
     const float2 as = asub[idx];
     const float bx = x - ax.v - (P[6] * x + P[7] * y) - as.x;
     const float by = y - ay.v - (P[7] * x - P[6] * y) - as.y;
-    const Jac6 I = sersic_jac(bx, by, P);
+    const Jac6 I = sersic_jac(bx, by, P, F);
     const float dIdbx = I.d[4], dIdby = I.d[5];
     // lens parameters: beta = theta - alpha  ->  dI/dp = -(dI/dbx dax/dp + dI/dby day/dp)
 #pragma unroll

@@ -110,44 +110,61 @@ __device__ __forceinline__ int epl_terms(float f) {
   return n < 1 ? 1 : (n > 200 ? 200 : n);
 }
 
-// The EPL series with its coefficients c_n = (2n - 2 + t)/(2n + 2 - t) taken from `coef(n)`:
-// computed in place here, read from a per-point table by the likelihood kernels.
+// EPL (Tessore & Metcalf 2015): the quantities of one lens that do not depend on the point
+// (its frame), and the deflection at a point from them, with the series coefficients
+// c_n = (2n - 2 + t)/(2n + 2 - t) taken from `coef(n)`: computed in place by alpha_epl, read
+// from a per-point table by the likelihood kernels (which also keep one frame per point).
+struct EplFrame {
+  float cp, sp;  // cos, sin of the position angle
+  float q, t;    // axis ratio, gamma - 1
+  float b, f;    // theta_E sqrt(q), (1 - q)/(1 + q)
+  float b2q;     // 2 b / (1 + q)
+  int nt;        // series terms
+};
+
+__device__ __forceinline__ EplFrame epl_frame(float thetaE, float gamma, float q, float phi) {
+  EplFrame e;
+  sincosf(phi, &e.sp, &e.cp);
+  e.q = q;
+  e.t = gamma - 1.f;
+  e.b = thetaE * sqrtf(q);
+  e.f = (1.f - q) / (1.f + q);
+  e.b2q = 2.f * e.b / (1.f + q);
+  e.nt = epl_terms(e.f);
+  return e;
+}
+
 template <class Coef>
-__device__ __forceinline__ void alpha_epl_series(float x, float y, float thetaE, float gamma, float q, float phi,
-                                                 float cx, float cy, Coef coef, float& ax, float& ay) {
-  float sp, cp;
-  sincosf(phi, &sp, &cp);
+__device__ __forceinline__ void alpha_epl_at(float x, float y, const EplFrame& e, float cx, float cy, Coef coef,
+                                             float& ax, float& ay) {
   float dx = x - cx, dy = y - cy, xp, yp;
-  to_frame(dx, dy, cp, sp, xp, yp);
-  float R = sqrtf(q * q * xp * xp + yp * yp);
+  to_frame(dx, dy, e.cp, e.sp, xp, yp);
+  float R = sqrtf(e.q * e.q * xp * xp + yp * yp);
   if (R < 1e-12f) { ax = 0.f; ay = 0.f; return; }
-  float t = gamma - 1.f;
-  float b = thetaE * sqrtf(q);
   float iR = 1.f / R;
-  float er = q * xp * iR, ei = yp * iR;
-  float f = (1.f - q) / (1.f + q);
-  float zr = -f * (er * er - ei * ei), zi = -f * (2.f * er * ei);
+  float er = e.q * xp * iR, ei = yp * iR;
+  float zr = -e.f * (er * er - ei * ei), zi = -e.f * (2.f * er * ei);
   float omr = er, omi = ei, sr = er, si = ei;
-  const int nt = epl_terms(f);
-  for (int n = 1; n <= nt; ++n) {
+  for (int n = 1; n <= e.nt; ++n) {
     const float c = coef(n);
     float nr = c * (omr * zr - omi * zi);
     float ni = c * (omr * zi + omi * zr);
     omr = nr; omi = ni;
     sr += omr; si += omi;
   }
-  float pref = 2.f * b / (1.f + q) * exp2f((t - 1.f) * log2f(b * iR));
+  float pref = e.b2q * exp2f((e.t - 1.f) * log2f(e.b * iR));
   float apx = pref * sr, apy = pref * si;
-  ax = cp * apx - sp * apy;
-  ay = sp * apx + cp * apy;
+  ax = e.cp * apx - e.sp * apy;
+  ay = e.sp * apx + e.cp * apy;
 }
 
 __device__ __forceinline__ float epl_coef(int n, float t) { return (2.f * n - 2.f + t) / (2.f * n + 2.f - t); }
 
 static __device__ __noinline__ void alpha_epl(float x, float y, float thetaE, float gamma, float q, float phi,
                                        float cx, float cy, float& ax, float& ay) {
-  const float t = gamma - 1.f;
-  alpha_epl_series(x, y, thetaE, gamma, q, phi, cx, cy, [t](int n) { return epl_coef(n, t); }, ax, ay);
+  const EplFrame e = epl_frame(thetaE, gamma, q, phi);
+  const float t = e.t;
+  alpha_epl_at(x, y, e, cx, cy, [t](int n) { return epl_coef(n, t); }, ax, ay);
 }
 
 // ---------------------------------------------------------------------------- NFW / TNFW
@@ -699,16 +716,36 @@ static __device__ __noinline__ void alpha_profile(const DevProfile& P, float x, 
 }
 
 // ---------------------------------------------------------------------------- Sersic source
+// Elliptical Sersic: the profile's point-independent quantities and its value at a point.
+struct SersicFrame {
+  float amp, Rs, n, q, cp, sp, bn, cx, cy;
+};
+
+__device__ __forceinline__ SersicFrame sersic_frame(float amp, float Rs, float n, float q, float phi, float cx,
+                                                    float cy) {
+  SersicFrame f;
+  sincosf(phi, &f.sp, &f.cp);
+  f.amp = amp;
+  f.Rs = Rs;
+  f.n = n;
+  f.q = q;
+  f.bn = 1.9992f * n - 0.3271f;
+  f.cx = cx;
+  f.cy = cy;
+  return f;
+}
+
+__device__ __forceinline__ float sersic_at(float x, float y, const SersicFrame& f) {
+  float xp, yp;
+  to_frame(x - f.cx, y - f.cy, f.cp, f.sp, xp, yp);
+  float R = sqrtf(f.q * xp * xp + yp * yp / f.q);
+  float pw = exp2f(log2f(R / f.Rs) / f.n);
+  return f.amp * expf(-f.bn * (pw - 1.f));
+}
+
 __device__ __forceinline__ float sersic(float x, float y, float amp, float Rs, float n, float q, float phi,
                                         float cx, float cy) {
-  float sp, cp;
-  sincosf(phi, &sp, &cp);
-  float xp, yp;
-  to_frame(x - cx, y - cy, cp, sp, xp, yp);
-  float R = sqrtf(q * xp * xp + yp * yp / q);
-  float bn = 1.9992f * n - 0.3271f;
-  float pw = exp2f(log2f(R / Rs) / n);
-  return amp * expf(-bn * (pw - 1.f));
+  return sersic_at(x, y, sersic_frame(amp, Rs, n, q, phi, cx, cy));
 }
 
 // Cartesian shapelets: the orthonormal Hermite functions phi_n(u) by their normalised
