@@ -136,6 +136,7 @@ def test_budget_refusal_and_a_bad_request_fails_alone(lenssim):
     srv.pause(False)
     assert srv.wait(t1) == lenssim.LENS_OK
     assert srv.wait(t2) == lenssim.LENS_ERR_INVALID_ARG
+    assert "q" in srv.last_error(), srv.last_error()  # the library's message for the bad axis ratio
     assert srv.wait(t3) == lenssim.LENS_OK
     np.testing.assert_array_equal(o1, o3)
     srv.close()
