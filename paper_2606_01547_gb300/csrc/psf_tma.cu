@@ -2,8 +2,10 @@
 // double-buffered kernel whose input tiles arrive by TMA (cp.async.bulk.tensor) into shared
 // memory, completion tracked by an mbarrier.
 //
-// Each CTA computes 64x32-output tiles; its input box is (64 + k - 1) rows of the tile plus
-// halo, with the left edge rounded down to a 16-byte boundary (TMA needs an aligned x) and
+// Each CTA computes tiles of 64 x 32 outputs (64 x 64 for k <= 7), or for images 65..128
+// columns wide one tile across the whole row (one thread per 4 columns: no columns computed
+// past the edge); its input box is the tile plus the k - 1 halo, with the left edge rounded
+// down to a 16-byte boundary (TMA needs an aligned x) and
 // out-of-image elements zero-filled by the TMA unit, which is exactly the zero padding of the
 // 'same' convolution.  While one tile is computed the next is in flight.  A thread owns 2x4
 // outputs: per kernel row it reads float4 windows of the two input rows it needs, so shared
@@ -25,19 +27,14 @@ namespace ls {
 
 namespace {
 
-constexpr int kTW = 64;        // output tile width
-constexpr int kThreads = 256;  // 16 x 16 threads, each 4 columns x rows_per_thread(K) rows
+constexpr int kThreads = 256;  // at most; 16 x 16 threads by default, each 4 columns x rows_per_thread(K) rows
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 // Small kernels (k <= 7, the HBM-bound regime) use 4 output rows per thread (64x64 tiles) with the
 // weights in registers; larger kernels (FP32-bound) use 2 rows (64x32 tiles).
 constexpr int rows_per_thread(int K) { return K <= 7 ? 4 : 2; }
-constexpr int tile_h(int K) { return 16 * rows_per_thread(K); }
 constexpr int cpad(int K) { return ((K - 1) / 2 + 3) / 4 * 4; }   // left halo rounded up to 4
 constexpr int coff(int K) { return cpad(K) - (K - 1) / 2; }        // tile column of the first tap
-constexpr int box_w(int K) { return (coff(K) + kTW + K - 1 + 3) / 4 * 4; }
-constexpr int box_h(int K) { return tile_h(K) + K - 1; }
-constexpr int tile_floats(int K) { return (box_w(K) * box_h(K) + 31) / 32 * 32; }  // 128-byte multiple
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -89,7 +86,11 @@ struct TmaConvArgs {
   float* out;
   const float* K;
   int nx, ny, n_img, tiles_x, tiles_y;
-  int* err;  // host-mapped flag, raised when a bounded wait expires
+  int tx_n;     // threads across a tile (4 output columns each)
+  int tw, th;   // tile width and height in outputs
+  int bw, bh;   // input box (shared-memory tile) width and height
+  int tile_fl;  // floats per shared-memory tile buffer (a 128-byte multiple)
+  int* err;     // host-mapped flag, raised when a bounded wait expires
 };
 
 // out[2x? rows][4 cols] of one thread from the tile in shared memory.  Small K: every input row
@@ -97,9 +98,9 @@ struct TmaConvArgs {
 // the weights in registers; large K: per kernel row, the two input rows, weights row hoisted.
 template <int K>
 __device__ __forceinline__ void conv_tile_compute(const float* __restrict__ T, const float* __restrict__ sK,
-                                                  const float (&kreg)[K <= 7 ? K * K : 1], int tx, int ty,
+                                                  const float (&kreg)[K <= 7 ? K * K : 1], int tx, int ty, int BW,
                                                   float (&acc)[rows_per_thread(K)][4]) {
-  constexpr int R = rows_per_thread(K), BW = box_w(K), OFF = coff(K);
+  constexpr int R = rows_per_thread(K), OFF = coff(K);
   constexpr int NV = (OFF + 4 + K - 1 + 3) / 4;  // float4 per window row
 #pragma unroll
   for (int rr = 0; rr < R; ++rr)
@@ -158,16 +159,17 @@ __device__ __forceinline__ void conv_tile_compute(const float* __restrict__ T, c
 template <int K>
 __global__ void __launch_bounds__(kThreads) conv_tma_kernel(const __grid_constant__ CUtensorMap tin,
                                                            const TmaConvArgs A) {
-  constexpr int BW = box_w(K), BH = box_h(K), C = (K - 1) / 2, R = rows_per_thread(K), TH = tile_h(K);
-  constexpr unsigned kBytes = BW * BH * sizeof(float);
+  constexpr int C = (K - 1) / 2, R = rows_per_thread(K);
+  const int TW = A.tw, TH = A.th;
+  const unsigned kBytes = (unsigned)(A.bw * A.bh) * sizeof(float);
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* tile0 = (float*)smem_raw;
-  float* tile1 = tile0 + tile_floats(K);
-  float* sK = tile1 + tile_floats(K);
+  float* tile1 = tile0 + A.tile_fl;
+  float* sK = tile1 + A.tile_fl;
   __shared__ __align__(8) unsigned long long bars[2];
 
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int q = tid; q < K * K; q += kThreads) sK[q] = A.K[K * K - 1 - q];  // flipped: out = sum sK . window
+  const int tid = threadIdx.x, tx = tid % A.tx_n, ty = tid / A.tx_n;
+  for (int q = tid; q < K * K; q += blockDim.x) sK[q] = A.K[K * K - 1 - q];  // flipped: out = sum sK . window
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) conv_tma_kernel(const __grid_constan
   auto issue = [&](long long t, int s) {
     const int z = (int)(t / per_img);
     const int r = (int)(t - (long long)z * per_img);
-    const int i0 = (r / A.tiles_x) * TH, j0 = (r % A.tiles_x) * kTW;
+    const int i0 = (r / A.tiles_x) * TH, j0 = (r % A.tiles_x) * TW;
     mbar_expect_tx(&bars[s], kBytes);
     tma_load_3d(s ? tile1 : tile0, &tin, j0 - cpad(K), i0 - C, z, &bars[s]);
   };
@@ -211,9 +213,9 @@ __global__ void __launch_bounds__(kThreads) conv_tma_kernel(const __grid_constan
     }
     const int z = (int)(t / per_img);
     const int r = (int)(t - (long long)z * per_img);
-    const int i0 = (r / A.tiles_x) * TH, j0 = (r % A.tiles_x) * kTW;
+    const int i0 = (r / A.tiles_x) * TH, j0 = (r % A.tiles_x) * TW;
     float acc[R][4];
-    conv_tile_compute<K>(s ? tile1 : tile0, sK, kreg, tx, ty, acc);
+    conv_tile_compute<K>(s ? tile1 : tile0, sK, kreg, tx, ty, A.bw, acc);
     const int j = j0 + 4 * tx;
     if (j < A.nx) {
 #pragma unroll
@@ -226,11 +228,6 @@ __global__ void __launch_bounds__(kThreads) conv_tma_kernel(const __grid_constan
     }
     __syncthreads();  // the buffer is refilled two tiles later
   }
-}
-
-template <int K>
-size_t tma_smem_bytes() {
-  return sizeof(float) * ((size_t)2 * tile_floats(K) + (size_t)K * K);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -253,41 +250,56 @@ cudaError_t launch_k(const float* in, float* out, int n_img, int ny, int nx, con
                      cudaStream_t st) {
   auto enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
+  constexpr int R = rows_per_thread(K);
+  TmaConvArgs A;
+  // tile shape: 16 x 16 threads (64-column tiles), or for rows of 65..128 columns one thread per
+  // 4 columns across the whole row (nx % 4 == 0 here) and as many thread rows as fit 256 threads
+  A.tx_n = 16;
+  int ty_n = 16;
+  if (nx > 64 && nx <= 128) {
+    A.tx_n = nx / 4;
+    ty_n = kThreads / A.tx_n;
+  }
+  A.tw = 4 * A.tx_n;
+  A.th = ty_n * R;
+  A.bw = (coff(K) + A.tw + K - 1 + 3) / 4 * 4;
+  A.bh = A.th + K - 1;
+  A.tile_fl = (A.bw * A.bh + 31) / 32 * 32;
   CUtensorMap map;
   std::memset(&map, 0, sizeof(map));
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)n_img};
   const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)box_w(K), (cuuint32_t)box_h(K), 1};
+  const cuuint32_t box[3] = {(cuuint32_t)A.bw, (cuuint32_t)A.bh, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)in, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const size_t smem = tma_smem_bytes<K>();
-  static thread_local bool configured = false;
-  if (!configured) {
+  const size_t smem = sizeof(float) * ((size_t)2 * A.tile_fl + (size_t)K * K);
+  const int threads = A.tx_n * ty_n;
+  static thread_local size_t configured = 0;  // the largest dynamic shared memory enabled so far
+  if (smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured = smem;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<K>, kThreads, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<K>, threads, smem) != cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
-  TmaConvArgs A;
   A.out = out;
   A.K = Kw;
   A.nx = nx;
   A.ny = ny;
   A.n_img = n_img;
-  A.tiles_x = (nx + kTW - 1) / kTW;
-  A.tiles_y = (ny + tile_h(K) - 1) / tile_h(K);
+  A.tiles_x = (nx + A.tw - 1) / A.tw;
+  A.tiles_y = (ny + A.th - 1) / A.th;
   A.err = err;
   const long long total = (long long)A.tiles_x * A.tiles_y * n_img;
   const int grid = (int)std::min<long long>(total, (long long)sm_count * per_sm);
-  conv_tma_kernel<K><<<grid, kThreads, smem, st>>>(map, A);
+  conv_tma_kernel<K><<<grid, threads, smem, st>>>(map, A);
   return cudaGetLastError();
 }
 

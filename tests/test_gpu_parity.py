@@ -344,22 +344,25 @@ def test_tma_convolution_matches_oracle(sim, k, ny, nx, n):
         assert rel_linf(out[i], oracle.convolve(imgs[i], K)) < 2e-6, i
 
 
-def test_tma_and_generic_convolution_agree_bitwise(sim):
-    # the same image through the TMA path (aligned) and the generic path (offset by one float)
-    rng = np.random.default_rng(7)
-    base = torch.from_numpy(rng.random((1, 64 * 65 + 1)).astype(np.float32)).cuda()
-    K = rng.random((9, 9)).astype(np.float32)
-    a = sim.convolve(base[:, :64 * 64].reshape(1, 64, 64).contiguous(), K)
-    b_in = base[:, 1:64 * 64 + 1]  # 4-byte offset: not 16-byte aligned -> generic kernel
-    b = torch.empty((1, 64, 64), device="cuda")
+@pytest.mark.parametrize("n,k", [(64, 9), (100, 13), (100, 5), (128, 31), (68, 3)])
+def test_tma_and_generic_convolution_agree_bitwise(sim, n, k):
+    # the same image through the TMA path (aligned; 64-column tiles, or whole-row tiles for
+    # 65..128 columns) and the generic path (offset by one float)
+    rng = np.random.default_rng(7 + n + k)
+    base = torch.from_numpy(rng.random((1, n * (n + 1) + 1)).astype(np.float32)).cuda()
+    K = rng.random((k, k)).astype(np.float32)
+    aligned = base[:, 1:n * n + 1].clone().reshape(1, n, n)  # fresh allocation: 16-byte aligned -> TMA
+    assert aligned.data_ptr() % 16 == 0
+    a = sim.convolve(aligned, K)
+    b_in = base[:, 1:n * n + 1]  # 4-byte offset: not 16-byte aligned -> generic kernel
+    assert b_in.data_ptr() % 16 != 0
+    b = torch.empty((1, n, n), device="cuda")
     from paper_2606_01547_gb300 import lenssim
     pid = sim.register_psf(K)
-    lenssim.lib().lens_sim_convolve(sim.h, b_in.data_ptr(), 1, 64, 64, pid, b.data_ptr(),
+    lenssim.lib().lens_sim_convolve(sim.h, b_in.data_ptr(), 1, n, n, pid, b.data_ptr(),
                                     int(torch.cuda.current_stream().cuda_stream))
-    ref_b = sim.convolve(base[:, 1:64 * 64 + 1].reshape(1, 64, 64).contiguous(), K)
     torch.cuda.synchronize()
-    np.testing.assert_array_equal(b.cpu().numpy(), ref_b.cpu().numpy())
-    assert a.shape == b.shape
+    np.testing.assert_array_equal(b.cpu().numpy(), a.cpu().numpy())
 
 
 @pytest.mark.parametrize("k,ny,nx,n", [(45, 60, 60, 2), (135, 180, 180, 1), (75, 97, 131, 3), (3, 17, 23, 1),
