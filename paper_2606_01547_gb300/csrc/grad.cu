@@ -47,7 +47,8 @@ __device__ __forceinline__ Jac6 jac_const(float v) {
 // Per parameter point, the EPL series coefficients c_n (the division alpha_epl makes) and
 // dc_n/dt = 4n/(2n + 2 - t)^2 for n = 1..kEplTab: t = gamma - 1 is the same for every sample of
 // a point, so each block fills the table once in shared memory instead of dividing per term and
-// sample.  kEplTab covers the longest series (epl_terms <= 200, plus 4 for the tangents).
+// sample.  kEplTab covers the longest series (epl_terms <= 200; the adjoint's own count is
+// capped at kEplTab).
 constexpr int kEplTab = 256;
 __device__ __forceinline__ void fill_epl_table(const float* P, float2* tab) {
   const float t = P[1] - 1.f;
