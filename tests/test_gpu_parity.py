@@ -486,9 +486,13 @@ def test_invalid_arguments_are_rejected(sim):
     assert rel_linf(gpu_image(sim, base), oracle.image(base)) <= 1e-5
 
 
-def test_trace_variants_are_bitwise_identical_and_autotune_picks_one(sim):
+@pytest.mark.parametrize("s,nx,ny,nsub", [(3, 45, 45, 1500), (1, 50, 27, 900), (2, 31, 40, 1200), (5, 17, 9, 300)])
+def test_trace_variants_are_bitwise_identical_and_autotune_picks_one(sim, s, nx, ny, nsub):
+    # every launch variant on each unit shape (24x12 pixels at s = 1, 12x6 at s = 2, 8x4 at s = 3,
+    # 5x2 at s = 5), grids with ragged unit rows and columns
     from paper_2606_01547_gb300 import lenssim
-    system = W.substructure_system(41, n_sub=1500, nx=45, s=3, k=7)
+    base = W.substructure_system(41 + s, n_sub=nsub, nx=8, s=s, k=7)
+    system = W.LensSystem(W.Grid(nx, ny, s, base.grid.dpix), base.deflectors, base.subhalos, base.source, base.psf)
     imgs = []
     for v in range(len(lenssim.TRACE_VARIANTS)):
         sim.set_variant(v)
