@@ -61,13 +61,13 @@ def lbfgs_fit(sim: lenssim.Simulator, system: W.LensSystem, data: torch.Tensor, 
                 loss = (Z * 0.0).sum() + 1e30
                 loss.backward()
                 return loss
-            total = float(L.sum())
+            total = float(L.detach().sum())
             if total > best["total"]:
                 best["total"] = total
                 best["P"] = (Z * sc).detach().clone()
             loss = -L.sum()
             loss.backward()
-            history.append(float(L.max()))
+            history.append(float(L.detach().max()))
             return loss
         return closure
 
