@@ -30,3 +30,12 @@ def test_warmup_below_three_is_refused():
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "2"],
                          cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert out.returncode != 0
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    # under torchrun only rank 0 runs and prints the reference line; the others exit 0 at once
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "2",
+                          "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert not [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
