@@ -122,7 +122,7 @@ constexpr double kLn2 = 0.69314718055994530942;
 // Profile type codes of this oracle's C interface (its own numbering).
 enum { O_SIS = 0, O_SIE = 1, O_EPL = 2, O_SHEAR = 3, O_POINT_MASS = 4, O_NFW = 5,
        O_TNFW = 6, O_EPL_E1E2 = 7, O_SIE_E1E2 = 8, O_MULTIPOLE = 9, O_EPL_MULTIPOLE_M1M3M4 = 10,
-       O_CSE = 11, O_NFW_ELLIPSE_CSE = 12, O_HERNQUIST_ELLIPSE_CSE = 13 };
+       O_CSE = 11, O_NFW_ELLIPSE_CSE = 12, O_HERNQUIST_ELLIPSE_CSE = 13, O_MULTIPOLE_ELL = 14 };
 enum { O_SERSIC_ELLIPSE_Q_PHI = 0, O_SERSIC_ELLIPSE = 1, O_SERSIC = 2, O_SHAPELETS = 3 };
 
 // ---------------------------------------------------------------------------
@@ -452,6 +452,92 @@ inline void alpha_hernquist_ellipse(double x, double y, double sigma0, double Rs
   alpha_elliptical(kap, x, y, q, phi, cx, cy, 1e-15 * std::fabs(sigma0), ax, ay);
 }
 
+// Elliptical multipole of order m (deflection table row MULTIPOLE_ELL).
+// reading: in the frame of an ellipse of axis ratio q and position angle phi_e about (cx, cy),
+//   kappa = r_E a_m cos(m (varphi - phi_m')) / (2 R),  R^2 = q x''^2 + y''^2 / q,
+// varphi = atan2(y'' / sqrt(q), x'' sqrt(q)) the elliptical angle, phi_m' = phi_m - phi_e;
+// parameters m, a_m, phi_m, q, phi_e, cx, cy, r_E.  q = 1 is the circular multipole above.
+// kappa r depends on the polar angle theta alone: with h(theta) = 2 kappa r and its Fourier
+// coefficients c_k, the potential is psi = r F(theta) + (1/2) r ln(r / r_E) h_1(theta), where
+// F = sum_{k != +-1} c_k e^{i k theta} / (1 - k^2) solves F + F'' = h - h_1 and the k = +-1 part
+// h_1 (present for odd m) is carried by the r ln r term, whose Laplacian is h_1 / r; so
+// laplacian(psi) = h / r = 2 kappa.  alpha = grad psi.  The c_k come from the trapezoid rule on
+// kEllN points, which converges geometrically for this analytic periodic h (its singularities
+// lie at |Im theta| = atanh(q)); kept up to order m + 256 (q >= 0.2).
+constexpr int kEllN = 4096;
+struct EllCoef {
+  int m = -1;
+  double q = -1.0, dphi = 0.0;
+  int K = 0;
+  std::vector<double> re, im;  // c_k / (a_m r_E), k = 0..K
+};
+
+inline const EllCoef& ell_coefficients(int m, double q, double dphi) {
+  static thread_local EllCoef c;
+  if (c.m == m && c.q == q && c.dphi == dphi) return c;
+  c.m = m;
+  c.q = q;
+  c.dphi = dphi;
+  c.K = std::min(m + 256, kEllN / 4);
+  std::vector<double> h(kEllN), cs(kEllN), sn(kEllN);
+  const double sq = std::sqrt(q);
+  for (int j = 0; j < kEllN; ++j) {
+    const double th = 2.0 * kPi * j / kEllN;
+    cs[j] = std::cos(th);
+    sn[j] = std::sin(th);
+    const double g = std::sqrt(q * cs[j] * cs[j] + sn[j] * sn[j] / q);  // R / r
+    const double vphi = std::atan2(sn[j] / sq, sq * cs[j]);
+    h[j] = std::cos(m * (vphi - dphi)) / g;                             // 2 kappa r / (a_m r_E)
+  }
+  c.re.assign(c.K + 1, 0.0);
+  c.im.assign(c.K + 1, 0.0);
+  for (int k = 0; k <= c.K; ++k) {
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < kEllN; ++j) {
+      const int idx = (int)(((long long)k * j) % kEllN);
+      sr += h[j] * cs[idx];
+      si -= h[j] * sn[idx];
+    }
+    c.re[k] = sr / kEllN;
+    c.im[k] = si / kEllN;
+  }
+  return c;
+}
+
+inline void alpha_multipole_ell(double x, double y, int m, double am, double phim, double q, double phie,
+                                double cx, double cy, double rE, double& ax, double& ay) {
+  const double ce = std::cos(phie), se = std::sin(phie);
+  const double dx = x - cx, dy = y - cy;
+  const double xp = ce * dx + se * dy, yp = -se * dx + ce * dy;
+  const double r = std::sqrt(xp * xp + yp * yp);
+  if (r < 1e-12) { ax = 0.0; ay = 0.0; return; }
+  const EllCoef& c = ell_coefficients(m, q, phim - phie);
+  const double s = am * rE;
+  const double cth = xp / r, sth = yp / r;
+  // F and F' from the harmonics k = 0 and 2..K (h real: c_{-k} = conj(c_k))
+  double F = c.re[0], Fd = 0.0;
+  double zr = cth, zi = sth;  // e^{i k theta}, k = 1
+  for (int k = 2; k <= c.K; ++k) {
+    const double nr = zr * cth - zi * sth, ni = zr * sth + zi * cth;
+    zr = nr;
+    zi = ni;
+    const double w = 2.0 / (1.0 - (double)k * k);
+    const double pr = c.re[k] * zr - c.im[k] * zi;  // Re(c_k e^{ik theta})
+    const double pi = c.re[k] * zi + c.im[k] * zr;  // Im(c_k e^{ik theta})
+    F += w * pr;
+    Fd -= w * k * pi;
+  }
+  // the resonant part h_1 = A cos(theta) + B sin(theta)
+  const double A = 2.0 * c.re[1], B = -2.0 * c.im[1];
+  const double h1 = A * cth + B * sth, h1d = -A * sth + B * cth;
+  const double L = std::log(r / rE);
+  const double ar = s * (F + 0.5 * (L + 1.0) * h1);
+  const double at = s * (Fd + 0.5 * L * h1d);
+  const double axp = ar * cth - at * sth, ayp = ar * sth + at * cth;
+  ax = ce * axp - se * ayp;
+  ay = se * axp + ce * ayp;
+}
+
 // Dispatch one profile; p holds the profile's parameters in the order of its layout.
 template <class T>
 int alpha_profile(int type, const T* p, const T& x, const T& y, T& ax, T& ay) {
@@ -495,6 +581,17 @@ int alpha_profile(int type, const T* p, const T& x, const T& y, T& ax, T& ay) {
         if (!(p[0] == p[0]) || !(p[1] > 0.0)) return -1;
         double q, phi; e1e2_to_qphi<double>(p[2], p[3], q, phi);
         alpha_cse(x, y, p[0], p[1], q, phi, p[4], p[5], ax, ay); return 0;
+      } else {
+        return -1;
+      }
+    }
+    case O_MULTIPOLE_ELL: {
+      if constexpr (std::is_same<T, double>::value) {
+        const int m = (int)std::lround(p[0]);
+        if (m < 1 || m > 32 || std::fabs(p[0] - m) > 1e-6 || !(p[3] >= 0.2 && p[3] <= 1.0) || !(p[7] > 0.0))
+          return -1;
+        alpha_multipole_ell(x, y, m, p[1], p[2], p[3], p[4], p[5], p[6], p[7], ax, ay);
+        return 0;
       } else {
         return -1;
       }

@@ -680,3 +680,73 @@ def test_hernquist_round_enclosed_mass():
     np.testing.assert_allclose(ax, ref, rtol=1e-11)
     assert np.abs(ay).max() < 1e-15
     assert abs(mp.quad(lambda t: kh(t) * t, [0, 1, 10, mp.inf]) - 1) < 1e-12
+
+
+# ----------------------------------------------------------------------------- elliptical multipoles
+def _kappa_multipole_ell(x, y, m, am, phim, q, phie, cx, cy, rE):
+    # reading: r_E a_m cos(m (varphi - (phi_m - phi_e))) / (2 R) in the ellipse frame,
+    # R^2 = q x''^2 + y''^2 / q, varphi = atan2(y'' / sqrt(q), x'' sqrt(q))
+    dx, dy = x - cx, y - cy
+    xp = math.cos(phie) * dx + math.sin(phie) * dy
+    yp = -math.sin(phie) * dx + math.cos(phie) * dy
+    R = np.sqrt(q * xp * xp + yp * yp / q)
+    vphi = np.arctan2(yp / math.sqrt(q), xp * math.sqrt(q))
+    return rE * am * np.cos(m * (vphi - (phim - phie))) / (2.0 * R)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 6])
+def test_elliptical_multipole_round_limit_is_the_circular_multipole(m):
+    # q = 1: the ellipse orientation drops out and the mode is the circular multipole, whose
+    # oracle (complex powers of the direction) is pinned above
+    x, y = _pts(300, 70 + m, -2.0, 2.0)
+    circ = oracle.alpha("MULTIPOLE", [m, 0.06, 0.35, 0.1, -0.2, 1.2], x, y)
+    ell = oracle.alpha("MULTIPOLE_ELL", [m, 0.06, 0.35, 1.0, 0.9, 0.1, -0.2, 1.2], x, y)
+    scale = np.abs(np.concatenate(circ)).max()
+    assert np.abs(ell[0] - circ[0]).max() < 1e-12 * scale
+    assert np.abs(ell[1] - circ[1]).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("m,q", [(1, 0.6), (2, 0.5), (3, 0.8), (4, 0.7), (4, 0.25), (7, 0.55)])
+def test_elliptical_multipole_divergence_is_twice_kappa_and_curl_free(m, q):
+    p = [m, 0.05, 0.7, q, -0.4, 0.05, 0.1, 1.1]
+    x, y = _pts(300, 80 + m, -2.5, 2.5)
+    keep = np.hypot(x - 0.05, y - 0.1) > 0.2
+    x, y = x[keep], y[keep]
+    div, curl = _fd_div_curl("MULTIPOLE_ELL", p, x, y, 1e-5)
+    k = _kappa_multipole_ell(x, y, *p)
+    scale = np.abs(2 * k).max()
+    assert np.abs(div - 2 * k).max() < 1e-7 * scale
+    assert np.abs(curl).max() < 1e-7 * scale
+
+
+def test_elliptical_multipole_rotates_with_its_angles():
+    # turning the ellipse and the multipole phase by t turns the deflection field by t
+    p = [3, 0.04, 0.3, 0.6, 1.1, 0.0, 0.0, 1.0]
+    x, y = _pts(100, 91, -1.5, 1.5)
+    a = oracle.alpha("MULTIPOLE_ELL", p, x, y)
+    t = 0.7
+    c, s = math.cos(t), math.sin(t)
+    q = list(p); q[2] += t; q[4] += t
+    b = oracle.alpha("MULTIPOLE_ELL", q, c * x - s * y, s * x + c * y)
+    np.testing.assert_allclose(b[0], c * a[0] - s * a[1], atol=1e-13)
+    np.testing.assert_allclose(b[1], s * a[0] + c * a[1], atol=1e-13)
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_elliptical_multipole_even_orders_are_scale_free(m):
+    # for even m, 2 kappa r is unchanged under theta -> theta + pi, so it has no k = +-1
+    # harmonic: the potential is r F(theta) and alpha is homogeneous of degree 0 in r
+    p = [m, 0.05, 0.2, 0.55, 0.3, 0.0, 0.0, 1.3]
+    x, y = _pts(100, 95 + m, -1.5, 1.5)
+    a1 = oracle.alpha("MULTIPOLE_ELL", p, x, y)
+    a2 = oracle.alpha("MULTIPOLE_ELL", p, 3.1 * x, 3.1 * y)
+    np.testing.assert_allclose(a2[0], a1[0], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(a2[1], a1[1], rtol=0, atol=1e-14)
+
+
+def test_elliptical_multipole_rejects_out_of_range_parameters():
+    x, y = _pts(4, 3)
+    for bad in ([0, 0.05, 0.0, 0.6, 0.0, 0.0, 0.0, 1.0], [2.5, 0.05, 0.0, 0.6, 0.0, 0.0, 0.0, 1.0],
+                [2, 0.05, 0.0, 0.1, 0.0, 0.0, 0.0, 1.0], [2, 0.05, 0.0, 0.6, 0.0, 0.0, 0.0, 0.0]):
+        with pytest.raises(ValueError):
+            oracle.alpha("MULTIPOLE_ELL", bad, x, y)
