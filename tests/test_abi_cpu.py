@@ -40,3 +40,42 @@ def test_library_loads_without_gpu():
     for name in lenssim.EXPORTED:
         assert hasattr(L, name)
     assert set(lenssim.EXPORTED) == _declared()
+
+
+def _header_text():
+    return re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lens_sim.h")).read(), flags=re.S)
+
+
+def _enum_block(text, name):
+    m = re.search(r"typedef enum \{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    return {k: int(v) for k, v in re.findall(r"\b([A-Z][A-Z0-9_]*)\s*=\s*(-?\d+)", m.group(1))}
+
+
+def _define(text, name):
+    m = re.search(r"#define\s+" + name + r"\s+(-?\d+)\b", text)
+    assert m, name
+    return int(m.group(1))
+
+
+def test_binding_constants_match_the_header():
+    # the binding marshals by these numbers: a drift from the header would silently send the
+    # wrong profile, light model or method to the library
+    from paper_2606_01547_gb300 import lenssim, workloads
+    text = _header_text()
+    lens = {k[len("LENS_"):]: v for k, v in _enum_block(text, "lens_profile_type").items()}
+    assert lens == lenssim.LENS_TYPES
+    light = {k[len("LIGHT_"):]: v for k, v in _enum_block(text, "light_profile_type").items()}
+    assert light == lenssim.LIGHT_TYPES
+    status = _enum_block(text, "lens_status")
+    assert {lenssim.STATUS_NAMES[v]: v for v in lenssim.STATUS_NAMES} == status
+    assert _define(text, "LENS_PROFILE_PARAMS") == lenssim.PROFILE_PARAMS
+    assert _define(text, "LENS_MAX_DEFLECTORS") == lenssim.MAX_DEFLECTORS
+    assert {m: _define(text, "LENS_CONV_" + m.upper()) for m in lenssim.CONV_METHODS} == lenssim.CONV_METHODS
+    assert _define(text, "LENS_CONV_FFT_MIN_K") == lenssim.CONV_FFT_MIN_K
+    kern = open(os.path.join(ROOT, "paper_2606_01547_gb300", "csrc", "kernels.h")).read()
+    assert int(re.search(r"kTraceVariants\s*=\s*(\d+)", kern).group(1)) == len(lenssim.TRACE_VARIANTS)
+    # every profile the library takes has a parameter layout in the input generators
+    for name in list(lenssim.LENS_TYPES) + list(lenssim.LIGHT_TYPES):
+        assert name in workloads.N_PARAMS, name
+        assert workloads.N_PARAMS[name] <= lenssim.PROFILE_PARAMS
