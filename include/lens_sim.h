@@ -57,6 +57,7 @@ typedef enum {
 #define LENS_MAX_SHAPELET_NMAX 10    /* SHAPELETS order limit: at most 66 amplitudes */
 #define LENS_MAX_SHAPELET_COEFFS ((LENS_MAX_SHAPELET_NMAX + 1) * (LENS_MAX_SHAPELET_NMAX + 2) / 2)
 #define LENS_MAX_MULTIPOLE_ORDER 32
+#define LENS_MAX_MULTIPOLE_ELL_ORDER 8   /* elliptical multipoles (LENS_MULTIPOLE_ELL) */
 
 /* Deflector profile types and their parameter layouts p[] (deflection table rows). */
 typedef enum {
@@ -82,8 +83,14 @@ typedef enum {
   LENS_NFW_ELLIPSE_CSE = 12, /* Rs, alpha_Rs, e1, e2, cx, cy   NFW convergence on ellipses
                          * xi^2 = q x'^2 + y'^2/q, evaluated as a sum of 44 CSEs (deflection
                          * within 1e-7 of the exact profile's maximum on 1e-3 < xi/Rs < 1e3) */
-  LENS_HERNQUIST_ELLIPSE_CSE = 13 /* sigma0, Rs, e1, e2, cx, cy  kappa = sigma0 ((2 + x^2) F(x) - 3)
+  LENS_HERNQUIST_ELLIPSE_CSE = 13, /* sigma0, Rs, e1, e2, cx, cy  kappa = sigma0 ((2 + x^2) F(x) - 3)
                          * / (x^2 - 1)^2, x = xi/Rs (Hernquist 1990 projection), 44 CSEs     */
+  LENS_MULTIPOLE_ELL = 14 /* m, a_m, phi_m, q, phi_e, cx, cy, r_E  elliptical multipole: kappa =
+                         * r_E a_m cos(m (varphi - phi_m)) / (2 R) in the frame of an ellipse of
+                         * axis ratio q and angle phi_e, R^2 = q x''^2 + y''^2/q, varphi =
+                         * atan2(y''/sqrt(q), x'' sqrt(q)); m an integer in [1, LENS_MAX_MULTIPOLE_ELL_ORDER],
+                         * q in [0.4, 1], r_E > 0, at most one per system.  Evaluated from the
+                         * Fourier series of 2 kappa r (its coefficients computed once per call). */
 } lens_profile_type;
 
 /* Source light profile types (light table rows). I = amp exp(-b_n [(R/R_s)^(1/n) - 1]),

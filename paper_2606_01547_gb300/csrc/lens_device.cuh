@@ -32,12 +32,18 @@ struct DevProfile {
 // One lens system as the kernels see it.  `sub` is the precomputed table of its n_sub subhalos
 // (kTableStride float4 per subhalo, see tnfw_write_table); `out` receives the binned,
 // unconvolved image.
+// Harmonics kept for the elliptical multipole (enough for 1e-8 of the largest coefficient at
+// m <= 8, q >= 0.4, where the series needs at most 74).
+constexpr int kEllMaxK = 80;
+
 struct DevSystem {
   int nx, ny, s, n_defl;
   float dpix, x0, y0;
   int src_type;
   float src[8];
   float src_coef[LENS_MAX_SHAPELET_COEFFS];  // SHAPELETS amplitudes
+  int ell_K;                                 // LENS_MULTIPOLE_ELL: harmonics 0..ell_K of 2 kappa r,
+  float ell_c[2 * (kEllMaxK + 1)];           // (Re, Im) pairs scaled by a_m r_E (0 if none)
   DevProfile defl[LENS_MAX_DEFLECTORS];
   int n_sub;
   int pad_;
@@ -655,9 +661,48 @@ __device__ __forceinline__ void alpha_cse_sum(const float* sig, const float* amp
   ay = sp * axp + cp * ayp;
 }
 
-static __device__ __noinline__ void alpha_profile(const DevProfile& P, float x, float y, float& ax, float& ay) {
+// Elliptical multipole (m, a_m, phi_m, q, phi_e, cx, cy, r_E).  2 kappa r depends on the polar
+// angle theta alone; with its Fourier coefficients c_k (scaled by a_m r_E, computed on the host
+// once per system) the potential is psi = r F(theta) + (1/2) r ln(r/r_E) h_1(theta), where
+// F = sum over k != +-1 of c_k e^{ik theta} / (1 - k^2) and h_1 = 2 Re(c_1 e^{i theta}) is the
+// k = +-1 part (present for odd m), whose r ln r potential has Laplacian h_1/r.  alpha = grad psi
+// from the radial derivative (F + (L + 1) h_1/2) and the tangential one (F' + L h_1'/2), L = ln(r/r_E).
+__device__ __forceinline__ void alpha_multipole_ell(const float* p, const float* c, int K, float x, float y,
+                                                    float& ax, float& ay) {
+  float se, ce;
+  sincosf(p[4], &se, &ce);
+  const float dx = x - p[5], dy = y - p[6];
+  const float xp = ce * dx + se * dy, yp = -se * dx + ce * dy;
+  const float r2 = xp * xp + yp * yp;
+  if (r2 < 1e-24f) { ax = 0.f; ay = 0.f; return; }
+  const float ir = rsqrtf(r2), r = r2 * ir;
+  const float ct = xp * ir, st = yp * ir;
+  float F = c[0], Fd = 0.f;
+  float zr = ct, zi = st;  // e^{i k theta}
+  for (int k = 2; k <= K; ++k) {
+    const float nr = zr * ct - zi * st, ni = zr * st + zi * ct;
+    zr = nr;
+    zi = ni;
+    const float w = 2.f / (1.f - (float)(k * k));
+    const float pr = c[2 * k] * zr - c[2 * k + 1] * zi, pim = c[2 * k] * zi + c[2 * k + 1] * zr;
+    F = fmaf(w, pr, F);
+    Fd = fmaf(-w * (float)k, pim, Fd);
+  }
+  const float A = 2.f * c[2], B = -2.f * c[3];
+  const float h1 = A * ct + B * st, h1d = B * ct - A * st;
+  const float L = logf(r / p[7]);
+  const float ar = F + 0.5f * (L + 1.f) * h1, at = Fd + 0.5f * L * h1d;
+  const float axp = ar * ct - at * st, ayp = ar * st + at * ct;
+  ax = ce * axp - se * ayp;
+  ay = se * axp + ce * ayp;
+}
+
+// One deflector at (x, y); ell_c / ell_K: the system's elliptical-multipole coefficients.
+static __device__ __noinline__ void alpha_profile(const DevProfile& P, const float* ell_c, int ell_K, float x, float y,
+                                                  float& ax, float& ay) {
   const float* p = P.p;
   switch (P.type) {
+    case LENS_MULTIPOLE_ELL: alpha_multipole_ell(p, ell_c, ell_K, x, y, ax, ay); return;
     case LENS_SIS: alpha_sis(x, y, p[0], p[1], p[2], ax, ay); return;
     case LENS_SIE: alpha_sie(x, y, p[0], p[1], p[2], p[3], p[4], ax, ay); return;
     case LENS_EPL: alpha_epl(x, y, p[0], p[1], p[2], p[3], p[4], p[5], ax, ay); return;

@@ -1,6 +1,7 @@
 // Host implementation of the C ABI in include/lens_sim.h: argument validation, device
 // workspace management, resident PSF/subhalo state, and the per-system launch sequence
 //   subhalo constants -> fused trace/source/bin-down kernel -> PSF convolution.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -114,6 +115,14 @@ int validate_profile(lens_sim* s, const lens_profile& p) {
                     LENS_MAX_MULTIPOLE_ORDER);
       if (!(p.p[5] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "multipole r_E must be > 0");
       return LENS_OK;
+    case LENS_MULTIPOLE_ELL:
+      if (!is_integer_in(p.p[0], 1, LENS_MAX_MULTIPOLE_ELL_ORDER))
+        return fail(s, LENS_ERR_INVALID_ARG, "elliptical multipole order m=%g not an integer in [1, %d]", p.p[0],
+                    LENS_MAX_MULTIPOLE_ELL_ORDER);
+      if (!(p.p[3] >= 0.4f && p.p[3] <= 1.f))
+        return fail(s, LENS_ERR_INVALID_ARG, "elliptical multipole q=%g not in [0.4, 1]", p.p[3]);
+      if (!(p.p[7] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "elliptical multipole r_E must be > 0");
+      return LENS_OK;
     case LENS_NFW_ELLIPSE_CSE:
     case LENS_HERNQUIST_ELLIPSE_CSE:
       if (!(p.p[p.type == LENS_NFW_ELLIPSE_CSE ? 0 : 1] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "Rs must be > 0");
@@ -183,6 +192,8 @@ int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
     int rc = validate_profile(s, y.deflectors[d]);
     if (rc) return rc;
   }
+  if (count_deflectors(y, LENS_MULTIPOLE_ELL) > 1)
+    return fail(s, LENS_ERR_INVALID_ARG, "at most one elliptical multipole per system");
   if (y.subhalo_table >= 0) {
     SubTable t;
     if (!s->res->table(y.subhalo_table, &t) || (!t.d && t.n))
@@ -227,6 +238,51 @@ int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* 
   return LENS_OK;
 }
 
+int count_deflectors(const lens_system& y, int type) {
+  int n = 0;
+  for (int k = 0; k < y.n_deflectors; ++k) n += y.deflectors[k].type == type;
+  return n;
+}
+
+// LENS_MULTIPOLE_ELL: the Fourier coefficients c_k of 2 kappa r / (a_m r_E), a function of the
+// polar angle alone, by the trapezoid rule on 1024 points (geometric convergence for this
+// analytic periodic function), kept up to the last harmonic above 1e-8 of the largest (at most
+// kEllMaxK) and stored scaled by a_m r_E as (Re, Im) pairs.
+static void ell_coefficients(const float* p, DevSystem& d) {
+  constexpr int N = 1024;
+  constexpr double kTwoPi = 6.283185307179586476925;
+  const int m = (int)std::lround(p[0]);
+  const double q = p[3], dphi = (double)p[2] - (double)p[4], scale = (double)p[1] * (double)p[7];
+  const double sq = std::sqrt(q);
+  double h[N], cs[N], sn[N];  // on the stack: no allocation (the allocation-free entry uses this too)
+  for (int j = 0; j < N; ++j) {
+    cs[j] = std::cos(kTwoPi * j / N);
+    sn[j] = std::sin(kTwoPi * j / N);
+    const double g = std::sqrt(q * cs[j] * cs[j] + sn[j] * sn[j] / q);  // R / r
+    h[j] = std::cos(m * (std::atan2(sn[j] / sq, sq * cs[j]) - dphi)) / g;
+  }
+  double re[kEllMaxK + 1], im[kEllMaxK + 1], amax = 0.0;
+  for (int k = 0; k <= kEllMaxK; ++k) {
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < N; ++j) {
+      const int idx = (k * j) % N;
+      sr += h[j] * cs[idx];
+      si -= h[j] * sn[idx];
+    }
+    re[k] = sr / N;
+    im[k] = si / N;
+    amax = std::max(amax, std::hypot(re[k], im[k]));
+  }
+  int K = 1;
+  for (int k = 2; k <= kEllMaxK; ++k)
+    if (std::hypot(re[k], im[k]) > 1e-8 * amax) K = k;
+  d.ell_K = K;
+  for (int k = 0; k <= K; ++k) {
+    d.ell_c[2 * k] = (float)(scale * re[k]);
+    d.ell_c[2 * k + 1] = (float)(scale * im[k]);
+  }
+}
+
 void fill_dev_system(const lens_system& y, DevSystem& d) {
   std::memset(&d, 0, sizeof(d));
   d.nx = y.grid.nx;
@@ -239,6 +295,7 @@ void fill_dev_system(const lens_system& y, DevSystem& d) {
   for (int k = 0; k < y.n_deflectors; ++k) {
     d.defl[k].type = y.deflectors[k].type;
     for (int q = 0; q < LENS_PROFILE_PARAMS; ++q) d.defl[k].p[q] = y.deflectors[k].p[q];
+    if (y.deflectors[k].type == LENS_MULTIPOLE_ELL) ell_coefficients(y.deflectors[k].p, d);
   }
   d.src_type = y.source.type;
   for (int q = 0; q < 8; ++q) d.src[q] = y.source.p[q];

@@ -68,6 +68,7 @@ extern "C" int lens_sim_image_noalloc(const lens_system* sys, const float* psf, 
     return LENS_ERR_INVALID_ARG;
   for (int d = 0; d < y.n_deflectors; ++d)
     if (validate_profile(nullptr, y.deflectors[d]) != LENS_OK) return LENS_ERR_INVALID_ARG;
+  if (count_deflectors(y, LENS_MULTIPOLE_ELL) > 1) return LENS_ERR_INVALID_ARG;
   if (validate_light(nullptr, y.source, y.source_coeffs, y.n_source_coeffs) != LENS_OK) return LENS_ERR_INVALID_ARG;
   const bool with_psf = psf != nullptr && k != 0;
   if (with_psf && (k < 1 || k > LENS_MAX_PSF || (k % 2) == 0)) return LENS_ERR_INVALID_ARG;

@@ -53,6 +53,8 @@ int sub_count(lens_sim* s, const lens_system& y);
 int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* raw_buf, const float4** out_tab,
                      int* out_n, cudaStream_t st);
 void fill_dev_system(const lens_system& y, DevSystem& d);
+// Deflectors of the given type in a system.
+int count_deflectors(const lens_system& y, int type);
 int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const* outs, cudaStream_t st);
 
 }  // namespace ls

@@ -300,7 +300,7 @@ __device__ __forceinline__ void unit_finalize(const DevSystem& sys, const UnitGe
     sample_xy(sys, g, q, x, y);
     for (int d = 0; d < sys.n_defl; ++d) {
       float dax, day;
-      alpha_profile(sys.defl[d], x, y, dax, day);
+      alpha_profile(sys.defl[d], sys.ell_c, sys.ell_K, x, y, dax, day);
       sx += dax;
       sy += day;
     }
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(256) deflection_kernel(const __grid_constant__
   }
   for (int d = 0; d < sys.n_defl; ++d) {
     float dax, day;
-    alpha_profile(sys.defl[d], px, py, dax, day);
+    alpha_profile(sys.defl[d], sys.ell_c, sys.ell_K, px, py, dax, day);
     ax += dax;
     ay += day;
   }

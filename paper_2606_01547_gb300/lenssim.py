@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "LENS_OK", -1: "LENS_ERR_INVALID_ARG", -2: "LENS_ERR_OOM", -3
 
 LENS_TYPES = {"SIS": 0, "SIE": 1, "EPL": 2, "SHEAR": 3, "POINT_MASS": 4, "NFW": 5, "TNFW": 6,
               "EPL_E1E2": 7, "SIE_E1E2": 8, "MULTIPOLE": 9, "EPL_MULTIPOLE_M1M3M4": 10, "CSE": 11,
-              "NFW_ELLIPSE_CSE": 12, "HERNQUIST_ELLIPSE_CSE": 13}
+              "NFW_ELLIPSE_CSE": 12, "HERNQUIST_ELLIPSE_CSE": 13, "MULTIPOLE_ELL": 14}
 LIGHT_TYPES = {"SERSIC_ELLIPSE_Q_PHI": 0, "SERSIC_ELLIPSE": 1, "SERSIC": 2, "SHAPELETS": 3}
 MAX_DEFLECTORS = 8
 CONV_METHODS = {"auto": 0, "direct": 1, "fft": 2}

@@ -40,7 +40,7 @@ LENS_NAMES = ("SIS", "SIE", "EPL", "SHEAR", "POINT_MASS", "NFW", "TNFW", "EPL_E1
 LIGHT_NAMES = ("SERSIC_ELLIPSE_Q_PHI", "SERSIC_ELLIPSE", "SERSIC")
 N_PARAMS = {"SIS": 3, "SIE": 5, "EPL": 6, "SHEAR": 2, "POINT_MASS": 3, "NFW": 4, "TNFW": 5,
             "EPL_E1E2": 6, "SIE_E1E2": 5, "MULTIPOLE": 6, "EPL_MULTIPOLE_M1M3M4": 12, "CSE": 6,
-            "NFW_ELLIPSE_CSE": 6, "HERNQUIST_ELLIPSE_CSE": 6,
+            "NFW_ELLIPSE_CSE": 6, "HERNQUIST_ELLIPSE_CSE": 6, "MULTIPOLE_ELL": 8,
             "SERSIC_ELLIPSE_Q_PHI": 7, "SERSIC_ELLIPSE": 7, "SERSIC": 5, "SHAPELETS": 4}
 # Order of the 15 free parameters of the likelihood (differentiation workload).
 FREE_PARAMS = ("epl_theta_E", "epl_gamma", "epl_e1", "epl_e2", "epl_cx", "epl_cy",

@@ -155,6 +155,36 @@ def test_sizes_beyond_the_limits_are_rejected(sim):
             sim.image(b)
         assert ei.value.code == lenssim.LENS_ERR_INVALID_ARG
 
+
+def test_elliptical_multipole_image_matches_oracle(sim):
+    # an EPL with an m = 4 elliptical multipole on its own ellipse, shear and subhalos
+    base = W.substructure_system(83, n_sub=300, nx=40, s=2, k=5)
+    (_, epl), shear = base.deflectors
+    th, g, q, phi = epl[:4]
+    e = [("EPL", epl), ("MULTIPOLE_ELL", [4, 0.02, phi + 0.1, q, phi, 0.0, 0.0, th]),
+         ("MULTIPOLE_ELL", [3, 0.01, 0.7, q, phi, 0.0, 0.0, th])]
+    for defl in ([e[0], e[1], shear], [e[0], e[2], shear]):
+        system = W.LensSystem(W.Grid(40, 40, 2, W.f32(0.06)), [(n, [W.f32(v) for v in p]) for n, p in defl],
+                              base.subhalos, base.source, base.psf)
+        ref = oracle.image(system)
+        tol, floor = image_tol(system, ref)
+        err = rel_linf(gpu_image(sim, system), ref)
+        assert err <= tol, (defl[1][1][0], err, floor)
+
+
+def test_elliptical_multipole_limits_are_refused(sim):
+    from paper_2606_01547_gb300 import lenssim
+    base = W.plain_system()
+    ok = ("MULTIPOLE_ELL", [4, 0.02, 0.1, 0.7, 0.3, 0.0, 0.0, 1.0])
+    bad = [[("MULTIPOLE_ELL", [9, 0.02, 0.1, 0.7, 0.3, 0.0, 0.0, 1.0])],
+           [("MULTIPOLE_ELL", [4, 0.02, 0.1, 0.3, 0.3, 0.0, 0.0, 1.0])],
+           [("MULTIPOLE_ELL", [4, 0.02, 0.1, 0.7, 0.3, 0.0, 0.0, 0.0])],
+           [ok, ok]]
+    for d in bad:
+        with pytest.raises(lenssim.LensSimError) as ei:
+            sim.image(W.LensSystem(base.grid, base.deflectors + d, base.subhalos, base.source, base.psf))
+        assert ei.value.code == lenssim.LENS_ERR_INVALID_ARG
+
 def test_image_path_with_largest_psf_matches_oracle(sim):
     # k = 135 (the paper's largest kernel) through the single-image path; auto takes the FFT
     base = W.substructure_system(70, n_sub=100, nx=60, s=1, k=0)
@@ -249,7 +279,12 @@ PROFILES = [("SIS", [1.1, 0.05, -0.02]), ("SIE", [1.0, 0.8, 0.3, 0.0, 0.0]),
             ("CSE", [0.1, 1.5, -0.4, 0.1, 0.0, 0.0]),
             ("NFW_ELLIPSE_CSE", [0.8, 0.3, 0.15, -0.2, 0.05, 0.0]), ("NFW_ELLIPSE_CSE", [3.0, 1.0, 0.05, 0.02, 0.0, 0.0]),
             ("HERNQUIST_ELLIPSE_CSE", [0.5, 0.8, 0.1, -0.2, 0.0, 0.1]),
-            ("HERNQUIST_ELLIPSE_CSE", [1.2, 0.3, 0.25, 0.2, 0.0, 0.0])]
+            ("HERNQUIST_ELLIPSE_CSE", [1.2, 0.3, 0.25, 0.2, 0.0, 0.0]),
+            ("MULTIPOLE_ELL", [1, 0.05, 0.4, 0.6, -0.3, 0.1, -0.1, 1.2]),
+            ("MULTIPOLE_ELL", [2, 0.05, 0.3, 1.0, 0.0, 0.0, 0.0, 1.0]),
+            ("MULTIPOLE_ELL", [3, 0.03, 1.1, 0.8, 0.5, 0.05, 0.02, 1.3]),
+            ("MULTIPOLE_ELL", [4, 0.02, 0.2, 0.45, 1.0, 0.0, 0.0, 0.9]),
+            ("MULTIPOLE_ELL", [8, 0.01, 2.0, 0.4, 0.3, 0.1, 0.1, 1.1])]
 
 
 @pytest.mark.parametrize("name,params", PROFILES)
