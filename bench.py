@@ -333,6 +333,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         extras["differentiation"] = grad_extra(sim, W, dev)
         extras["fitting"] = fitting_extra(sim, W, dev)
         extras["serving"] = serving_extra(lenssim, W, args.serve_rates, args.serve_seconds)
+        extras["per_config"] = per_config_extra(sim, lenssim, W, dev, args.cpu_budget_s)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -412,6 +413,142 @@ def batched_extra(sim, lenssim, W, dev, n_sys: int, small: bool = False):
             "workload": ("grids 64^2, s in {1,2,3}, subhalos log-uniform in [0,100], PSF 5..31" if small else
                          "grids {64,100,128,200,256}^2, s in {1,2,3}, subhalos log-uniform in [0,20000], PSF 5..31")
                         + "; one graph launch vs per-image calls with a sync each"}
+
+
+def _rel_linf(a, b) -> float:
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def per_config_extra(sim, lenssim, W, dev, cpu_budget_s: float = 10.0):
+    """Per-configuration report: for the plain (60^2), substructure (200^2, s = 3, 10k), batched
+    (uneven mix) and differentiation (100^2, 15 parameters) workloads, the GPU's error against
+    the FP64 oracle beside the oracle's conditioning floor (its own error when every quantity an
+    FP32 evaluation must round is rounded to FP32), and the oracle's CPU throughput on this
+    host; plus the plain 60^2 image's GPU images/s (a launch-bound single-system call)."""
+    import torch
+    import oracle
+    oracle.build()
+    out = {}
+    cores = oracle.nthreads()
+
+    def gpu_img(system):
+        img = sim.image(system)[0]
+        torch.cuda.synchronize()
+        return img.cpu().numpy()
+
+    # C1 plain
+    c1 = W.plain_system()
+    ref = oracle.image(c1)
+    floor = _rel_linf(oracle.image(c1, fp32=True), ref)
+    t0 = time.perf_counter()
+    n1 = 0
+    while n1 < 3 or time.perf_counter() - t0 < min(2.0, cpu_budget_s / 4):
+        oracle.image(c1)
+        n1 += 1
+    cpu_c1 = n1 / (time.perf_counter() - t0)
+    keep = []
+    cc = sim.system_struct(c1, keep)
+    outd = torch.empty((60, 60), device=dev)
+    import ctypes
+    L = lenssim.lib()
+    ptr = (ctypes.c_void_p * 1)(outd.data_ptr())
+    sp = int(torch.cuda.current_stream().cuda_stream)
+    for _ in range(20):
+        L.lens_sim_image(sim.h, ctypes.byref(cc), 1, ptr, sp)
+    torch.cuda.synchronize()
+    reps = 2000
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        rc = L.lens_sim_image(sim.h, ctypes.byref(cc), 1, ptr, sp)
+        if rc:
+            raise lenssim.LensSimError(rc, sim.last_error())
+    torch.cuda.synchronize()
+    gpu_c1 = reps / (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    for _ in range(500):
+        L.lens_sim_image(sim.h, ctypes.byref(cc), 1, ptr, sp)
+        torch.cuda.synchronize()
+    gpu_c1_sync = 500 / (time.perf_counter() - t0)
+    out["plain"] = {"workload": "60x60 at 0.05\", s = 1, SIE + shear, Sersic, 5x5 Gaussian PSF",
+                    "gpu_rel_linf": _rel_linf(gpu_img(c1), ref), "oracle_floor": floor,
+                    "tolerance": max(1e-5, 2 * floor), "gpu_images_per_s": gpu_c1,
+                    "gpu_images_per_s_sync_each": gpu_c1_sync,
+                    "cpu_oracle": {"images_per_s": cpu_c1, "cores": cores, "sample": f"{n1} full images"}}
+
+    # C2 substructure: the first benchmark system, whole image
+    c2 = W.substructure_system(1000)
+    ref = oracle.image(c2)
+    floor = _rel_linf(oracle.image(c2, fp32=True), ref)
+    out["substructure"] = {"workload": "200x200 at 0.04\", s = 3, EPL + shear, 10,000 TNFW, Sersic, 21x21 Moffat "
+                                       "(seed 1000, whole image)",
+                           "gpu_rel_linf": _rel_linf(gpu_img(c2), ref), "oracle_floor": floor,
+                           "tolerance": max(1e-5, 2 * floor)}
+
+    # C3 batched: four members of the uneven mix through one batched call, whole images; the
+    # oracle's CPU rate is extrapolated from two-row bands of 64 seeded members
+    mix = W.batched_systems(2024, count=64)
+    order = sorted(range(len(mix)), key=lambda i: mix[i].pairs())
+    pick = [order[0], order[len(order) // 4], order[len(order) // 2], order[(3 * len(order)) // 5]]
+    members = [mix[i] for i in pick]
+    imgs = sim.image(members)
+    torch.cuda.synchronize()
+    errs, floors = [], []
+    for sy, im in zip(members, imgs):
+        r = oracle.image(sy)
+        errs.append(_rel_linf(im.cpu().numpy(), r))
+        floors.append(_rel_linf(oracle.image(sy, fp32=True), r))
+    t_est = 0.0
+    t0 = time.perf_counter()
+    for sy in mix:
+        ny = sy.grid.ny
+        r0 = ny // 2 - 1
+        ta = time.perf_counter()
+        oracle.image_rows(sy, r0, r0 + 2)
+        t_rows = time.perf_counter() - ta
+        ta = time.perf_counter()
+        if sy.psf is not None:
+            oracle.convolve(np.zeros((ny, sy.grid.nx)), sy.psf)
+        t_est += t_rows * ny / 2 + (time.perf_counter() - ta)
+    out["batched"] = {"workload": "uneven mix: grids {64,100,128,200,256}^2, s in {1,2,3}, 0..20,000 TNFW, PSF 5..31",
+                      "members": [{"grid": m.grid.nx, "s": m.grid.s, "n_sub": m.n_sub,
+                                   "psf": 0 if m.psf is None else int(m.psf.shape[0]),
+                                   "gpu_rel_linf": e, "oracle_floor": f, "tolerance": max(1e-5, 2 * f)}
+                                  for m, e, f in zip(members, errs, floors)],
+                      "cpu_oracle": {"images_per_s": len(mix) / t_est, "cores": cores, "extrapolated": True,
+                                     "sample": "two central rows of each of 64 seeded members of the mix plus "
+                                               "each one's full PSF convolution, extrapolated to whole images",
+                                     "seconds": time.perf_counter() - t0}}
+
+    # C4 differentiation: likelihood + gradient at 4 of the 512 points
+    pb = W.diff_problem(42)
+    data = W.observe(oracle.model_image(pb.system, pb.truth), pb.sigma_bkg, pb.t_exp, 42)
+    idx = [0, 131, 257, 511]
+    tid = sim.register_subhalos(pb.system.subhalos)
+    Lg, Gg = sim.grad(pb.system, torch.from_numpy(data).to(dev), pb.sigma_bkg, pb.t_exp,
+                      torch.from_numpy(pb.points).to(dev), subhalo_table=tid)
+    torch.cuda.synchronize()
+    Lg, Gg = Lg.cpu().numpy()[idx], Gg.cpu().numpy()[idx]
+    pts = pb.points[idx].astype(np.float64)
+    Lr, Gr = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts)
+    n_cpu = max(16, cores)
+    t0 = time.perf_counter()
+    oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pb.points[:n_cpu].astype(np.float64))
+    t_grad = time.perf_counter() - t0
+    _, Gf = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts, fp32=True)
+    gmax = np.abs(Gr).max(axis=1, keepdims=True)
+    scale = np.maximum(np.abs(Gr), 1e-3 * gmax)
+    out["differentiation"] = {
+        "workload": "100x100 at 0.05\", 13x13 Gaussian PSF, 1000 fixed TNFW, 15 parameters (points 0, 131, 257, 511)",
+        "logL_rel_err_max": float(np.max(np.abs(Lg - Lr) / np.abs(Lr))),
+        "grad_normwise_err_max": float(np.max(np.abs(Gg - Gr).max(axis=1) / gmax[:, 0])),
+        "grad_componentwise_err_max": float(np.max(np.abs(Gg - Gr) / scale)),
+        "grad_floor_componentwise_max": float(np.max(np.abs(Gf - Gr) / scale)),
+        "cpu_oracle": {"gradients_per_s": n_cpu / t_grad, "cores": cores,
+                       "sample": f"{n_cpu} of the 512 points, forward-mode dual numbers (15 tangents), "
+                                 f"including the 10^7-pair subhalo field"}}
+    return out
 
 
 def measured_hbm_gbs():
@@ -592,16 +729,23 @@ def fitting_extra(sim, W, dev):
     return {"pso": out, "lbfgs": lbfgs, "workload": "100x100, 13x13 PSF, 1000 fixed TNFW, 15 free parameters"}
 
 
-def serving_full_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_sets: int = 2):
-    """The long serving sweep: open-loop Poisson arrivals at each rate for `seconds`, drawn from a
-    pool of `pool_size` pre-generated requests (the serving mix) that is cycled.  Each pool entry
-    has `out_sets` sets of output buffers used in turn, so a buffer set is reused only
-    pool_size * out_sets arrivals later, after its previous request finished (a reuse that had to
-    wait for it is counted in `blocked_reuses`); a submit refused with LENS_ERR_BUSY (more than
-    max_inflight = 4096 requests admitted) counts as rejected.  p50/p99 are the server's own
-    submit-to-result latencies of the admitted requests."""
+def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_sets: int = 2,
+                  warmup_requests: int = 3000):
+    """Serving: open-loop Poisson arrivals at each rate for `seconds`, drawn from a pool of
+    `pool_size` pre-generated requests of the serving mix (70 % image / 30 % likelihood +
+    gradient, grids 64..256, subhalos 0..20,000, PSF 5..31) that is cycled.  One server serves
+    every rate; its PSFs are registered up front, as a deployment would, and an untimed warm-up
+    (the first `warmup_requests` of the pool submitted back to back) lets its slots size their
+    workspaces and capture their batch graphs before the first measured rate, whose statistics
+    are then reset.  Each pool entry has `out_sets` sets of output buffers used in turn, so a
+    buffer set is reused only pool_size * out_sets arrivals later, after its previous request
+    finished (a reuse that had to wait for it is counted in `blocked_reuses`); a submit refused
+    with LENS_ERR_BUSY (more than max_inflight = 4096 requests admitted) counts as rejected.
+    p50/p99 are the server's own submit-to-result latencies of the admitted requests.  The image
+    requests of the pool are then run one by one through lens_sim_image with a synchronisation
+    each: the plain per-image path on the same GPU."""
     import collections
-    import numpy as np
+    import torch
     pool = W.serving_stream(7, rate=1.0, duration=1.3 * pool_size)[:pool_size]
     inputs, outs = [], []
     for rq in pool:
@@ -614,15 +758,27 @@ def serving_full_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000,
                          np.float32)
             inputs.append((np.zeros((g.ny, g.nx), np.float32), p))
             outs.append([(np.empty(1, np.float32), np.empty(15, np.float32)) for _ in range(out_sets)])
+
+    def submit(srv, j, c):
+        rq, b, o = pool[j], inputs[j], outs[j][c]
+        if rq.kind == 0:
+            return srv.submit_image(rq.system, o[0])
+        return srv.submit_loglike(rq.system, b[0], 0.01, 1000.0, b[1], o[0], o[1])
+
+    srv = lenssim.Server(device=0)
+    for rq in pool:
+        srv.sim.register_psf(rq.system.psf)
+    t0 = time.perf_counter()
+    warm = [submit(srv, j, 0) for j in range(min(warmup_requests, pool_size))]
+    for t in warm:
+        srv.wait(t, 600000)
+    t_warm = time.perf_counter() - t0
     out = []
     for rate in rates:
+        srv.reset_stats()
         rng = np.random.default_rng(int(rate))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, int(rate * seconds * 1.2) + 16))
         arrivals = arrivals[arrivals < seconds]
-        srv = lenssim.Server(device=0)
-        # the PSFs are registered up front, as a deployment would
-        for rq in pool:
-            srv.sim.register_psf(rq.system.psf)
         codes = collections.Counter()
         pending = {}
         rejected = blocked = 0
@@ -643,12 +799,8 @@ def serving_full_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000,
                     blocked += 1
                     rc = srv.wait(prev, 600000)
                 codes[rc] += 1
-            rq, b, o = pool[j], inputs[j], outs[j][c]
             try:
-                if rq.kind == 0:
-                    pending[(j, c)] = srv.submit_image(rq.system, o[0])
-                else:
-                    pending[(j, c)] = srv.submit_loglike(rq.system, b[0], 0.01, 1000.0, b[1], o[0], o[1])
+                pending[(j, c)] = submit(srv, j, c)
             except lenssim.LensSimError as e:
                 if e.code != lenssim.LENS_ERR_BUSY:
                     raise
@@ -667,66 +819,25 @@ def serving_full_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000,
         if rec["failed"]:
             rec["last_error"] = srv.last_error()
         out.append(rec)
-        srv.close()
-    return {"rates": out, "pool": pool_size, "mix": "70% image / 30% likelihood+gradient, grids 64..256 (even), "
-                                                   "s = 1, subhalos log-uniform 0..20000, PSF 5..31"}
-
-def serving_extra(lenssim, W, rates, seconds: float):
-    """Open-loop Poisson arrivals (70% image / 30% likelihood+gradient, grids 64..256, subhalos
-    0..20,000, PSF 5..31) at each rate: p50/p99 latency (submit to result in host memory) and
-    completed requests/s.  The image requests of the first rate are also run one by one through
-    lens_sim_image with a synchronisation each: the plain per-image path on the same GPU."""
-    import collections
-    import numpy as np
-    import torch
-    out = []
-    plain = None
-    for rate in rates:
-        dur = min(seconds, 6000.0 / rate)  # bounded number of requests (host buffers)
-        reqs = W.serving_stream(7, rate=rate, duration=dur)
-        srv = lenssim.Server(device=0)
-        bufs = []
-        tickets = []
-        t0 = time.perf_counter()
-        for rq in reqs:
-            delay = rq.t_arrival - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            g = rq.system.grid
-            if rq.kind == 0:
-                o = np.empty((g.ny, g.nx), np.float32)
-                bufs.append(o)
-                tickets.append(srv.submit_image(rq.system, o))
-            else:
-                d = np.zeros((g.ny, g.nx), np.float32)
-                p = np.array([*rq.system.deflectors[0][1], *rq.system.deflectors[1][1], *rq.system.source[1]],
-                             np.float32)
-                o, gr = np.empty(1, np.float32), np.empty(15, np.float32)
-                bufs += [d, p, o, gr]
-                tickets.append(srv.submit_loglike(rq.system, d, 0.01, 1000.0, p, o, gr))
-        codes = collections.Counter(srv.wait(t, 600000) for t in tickets)
-        st = srv.stats()
-        n_img = sum(1 for rq in reqs if rq.kind == 0)
-        rec = {"rate_req_per_s": rate, "seconds": dur, "requests": len(reqs), "images": n_img,
-               "completed_ok": codes.get(0, 0), "failed": {str(k): v for k, v in codes.items() if k != 0},
-               "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "served_req_per_s": st["requests_per_s"]}
-        if rec["failed"]:
-            rec["last_error"] = srv.last_error()
-        out.append(rec)
-        srv.close()
-        if plain is None:
-            sim = lenssim.Simulator(device=0)
-            imgs = [rq.system for rq in reqs if rq.kind == 0]
-            dev_out = [torch.empty((s_.grid.ny, s_.grid.nx), device="cuda") for s_ in imgs]
-            sim.image(imgs[0], out=[dev_out[0]])
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            for s_, o in zip(imgs, dev_out):
-                sim.image(s_, out=[o])
-                torch.cuda.synchronize()
-            plain = len(imgs) / (time.perf_counter() - t1)
-            sim.close()
-    return {"rates": out, "plain_images_per_s": plain}
+    srv.close()
+    sim = lenssim.Simulator(device=0)
+    imgs = [rq.system for rq in pool if rq.kind == 0][:2000]
+    dev_out = [torch.empty((s_.grid.ny, s_.grid.nx), device="cuda") for s_ in imgs]
+    for s_, o in zip(imgs[:50], dev_out):  # untimed: workspaces and PSF registrations
+        sim.image(s_, out=[o])
+    for s_ in imgs:
+        sim.register_psf(s_.psf)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for s_, o in zip(imgs, dev_out):
+        sim.image(s_, out=[o])
+        torch.cuda.synchronize()
+    plain = len(imgs) / (time.perf_counter() - t1)
+    sim.close()
+    return {"rates": out, "pool": pool_size, "warmup_requests": len(warm), "warmup_seconds": t_warm,
+            "plain_images_per_s": plain, "plain_images": len(imgs),
+            "mix": "70% image / 30% likelihood+gradient, grids 64..256 (even), s = 1, subhalos log-uniform "
+                   "0..20000, PSF 5..31"}
 
 
 def main():
@@ -743,18 +854,15 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, gradient and serving lines")
     ap.add_argument("--variant", type=int, default=-1, help="fixed trace launch variant instead of autotuning")
     ap.add_argument("--extra-only", default="", choices=["", "differentiation", "batched", "batched_small_systems",
-                                                          "fitting", "scaling", "serving_full"],
+                                                          "fitting", "scaling", "serving", "per_config"],
                     help="profiling mode: only this one extra measurement")
     ap.add_argument("--fft-only", type=int, default=0, metavar="N_IMG",
                     help="profiling mode: only the FFT-versus-direct PSF measurement (N_IMG images per call)")
     ap.add_argument("--psf-only", type=int, default=0, metavar="N_IMG",
                     help="only the standalone PSF measurement on N_IMG 256^2 images (profiling runs)")
     ap.add_argument("--batch-systems", type=int, default=4096)
-    ap.add_argument("--serve-rates", type=float, nargs="*", default=[300.0, 3000.0, 12000.0])
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
-    ap.add_argument("--serve-full-rates", type=float, nargs="*",
-                    default=[100.0, 300.0, 1000.0, 3000.0, 10000.0, 20000.0],
-                    help="rates of --extra-only serving_full (10 s each)")
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[1000.0, 3000.0, 10000.0, 20000.0])
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -775,7 +883,8 @@ def main():
               "batched_small_systems": lambda: batched_extra(sim, lenssim, W, dev, args.batch_systems, small=True),
               "fitting": lambda: fitting_extra(sim, W, dev),
               "scaling": lambda: subhalo_scaling_extra(sim, W, dev),
-              "serving_full": lambda: serving_full_extra(lenssim, W, args.serve_full_rates, 10.0)}[args.extra_only]
+              "serving": lambda: serving_extra(lenssim, W, args.serve_rates, args.serve_seconds),
+              "per_config": lambda: per_config_extra(sim, lenssim, W, dev, args.cpu_budget_s)}[args.extra_only]
         print(json.dumps({args.extra_only: fn()}), flush=True)
         sim.close()
         return

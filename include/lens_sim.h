@@ -225,23 +225,29 @@ int lens_sim_linear_amp(lens_sim* sim, const lens_system* sys, const float* data
 
 /* ---------------------------------------------------------------- allocation-free form
  * The paper has no counterpart to this entry point; it is a deployment convenience.
- * lens_sim_image_noalloc simulates one system with the same kernels as lens_sim_image, for
- * callers that cannot allocate device memory: applications whose device memory is reserved
- * up front by their own pool allocator, and latency-critical loops that forbid
- * cudaMalloc/cudaFree after start-up because those calls can synchronise the whole device.
- * It takes no handle and calls no cudaMalloc, cudaFree or allocating library routine.  Its
- * scratch (per-subhalo constants and the unconvolved image) is one fixed array of
- * LENS_NOALLOC_SCRATCH_BYTES of device memory that every GPU loading the library holds until
- * the process exits.
- *  - sys: grid, HOST deflector list, source; subhalos in DEVICE memory (SoA [5][n]);
- *    subhalo_table must be -1; psf_id is ignored.
- *  - psf: DEVICE pointer to an odd k x k kernel (1 <= k <= LENS_MAX_PSF), or NULL (or k = 0)
- *    to skip the PSF step.  out_image: caller-owned DEVICE buffer of ny*nx floats.
+ * lens_sim_image_noalloc simulates one system for callers that cannot allocate device
+ * memory: applications whose device memory is reserved up front by their own pool allocator,
+ * and latency-critical loops that forbid cudaMalloc/cudaFree after start-up because those
+ * calls can synchronise the whole device.  It runs lens_sim_image's single-system kernels
+ * (subhalo constants and the fused trace kernel) and always the direct PSF convolution (where
+ * lens_sim_image's automatic choice takes the FFT for k >= LENS_CONV_FFT_MIN_K; both compute
+ * the same convolution, within the image tolerance).  It takes no handle and calls no
+ * cudaMalloc, cudaFree or allocating library routine.  Its scratch (per-subhalo constants and
+ * the unconvolved image) is one fixed array of LENS_NOALLOC_SCRATCH_BYTES of device memory
+ * that every GPU loading the library holds until the process exits.
+ *  - It runs on the CURRENT device.  sys: grid (as for lens_sim_image: 1..16384 pixels per
+ *    side, a finite positive pixel scale, a finite centre), HOST deflector list, source;
+ *    subhalos in device memory (SoA [5][n]); subhalo_table must be -1; psf_id is ignored.
+ *  - psf: device pointer to an odd k x k kernel (1 <= k <= LENS_MAX_PSF), or NULL (or k = 0)
+ *    to skip the PSF step.  out_image: caller-owned device buffer of ny*nx floats.  Every
+ *    buffer must be memory of the current device: a host pointer or another GPU's memory
+ *    returns LENS_ERR_INVALID_ARG with nothing launched.
  *  - n_subhalos > LENS_NOALLOC_MAX_SUBHALOS or nx*ny > LENS_NOALLOC_MAX_PIXELS returns
  *    LENS_ERR_OOM with nothing launched; bad arguments return LENS_ERR_INVALID_ARG and a
  *    failed CUDA call LENS_ERR_CUDA (there is no handle, hence no error text).
- *  - The first call on each device, made with that device current, looks up the array's
- *    device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Each call looks up the array's device address in the current device's context
+ *    (cudaGetSymbolAddress, which allocates nothing).  The first call on a device also loads
+ *    the library's kernels there: make that first call before any stream capture.
  *  - All calls share the one array, which keeps the last call's contents; each call writes
  *    everything it reads.  Calls that overlap on the GPU (different streams, or several host
  *    threads) race on the array: serialise them on one stream. */

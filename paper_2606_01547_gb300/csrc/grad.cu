@@ -69,8 +69,9 @@ struct PointFrame {
   float l_k0;        // t/(2q) - 1/(1 + q), the point-independent part of d ln(prefactor)/dq
   float s_qc, s_pc;  // the same for the source ellipticity
   float s_in;        // 1/n
-  int nt_adj;        // series terms of the adjoint: f^n <= 1e-7 with two more for the tangents'
-                     // n f^(n-1) (the value's own count, epl_terms, goes to 1.5e-8)
+  int nt_adj;        // series terms of the adjoint: the value's own count (|Omega_n| <= f^n
+                     // below 2^-26, as in the image kernels) plus the terms that bring the
+                     // tangents' n f^(n-1) below the same bound
 };
 
 __device__ __forceinline__ void point_frame(const float* P, PointFrame& F) {
@@ -84,7 +85,11 @@ __device__ __forceinline__ void point_frame(const float* P, PointFrame& F) {
   F.l_dT = F.lens.t / P[0];
   F.l_k0 = F.lens.t / (2.f * q) - 1.f / (1.f + q);
   const float f = F.lens.f;
-  F.nt_adj = f < 1e-20f ? 0 : min((int)ceilf(-16.2f / logf(f)) + 2, kEplTab);
+  // The adjoint's value series is summed at least as far as the image kernels' (tail below
+  // 2^-26 of the sum), so its traced positions are those of the forward model to FP32
+  // resolution, and its tangent series to the same bound.
+  const int nv = F.lens.nt;
+  F.nt_adj = nv == 0 ? 0 : min(nv + (int)ceilf(logf((float)nv) / -logf(f)) + 1, kEplTab);
   float qs, phis;
   e1e2_to_qphi(P[11], P[12], qs, phis);
   F.src = sersic_frame(P[8], P[9], P[10], qs, phis, P[13], P[14]);

@@ -42,6 +42,22 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+bool on_other_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type != cudaMemoryTypeDevice) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.device != dev;
+}
+
 int ensure(lens_sim* s, DevBuffer& b, size_t bytes) {
   if (bytes <= b.cap) return LENS_OK;
   size_t want = bytes + bytes / 4;  // geometric growth
@@ -170,15 +186,19 @@ int validate_light(lens_sim* s, const light_profile& p, const float* coeffs, int
   }
 }
 
+int validate_grid(lens_sim* s, const lens_grid& g) {
+  if (g.nx < 1 || g.ny < 1 || g.nx > 16384 || g.ny > 16384)
+    return fail(s, LENS_ERR_INVALID_ARG, "grid %dx%d out of range [1, 16384]", g.nx, g.ny);
+  if (g.supersample < 1 || g.supersample > LENS_MAX_SUPERSAMPLE)
+    return fail(s, LENS_ERR_INVALID_ARG, "supersample %d not in [1, %d]", g.supersample, LENS_MAX_SUPERSAMPLE);
+  if (!(g.pixel_scale > 0.f) || !finite(g.pixel_scale) || !finite(g.x0) || !finite(g.y0))
+    return fail(s, LENS_ERR_INVALID_ARG, "bad pixel scale or grid centre");
+  return LENS_OK;
+}
+
 int validate_system(lens_sim* s, const lens_system& y, bool need_grid) {
   if (need_grid) {
-    const lens_grid& g = y.grid;
-    if (g.nx < 1 || g.ny < 1 || g.nx > 16384 || g.ny > 16384)
-      return fail(s, LENS_ERR_INVALID_ARG, "grid %dx%d out of range [1, 16384]", g.nx, g.ny);
-    if (g.supersample < 1 || g.supersample > LENS_MAX_SUPERSAMPLE)
-      return fail(s, LENS_ERR_INVALID_ARG, "supersample %d not in [1, %d]", g.supersample, LENS_MAX_SUPERSAMPLE);
-    if (!(g.pixel_scale > 0.f) || !finite(g.pixel_scale) || !finite(g.x0) || !finite(g.y0))
-      return fail(s, LENS_ERR_INVALID_ARG, "bad pixel scale or grid centre");
+    if (int rg = validate_grid(s, y.grid)) return rg;
     int rc = validate_light(s, y.source, y.source_coeffs, y.n_source_coeffs);
     if (rc) return rc;
     PsfEntry pe;

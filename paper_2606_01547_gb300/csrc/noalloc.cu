@@ -3,12 +3,11 @@
 // Some callers cannot call cudaMalloc: applications that reserve the device's memory up front
 // for their own pool allocator (a library's cudaMalloc would fail or fragment that pool), and
 // latency-critical loops that forbid allocation after start-up because cudaMalloc/cudaFree can
-// synchronise the whole device.  This entry point serves them.  It runs the same kernels as
-// lens_sim_image does for one system, with no handle: its scratch -- the per-subhalo constants
-// and the unconvolved image -- lives in one fixed file-scope device array instead of a
-// handle's workspace.  It calls no cudaMalloc, cudaFree or allocating library routine.
-#include <mutex>
-
+// synchronise the whole device.  This entry point serves them.  It runs the single-system
+// kernels of lens_sim_image (subhalo constants, the fused trace kernel, and the direct PSF
+// convolution for every k) with no handle: its scratch -- the per-subhalo constants and the
+// unconvolved image -- lives in one fixed file-scope device array instead of a handle's
+// workspace.  It calls no cudaMalloc, cudaFree or allocating library routine.
 #include "kernels.h"
 #include "lens_sim.h"
 #include "sim_internal.h"
@@ -29,27 +28,16 @@ static_assert(kTableBytes + kImageBytes == LENS_NOALLOC_SCRATCH_BYTES, "scratch 
 // stand-in, not device memory); it uses the address looked up below.
 static __device__ __align__(256) unsigned char g_scratch[LENS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device, looked up once per device.
+// Device address of g_scratch in the current device's context.  Looked up on every call:
+// cudaGetSymbolAddress allocates nothing, and a fresh lookup stays right after the context has
+// been re-created (for instance after cudaDeviceReset reloads the module).
 int scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
     cudaGetLastError();
     return LENS_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return LENS_ERR_CUDA;
-    }
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
+  *out = p;
   return LENS_OK;
 }
 
@@ -61,8 +49,7 @@ extern "C" int lens_sim_image_noalloc(const lens_system* sys, const float* psf, 
   if (!sys || !out_image) return LENS_ERR_INVALID_ARG;
   const lens_system& y = *sys;
   const lens_grid& g = y.grid;
-  if (g.nx < 1 || g.ny < 1 || g.supersample < 1 || g.supersample > LENS_MAX_SUPERSAMPLE || !(g.pixel_scale > 0.f))
-    return LENS_ERR_INVALID_ARG;
+  if (validate_grid(nullptr, g) != LENS_OK) return LENS_ERR_INVALID_ARG;
   if (y.subhalo_table != -1 || y.n_subhalos < 0 || (y.n_subhalos > 0 && !y.subhalos)) return LENS_ERR_INVALID_ARG;
   if (y.n_deflectors < 0 || y.n_deflectors > LENS_MAX_DEFLECTORS || (y.n_deflectors > 0 && !y.deflectors))
     return LENS_ERR_INVALID_ARG;
@@ -75,8 +62,11 @@ extern "C" int lens_sim_image_noalloc(const lens_system* sys, const float* psf, 
   // sizes beyond the fixed scratch are refused before anything is launched
   if (y.n_subhalos > LENS_NOALLOC_MAX_SUBHALOS || (long long)g.nx * g.ny > (long long)LENS_NOALLOC_MAX_PIXELS)
     return LENS_ERR_OOM;
-  if (!is_device_ptr(out_image) || (y.n_subhalos > 0 && !is_device_ptr(y.subhalos)) ||
-      (with_psf && !is_device_ptr(psf)))
+  // every buffer must be memory of the current device, where the kernels run
+  const bool has_sub = y.n_subhalos > 0;
+  if (!is_device_ptr(out_image) || (has_sub && !is_device_ptr(y.subhalos)) || (with_psf && !is_device_ptr(psf)))
+    return LENS_ERR_INVALID_ARG;
+  if (on_other_device(out_image) || (has_sub && on_other_device(y.subhalos)) || (with_psf && on_other_device(psf)))
     return LENS_ERR_INVALID_ARG;
 
   void* base = nullptr;

@@ -9,6 +9,8 @@ namespace ls {
 
 constexpr int kConvT = 32;
 constexpr int kConvRows = 8;
+// From this kernel size on (above the TMA kernel's k <= 31) the direct sum is taken by rows.
+constexpr int kConvRowSumMinK = 33;
 
 __global__ void __launch_bounds__(kConvT * kConvRows)
 conv_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int nx,
@@ -32,14 +34,36 @@ conv_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int n
   float acc[kConvT / kConvRows];
 #pragma unroll
   for (int q = 0; q < kConvT / kConvRows; ++q) acc[q] = 0.f;
-  for (int a = 0; a < k; ++a) {
-    for (int b = 0; b < k; ++b) {
-      const float kv = sK[a * k + b];
+  if (k < kConvRowSumMinK) {
+    // one running sum over the k^2 taps, in the order of the TMA kernel (bitwise equal to it)
+    for (int a = 0; a < k; ++a) {
+      for (int b = 0; b < k; ++b) {
+        const float kv = sK[a * k + b];
 #pragma unroll
-      for (int q = 0; q < kConvT / kConvRows; ++q) {
-        const int r = threadIdx.y + q * kConvRows;
-        acc[q] = fmaf(kv, sT[(r + a) * tw + threadIdx.x + b], acc[q]);
+        for (int q = 0; q < kConvT / kConvRows; ++q) {
+          const int r = threadIdx.y + q * kConvRows;
+          acc[q] = fmaf(kv, sT[(r + a) * tw + threadIdx.x + b], acc[q]);
+        }
       }
+    }
+  } else {
+    // large kernels: a partial sum per kernel row, then the sum of the rows.  One running sum
+    // over k^2 = 18,225 taps (k = 135) drifts by ~sqrt(k^2) roundings, 1.6e-5 of the image
+    // maximum on a lensed image; two levels keep it to ~2 sqrt(k).
+    for (int a = 0; a < k; ++a) {
+      float row[kConvT / kConvRows];
+#pragma unroll
+      for (int q = 0; q < kConvT / kConvRows; ++q) row[q] = 0.f;
+      for (int b = 0; b < k; ++b) {
+        const float kv = sK[a * k + b];
+#pragma unroll
+        for (int q = 0; q < kConvT / kConvRows; ++q) {
+          const int r = threadIdx.y + q * kConvRows;
+          row[q] = fmaf(kv, sT[(r + a) * tw + threadIdx.x + b], row[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kConvT / kConvRows; ++q) acc[q] += row[q];
     }
   }
 #pragma unroll
@@ -54,11 +78,11 @@ cudaError_t launch_conv(const float* in, float* out, int n_img, int ny, int nx, 
   if (n_img <= 0) return cudaSuccess;
   const int tw = kConvT + k - 1;
   const size_t smem = sizeof(float) * ((size_t)k * k + (size_t)tw * tw);
-  static thread_local size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  // The opt-in is an attribute of the kernel on the current device, so it is set before every
+  // launch that needs more than the default 48 KB (a cached flag would miss other devices).
+  if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   dim3 grid((nx + kConvT - 1) / kConvT, (ny + kConvT - 1) / kConvT, n_img);
   dim3 block(kConvT, kConvRows);
@@ -142,11 +166,9 @@ int conv_batch_grid(int sm_count, int kmax) {
 
 cudaError_t launch_conv_batch_meta(const BatchMeta* meta, int kmax, int grid, cudaStream_t st) {
   const size_t smem = conv_batch_smem(kmax);
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  if (smem > 48 * 1024) {  // per device, as in launch_conv
     cudaError_t e = cudaFuncSetAttribute(conv_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   conv_batch_kernel<<<grid, dim3(kConvT, kConvRows), smem, st>>>(const_cast<BatchMeta*>(meta));
   return cudaGetLastError();

@@ -277,11 +277,10 @@ cudaError_t launch_k(const float* in, float* out, int n_img, int ny, int nx, con
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * ((size_t)2 * A.tile_fl + (size_t)K * K);
   const int threads = A.tx_n * ty_n;
-  static thread_local size_t configured = 0;  // the largest dynamic shared memory enabled so far
-  if (smem > configured) {
+  // an attribute of the kernel on the current device: set before every launch that needs it
+  if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(conv_tma_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    configured = smem;
   }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tma_kernel<K>, threads, smem) != cudaSuccess ||

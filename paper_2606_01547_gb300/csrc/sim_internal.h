@@ -43,6 +43,12 @@ class DeviceGuard {
 int fail(lens_sim* s, int code, const char* fmt, ...);
 int cuda_fail(lens_sim* s, cudaError_t e, const char* what);
 bool is_device_ptr(const void* p);
+// True for device memory of a GPU other than the current one (a kernel launched here would
+// read it through a peer mapping, or fault without one).
+bool on_other_device(const void* p);
+// Grid checks of validate_system: 1..16384 pixels per side, supersampling in
+// [1, LENS_MAX_SUPERSAMPLE], a finite positive pixel scale and a finite centre.
+int validate_grid(lens_sim* s, const lens_grid& g);
 int ensure(lens_sim* s, DevBuffer& b, size_t bytes);
 void release(lens_sim* s, DevBuffer& b);
 int validate_system(lens_sim* s, const lens_system& y, bool need_grid);

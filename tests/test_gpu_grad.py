@@ -2,13 +2,18 @@
 oracle (exact dual-number gradient).
 
 Tolerances: logL within 1e-5 relative; the gradient within 1e-4 relative in the L-infinity
-norm (|g - g_ref|_inf <= 1e-4 |g_ref|_inf); and, as a guard against a wrong term in any one
-component, every component within 2e-3 of max(|g_ref_i|, 1e-2 |g_ref|_inf).  Components that
-are a few percent of the largest are sums of thousands of per-pixel terms with heavy
-cancellation, and the FP32 model image carries ~1e-6 relative evaluation error (EPL series,
-exp of Sersic exponents up to ~30), so their component-wise error reaches a few 1e-4 without
-any defect in the adjoint; the oracle's conditioning-floor mode (rounding alone) already
-moves some by 1e-4.
+norm (|g - g_ref|_inf <= 1e-4 |g_ref|_inf); and every component within max(1e-4, 2 floor_i)
+of max(|g_ref_i|, 1e-3 |g_ref|_inf), where floor_i is the component's conditioning floor: the
+larger of (a) the change the oracle's rounding mode makes (grid, deflection terms, traced
+positions and model image rounded to FP32) and (b) the first-order bound on the change of the
+exact gradient when each of the 15 FP32 parameters moves by one FP32 unit in the last place
+(relative 2^-23): sum_j |dG_i/dp_j| 2^-23 |p_j|, from central differences of the FP64
+gradient.  (b) is the forward error of an evaluation whose backward error is one ulp per
+parameter, the single-precision level: every FP32 evaluation derives the profiles' constants
+(axis ratios and angles from e1/e2, their cosines and sines, b = theta_E sqrt(q), the series
+ratio f, b_n, 1/n) and the per-sample deflections with functions accurate to an ulp or a few.
+Near the cusp of a compact high-index Sersic source the gradient is ill-conditioned at this
+level: (b) reaches 1e-3 for some components, while (a) alone stays near 1e-5 there.
 """
 import numpy as np
 import pytest
@@ -30,20 +35,39 @@ def sim():
     s.close()
 
 
+def _floor(pb, data, pts, Gr):
+    """Per-component conditioning floor (absolute) at the points `pts` (see the module notes):
+    the larger of the oracle's rounding-mode change and the first-order change of the exact
+    gradient under a one-ulp (2^-23 relative) perturbation of each parameter, summed over the
+    parameters (central differences of the FP64 gradient)."""
+    _, Gf = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts, fp32=True)
+    lin = np.zeros_like(Gr)
+    for j in range(15):
+        d = np.zeros_like(pts)
+        d[:, j] = np.abs(pts[:, j]) * 2.0 ** -23
+        _, Gp = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts + d)
+        _, Gm = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts - d)
+        lin += 0.5 * np.abs(Gp - Gm)
+    return np.maximum(np.abs(Gf - Gr), lin)
+
+
 def _check(sim, pb, data, idx, sub_table=-1):
     P = torch.from_numpy(pb.points).cuda()
     L, G = sim.grad(pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp, P, subhalo_table=sub_table)
     torch.cuda.synchronize()
     L = L.cpu().numpy()
     G = G.cpu().numpy()
-    Lr, Gr = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pb.points[idx])
+    pts = pb.points[idx].astype(np.float64)
+    Lr, Gr = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts)
+    floor = _floor(pb, data, pts, Gr)
     for n, i in enumerate(idx):
         assert abs(L[i] - Lr[n]) <= 1e-5 * abs(Lr[n]), (i, L[i], Lr[n])
         gmax = np.abs(Gr[n]).max()
         assert np.abs(G[i] - Gr[n]).max() <= 1e-4 * gmax, (i, np.abs(G[i] - Gr[n]).max() / gmax)
-        scale = np.maximum(np.abs(Gr[n]), 1e-2 * gmax)
+        scale = np.maximum(np.abs(Gr[n]), 1e-3 * gmax)
         err = np.abs(G[i] - Gr[n]) / scale
-        assert err.max() <= 2e-3, (i, err.argmax(), err.max(), G[i], Gr[n])
+        bound = np.maximum(1e-4, 2.0 * floor[n] / scale)
+        assert np.all(err <= bound), (i, (err / bound).argmax(), err, bound)
     return L, G
 
 
@@ -62,7 +86,7 @@ def test_differentiation_workload_sampled_points(sim):
     pb = W.diff_problem(42)
     data = W.observe(oracle.model_image(pb.system, pb.truth), pb.sigma_bkg, pb.t_exp, 42)
     tid = sim.register_subhalos(pb.system.subhalos)
-    L, G = _check(sim, pb, data, [0, 131, 257, 511], sub_table=tid)
+    L, G = _check(sim, pb, data, [0, 1, 2, 3, 131, 257, 384, 511], sub_table=tid)
     assert np.all(np.isfinite(L)) and np.all(np.isfinite(G))
 
 

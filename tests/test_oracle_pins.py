@@ -384,6 +384,48 @@ def test_loglike_reduces_to_gaussian_chi2_without_poisson_term():
     assert abs(L[0] + 0.5 * chi2) < 1e-9 * chi2
 
 
+def test_loglike_variance_model_matches_the_noise_law():
+    # Pins the pixel variance of the likelihood, sigma^2 = sigma_bkg^2 + max(m, 0)/t_exp, against
+    # the noise law itself: the observation generator draws Gaussian background noise of
+    # variance sigma_bkg^2 plus Poisson counts of mean max(m, 0) t_exp divided by t_exp, whose
+    # variance is max(m, 0)/t_exp.  Over many seeded draws at the truth, the oracle's
+    # (d - m)^2 / sigma^2 must then average 1 per pixel, separately in pixels dominated by the
+    # background and in pixels dominated by the Poisson term.  Each pixel group is isolated by
+    # setting the data of every other pixel to the model (zero residual there).
+    pb = _small_diff()
+    sb, t = 0.01, 100.0
+    m = oracle.model_image(pb.system, pb.truth)
+    mp = np.maximum(m, 0.0)
+    groups = {"background": mp / t <= 0.1 * sb ** 2, "poisson": mp / t >= 10.0 * sb ** 2}
+    assert all(g.sum() >= 30 for g in groups.values()), {k: int(g.sum()) for k, g in groups.items()}
+    n_seeds = 300
+    chi = {k: [] for k in groups}
+    alt = {("background", "data in place of the model"): [], ("poisson", "t_exp^2 in place of t_exp"): []}
+    for seed in range(n_seeds):
+        d = W.observe(m, sb, t, 5000 + seed).astype(np.float64)
+        for name, mask in groups.items():
+            dm = np.where(mask, d, m)
+            L = oracle.loglike(pb.system, dm, sb, t, pb.truth[None, :], grad=False)[0]
+            chi[name].append(-2.0 * L / mask.sum())
+        r2 = (d - m) ** 2
+        g = groups["background"]
+        alt[("background", "data in place of the model")].append(
+            np.mean(r2[g] / (sb ** 2 + np.maximum(d[g], 0.0) / t)))
+        g = groups["poisson"]
+        alt[("poisson", "t_exp^2 in place of t_exp")].append(np.mean(r2[g] / (sb ** 2 + mp[g] / t ** 2)))
+    for name, v in chi.items():
+        v = np.array(v)
+        se = v.std(ddof=1) / math.sqrt(n_seeds)
+        assert se < 0.03, (name, se)
+        assert abs(v.mean() - 1.0) < 5.0 * se, (name, v.mean(), se)
+    # the statistic separates the plausible misreadings of the variance by far more than its
+    # sampling error (computed here from the same draws, outside the oracle)
+    for (name, what), v in alt.items():
+        v = np.array(v)
+        se = np.array(chi[name]).std(ddof=1) / math.sqrt(n_seeds)
+        assert abs(v.mean() - 1.0) > 20.0 * se, (name, what, v.mean(), se)
+
+
 def test_conditioning_floor_mode_is_close_to_fp64():
     sysm = W.substructure_system(1, n_sub=200, nx=24, s=2, k=5)
     a = oracle.image(sysm)
