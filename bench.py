@@ -37,14 +37,55 @@ UNIT = "images/s"
 WORKLOAD = ("substructure image: 200x200 grid at 0.04\", supersampling 3 (360,000 traced points), "
             "EPL + shear, 10,000 truncated-NFW subhalos, elliptical Sersic, 21x21 Moffat PSF, FP32")
 N_SYSTEMS = 8            # distinct seeded systems cycled through the steps
-# Algorithmic work of one point-subhalo pair, frozen from the far-field series pair formula that
-# almost every pair takes: dx, dy (2 FADD); r^2 = dx^2 + dy^2 (FMUL, FFMA); u = rsqrt(r^2)
-# (1 MUFU); u^2 (FMUL); Horner over the 6 coefficients (5 FFMA); g = p u^2 (FMUL);
-# alpha += g (dx, dy) (2 FFMA)  ->  8 FFMA + 3 FMUL + 2 FADD = 21 FP32 flops (FMA = 2), 1 MUFU.
-FLOPS_PER_PAIR = 21
+# Algorithmic work of one point-subhalo pair, by the form the pair takes.  Far pairs (a unit's
+# bounding box beyond 7 max(tau, 1) Rs of the subhalo): dx, dy (2 FADD); r^2 = dx^2 + dy^2 (FMUL,
+# FFMA); u = rsqrt(r^2) (1 MUFU); u^2 (FMUL); Horner over the series coefficients; g = p u^2
+# (FMUL); alpha += g (dx, dy) (2 FFMA).  With c_0, c_2 .. c_K that is K - 1 Horner FFMA, so
+# 8 FFMA + 3 FMUL + 2 FADD = 21 flops (FMA = 2) for the 6-term series (from 7 max(tau, 1) Rs),
+# 17 for the 4-term series (from 20), 15 for the 3-term series (from 40).  Marked (near) pairs
+# evaluate the 6-term series and the 12-term annulus polynomial (t = a u + b, 11 Horner FFMA,
+# one FMUL) for every sample: 21 + 25 = 46 flops (the closed forms of the few samples within
+# 4 Rs are not counted).  One MUFU per pair in every form.
+FLOPS_BY_FORM = {"near": 46, "series6": 21, "series4": 17, "series3": 15}
+FLOPS_PER_PAIR = 21  # the 6-term series formula: the previous single-form ledger, reported beside
 KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh",
                   "paper_2606_01547_gb300/csrc/kernels.h")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trace_kernel_substructure_200x200_traffic.txt")
+
+
+def pair_census(system) -> dict:
+    """Pairs of a system by the form the trace kernel gives them: the class of each (work unit,
+    subhalo) follows from the distance of the unit's sample bounding box to the subhalo, against
+    7, 20 and 40 max(tau, 1) Rs (computed here in FP64; the kernel compares FP32 copies, so a
+    pair on a boundary may fall on the other side)."""
+    g = system.grid
+    s = g.s
+    bw, bh = {1: (24, 12), 2: (12, 6), 3: (8, 4), 4: (6, 3), 5: (5, 2), 6: (4, 2), 7: (5, 1)}.get(s, (2, 2))
+    cx, cy, rs, _, rt = system.subhalos.astype(np.float64)
+    tm = np.maximum(rt / rs, 1.0) * rs
+    counts = {k: 0 for k in FLOPS_BY_FORM}
+
+    def coord(c0, j, n, b):
+        return c0 + (j - 0.5 * (n - 1) + (b + 0.5) / s - 0.5) * g.dpix
+
+    for by in range((g.ny + bh - 1) // bh):
+        for bx in range((g.nx + bw - 1) // bw):
+            j1 = min(bx * bw + bw, g.nx) - 1
+            i1 = min(by * bh + bh, g.ny) - 1
+            npts = (j1 - bx * bw + 1) * (i1 - by * bh + 1) * s * s
+            xmin, xmax = coord(g.x0, bx * bw, g.nx, 0), coord(g.x0, j1, g.nx, s - 1)
+            ymin, ymax = coord(g.y0, by * bh, g.ny, 0), coord(g.y0, i1, g.ny, s - 1)
+            ddx = np.maximum(np.maximum(xmin - cx, cx - xmax), 0.0)
+            ddy = np.maximum(np.maximum(ymin - cy, cy - ymax), 0.0)
+            rho = np.hypot(ddx, ddy) / tm
+            counts["near"] += npts * int((rho < 7).sum())
+            counts["series6"] += npts * int(((rho >= 7) & (rho < 20)).sum())
+            counts["series4"] += npts * int(((rho >= 20) & (rho < 40)).sum())
+            counts["series3"] += npts * int((rho >= 40).sum())
+    total = sum(counts.values())
+    flops = sum(counts[k] * FLOPS_BY_FORM[k] for k in counts)
+    return {"pairs": total, "fractions": {k: v / total for k, v in counts.items()},
+            "flops": flops, "flops_per_pair": flops / total}
 
 
 def kernel_hash() -> str:
@@ -272,7 +313,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     clocks = clk.summary()
     max_mhz = clocks["sm_max_mhz"] or 2070.0
     peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
-    achieved = pairs * FLOPS_PER_PAIR / avg_trace_s / 1e12
+    census = pair_census(systems[0])
+    achieved = census["flops"] / avg_trace_s / 1e12
     traffic = None
     if os.path.exists(PROFILE_TRAFFIC):
         prof = dict(l.split(": ", 1) for l in open(PROFILE_TRAFFIC).read().splitlines()
@@ -285,7 +327,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz (derived, FP32 FMA)",
                 "frac_at_median_clock": (achieved / (sms * 128 * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
                                          if clocks["sm_mhz"] else None),
-                "pairs_per_s": pairs / avg_trace_s, "flops_per_pair": FLOPS_PER_PAIR,
+                "pairs_per_s": pairs / avg_trace_s, "flops_per_pair": census["flops_per_pair"],
+                "pair_forms": census["fractions"], "flops_by_form": FLOPS_BY_FORM,
+                "frac_21_flop_ledger": pairs * FLOPS_PER_PAIR / avg_trace_s / 1e12 / peak_tflops,
                 "trace_ms": avg_trace_s * 1e3,
                 # SFU: one MUFU.RSQ per pair against 16 MUFU results per clock per SM
                 "sfu": {"mufu_per_s": pairs / avg_trace_s, "peak_per_s": sms * 16 * max_mhz * 1e6,

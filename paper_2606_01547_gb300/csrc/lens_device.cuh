@@ -297,7 +297,14 @@ __device__ __forceinline__ float tnfw_g_far(float x2, float tau, float t2, float
 // 3e-6), and Horner in FP32 is well conditioned (sum |c_k y^k| / |G| < 1.1).
 constexpr int kFarTerms = 6;
 constexpr float kFarRadius = 7.f;  // the series' range: r >= kFarRadius max(tau, 1) Rs
-static_assert(kFarTerms >= 3 && kFarTerms <= 8, "the record holds d_0, d_2 .. d_8 in t2..t5");
+static_assert(kFarTerms >= 3 && kFarTerms <= 6, "the record holds d_0, d_2 .. d_6 in t2..t4");
+// Farther out the series converges faster, so fewer terms reach the same accuracy (largest
+// relative truncation error over tau in [0.1, 30], in FP64 against the closed form):
+//   c_0 .. c_6 from 7 max(tau, 1) Rs: 9.5e-7;  c_0 .. c_4 from 20: 2.3e-7;  c_0 .. c_3 from 40: 3.6e-7.
+// A subhalo takes the shortest series whose range holds every sample of a unit (its distance
+// to the unit's bounding box decides).
+constexpr float kFarRadius4 = 20.f;  // 4-term series (c_0, c_2, c_3, c_4) from here
+constexpr float kFarRadius3 = 40.f;  // 3-term series (c_0, c_2, c_3) from here
 constexpr int kSubStride = 8;   // float4 per subhalo record (staged through shared memory)
 constexpr int kMidTerms = 12;   // coefficients of the annulus polynomial
 constexpr int kMidStride = 3;   // float4 per subhalo in the annulus block
@@ -311,7 +318,8 @@ constexpr float kMidTauMax = 8.5f;
 // per instruction): centres negated and every series coefficient stored as a duplicated pair,
 //   t0 = (-cx, -cx, -cy, -cy),           t1 = (r_far^2 = 49 max(tau,1)^2 Rs^2, 1/Rs^2, tau, A),
 //   t2 = (d_0, d_0, d_2, d_2),  t3 = (d_3, d_3, d_4, d_4),  t4 = (d_5, d_5, d_6, d_6),
-//   t5 = 0 (room for d_7, d_8),  t6 = (a_t, b_t, r_in^2, C),  t7 = 0,
+//   t5 = (r_4^2, r_3^2, 0, 0): the ranges of the 4- and 3-term series (kFarRadius4 and
+//   kFarRadius3 times max(tau, 1) Rs, squared),  t6 = (a_t, b_t, r_in^2, C),  t7 = 0,
 // with A = alpha_Rs tau^2 / ((1 - ln 2) Rs (tau^2+1)^2), so that alpha = A g(x^2) (dx, dy), and
 // d_k = A c_k Rs^(k+2): the series then runs in u = 1/r with no per-pair scaling by 1/Rs^2.
 // C = tau pi + (tau^2-1) ln tau.  The annulus block holds the 12 coefficients e_0..e_11 of
@@ -361,7 +369,9 @@ __device__ __forceinline__ void tnfw_constants(float cx, float cy, float Rs, flo
   float seq[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // d_0, d_2, ..., d_kFarTerms
   seq[0] = d[0];
   for (int k = 2; k <= kFarTerms; ++k) seq[k - 1] = d[k];
-  for (int j = 0; j < 4; ++j) t[2 + j] = make_float4(seq[2 * j], seq[2 * j], seq[2 * j + 1], seq[2 * j + 1]);
+  for (int j = 0; j < 3; ++j) t[2 + j] = make_float4(seq[2 * j], seq[2 * j], seq[2 * j + 1], seq[2 * j + 1]);
+  const float tmR = tm * Rs;
+  t[5] = make_float4(kFarRadius4 * kFarRadius4 * tmR * tmR, kFarRadius3 * kFarRadius3 * tmR * tmR, 0.f, 0.f);
   t[6] = make_float4(at, bt, annulus ? 16.f * Rs * Rs : r_far2, C);
   t[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
@@ -465,6 +475,17 @@ __device__ __forceinline__ float tnfw_series(float r2, const float4* t) {
   return tnfw_series_u(u, u * u, t);
 }
 
+// The series truncated after d_K (K = 3 .. kFarTerms; K = kFarTerms is tnfw_series_u itself).
+template <int K>
+__device__ __forceinline__ float tnfw_series_k(float u, float u2, const float4* t) {
+  static_assert(K >= 3 && K <= kFarTerms, "series length");
+  float p = fmaf(tnfw_coef(t, K), u, tnfw_coef(t, K - 1));
+#pragma unroll
+  for (int k = K - 2; k >= 2; --k) p = fmaf(p, u, tnfw_coef(t, k));
+  p = fmaf(p, u2, tnfw_coef(t, 0));
+  return p * u2;
+}
+
 // Packed forms (two samples per instruction): element-wise the same operations, hence the same
 // rounding, as the scalar forms.
 __device__ __forceinline__ float2 tnfw_series2_u(float2 u, float2 u2, const float4* t) {
@@ -478,6 +499,16 @@ __device__ __forceinline__ float2 tnfw_series2_u(float2 u, float2 u2, const floa
 __device__ __forceinline__ float2 tnfw_series2(float2 r2, const float4* t) {
   const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
   return tnfw_series2_u(u, __fmul2_rn(u, u), t);
+}
+
+template <int K>
+__device__ __forceinline__ float2 tnfw_series2_k(float2 u, float2 u2, const float4* t) {
+  static_assert(K >= 3 && K <= kFarTerms, "series length");
+  float2 p = __ffma2_rn(tnfw_coef2(t, K), u, tnfw_coef2(t, K - 1));
+#pragma unroll
+  for (int k = K - 2; k >= 2; --k) p = __ffma2_rn(p, u, tnfw_coef2(t, k));
+  p = __ffma2_rn(p, u2, tnfw_coef2(t, 0));
+  return __fmul2_rn(p, u2);
 }
 
 // Annulus polynomial: A g = u^2 sum_j e_j t^j, t = a_t u + b_t (Horner in t).

@@ -11,6 +11,7 @@
 // Two launch forms share the unit body: one CTA per unit of a single system, and a persistent
 // kernel that pulls units of many systems from a device-side queue (largest cost first).
 #include <algorithm>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 
@@ -156,13 +157,16 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, off));
   }
   // 32 subhalos per shared-memory stage.  While staging, each lane tests its subhalo against
-  // the unit's bounding box; the ballot marks the subhalos some sample might see inside the
-  // far-field radius.  All other pairs take the straight-line series; marked subhalos let
-  // every sample pick its own form (the series again beyond the radius), so the result does
-  // not depend on the mask.
+  // the unit's bounding box: subhalos some sample might see inside the far-field radius are
+  // marked (near); the others take the shortest far-field series whose range holds the whole
+  // box (6 terms from 7, 4 from 20, 3 from 40 max(tau, 1) Rs).  Marked subhalos let every
+  // sample pick its own form (the 6-term series again beyond the radius).  The stage is summed
+  // class by class (6-, 4-, 3-term, then marked), each in subhalo order: an order fixed by the
+  // unit, so every launch form gives the same sums.
   for (int base = lo; base < hi; base += 32) {
     const int idx = base + lane;
     bool near = false;
+    int tier = 0;  // 0: 6-term series, 1: 4-term, 2: 3-term
     if (idx < hi) {
       float4 st[kSubStride];
 #pragma unroll
@@ -173,29 +177,39 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       // st[0] holds the negated centre
       const float ddx = fmaxf(fmaxf(xmin + st[0].x, -st[0].x - xmax), 0.f);
       const float ddy = fmaxf(fmaxf(ymin + st[0].z, -st[0].z - ymax), 0.f);
-      near = fmaf(ddx, ddx, ddy * ddy) < st[1].x;
+      const float d2 = fmaf(ddx, ddx, ddy * ddy);
+      near = d2 < st[1].x;
+      tier = d2 >= st[5].y ? 2 : (d2 >= st[5].x ? 1 : 0);
       if (near) {
 #pragma unroll
         for (int c = 0; c < kMidStride; ++c) area.mid[lane][c] = __ldg(mid_tab + (size_t)kMidStride * idx + c);
       }
     }
-    const unsigned near_mask = __ballot_sync(0xffffffffu, near);
-    __syncwarp();
     const int cnt = min(32, hi - base);
-    // far-field series for subhalo record t, all samples of the lane
-    auto far_pairs = [&](const float4* t) {
+    const unsigned live = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
+    const unsigned near_mask = __ballot_sync(0xffffffffu, near);
+    const unsigned m3 = __ballot_sync(0xffffffffu, !near && tier == 2) & live;
+    const unsigned m4 = __ballot_sync(0xffffffffu, !near && tier == 1) & live;
+    const unsigned m6 = live & ~(near_mask | m3 | m4);
+    __syncwarp();
+    // far-field series truncated after d_K for subhalo record t, all samples of the lane
+    auto far_pairs = [&](const float4* t, auto Kc) {
+      constexpr int K = decltype(Kc)::value;
       const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
 #pragma unroll
       for (int i = 0; i < kP; ++i) {
         const float2 dx = __fadd2_rn(px2[i], ncx), dy = __fadd2_rn(py2[i], ncy);
-        const float2 gg = tnfw_series2(__ffma2_rn(dx, dx, __fmul2_rn(dy, dy)), t);
+        const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+        const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+        const float2 gg = tnfw_series2_k<K>(u, __fmul2_rn(u, u), t);
         ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
         ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
       }
 #pragma unroll
       for (int i = 0; i < kS; ++i) {
         const float dx = pxs[i] + t[0].x, dy = pys[i] + t[0].z;
-        const float gg = tnfw_series(fmaf(dx, dx, dy * dy), t);
+        const float u = rsqrt_ftz(fmaf(dx, dx, dy * dy));
+        const float gg = tnfw_series_k<K>(u, u * u, t);
         axs[i] = fmaf(gg, dx, axs[i]);
         ays[i] = fmaf(gg, dy, ays[i]);
       }
@@ -233,41 +247,44 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
         ays[i] = fmaf(gg, dy, ays[i]);
       }
     };
-    auto one = [&](int q) {
-      float4 t[kSubStride];
+    // a class of far subhalos, kFuseSubhalos per basic block: the scheduler overlaps one's
+    // reciprocal square roots and loads with another's polynomial
+    auto far_class = [&](unsigned mask, auto Kc) {
+      constexpr int kRec = 5;  // t0..t4: centre and series coefficients
+      while (mask) {
+        const int q0 = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        if (kFuseSubhalos > 1 && mask) {
+          const int q1 = __ffs(mask) - 1;
+          mask &= mask - 1u;
+          float4 ta[kRec], tb[kRec];
 #pragma unroll
-      for (int c = 0; c < kSubStride; ++c) t[c] = area.sub[q][c];
-      if (!((near_mask >> q) & 1u)) {
-        far_pairs(t);
-      } else {
-        float4 m[kMidStride];
-#pragma unroll
-        for (int c = 0; c < kMidStride; ++c) m[c] = area.mid[q][c];
-        near_pairs(t, m);
-      }
-    };
-    int q = 0;
-    if constexpr (kFuseSubhalos > 1) {
-      // kFuseSubhalos far-field subhalos in one basic block: the scheduler overlaps one's
-      // reciprocal square roots and loads with another's polynomial (the sums still run in
-      // subhalo order)
-      constexpr unsigned kGroup = (1u << kFuseSubhalos) - 1u;
-      for (; q + kFuseSubhalos <= cnt; q += kFuseSubhalos) {
-        if (!((near_mask >> q) & kGroup)) {
-          float4 tg[kFuseSubhalos][kSubStride];
-#pragma unroll
-          for (int f = 0; f < kFuseSubhalos; ++f)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) tg[f][c] = area.sub[q + f][c];  // t0..t5: centre and series
-#pragma unroll
-          for (int f = 0; f < kFuseSubhalos; ++f) far_pairs(tg[f]);
+          for (int c = 0; c < kRec; ++c) {
+            ta[c] = area.sub[q0][c];
+            tb[c] = area.sub[q1][c];
+          }
+          far_pairs(ta, Kc);
+          far_pairs(tb, Kc);
         } else {
+          float4 ta[kRec];
 #pragma unroll
-          for (int f = 0; f < kFuseSubhalos; ++f) one(q + f);
+          for (int c = 0; c < kRec; ++c) ta[c] = area.sub[q0][c];
+          far_pairs(ta, Kc);
         }
       }
+    };
+    far_class(m6, std::integral_constant<int, kFarTerms>{});
+    far_class(m4, std::integral_constant<int, 4>{});
+    far_class(m3, std::integral_constant<int, 3>{});
+    for (unsigned mask = near_mask; mask; mask &= mask - 1u) {
+      const int q = __ffs(mask) - 1;
+      float4 t[kSubStride], m[kMidStride];
+#pragma unroll
+      for (int c = 0; c < kSubStride; ++c) t[c] = area.sub[q][c];
+#pragma unroll
+      for (int c = 0; c < kMidStride; ++c) m[c] = area.mid[q][c];
+      near_pairs(t, m);
     }
-    for (; q < cnt; ++q) one(q);
     __syncwarp();
   }
   // the warp's staged records are dead from here on: its partials take their place
