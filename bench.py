@@ -372,7 +372,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         extras["psf_conv"] = conv_extra(sim, W, dev)
         extras["psf_fft"] = fft_conv_extra(sim, W, dev)
         extras["subhalo_scaling"] = subhalo_scaling_extra(sim, W, dev)
-        extras["batched"] = batched_extra(sim, lenssim, W, dev, args.batch_systems)
+        extras["batched"] = batched_extra(sim, lenssim, W, dev, args.batch_systems,
+                                          single_pairs_per_s=roofline["pairs_per_s"])
         extras["batched_small_systems"] = batched_extra(sim, lenssim, W, dev, args.batch_systems, small=True)
         extras["differentiation"] = grad_extra(sim, W, dev)
         extras["fitting"] = fitting_extra(sim, W, dev)
@@ -408,10 +409,13 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     sim.close()
 
 
-def batched_extra(sim, lenssim, W, dev, n_sys: int, small: bool = False):
+def batched_extra(sim, lenssim, W, dev, n_sys: int, small: bool = False, single_pairs_per_s: float = 0.0):
     """Uneven batch (grids 64..256, s 1..3, 0..20,000 subhalos, PSF 5..31): one lens_sim_image
     call (persistent fused launches replayed from a CUDA graph) against a host loop of
-    single-system calls with a stream synchronisation per call, on the same device inputs."""
+    single-system calls with a stream synchronisation per call, on the same device inputs.  The
+    batched launch's schedule (persistent kernel form, unit-queue order) is autotuned on the
+    batch first.  The pair-rate ceiling is the images/s the batch would reach if all its pairs
+    ran at the single-image kernel's pair rate on the benchmark image."""
     import ctypes
     import torch
     if small:  # launch-bound mix: small grids and few subhalos
@@ -429,13 +433,21 @@ def batched_extra(sim, lenssim, W, dev, n_sys: int, small: bool = False):
     st = torch.cuda.current_stream()
     sp = int(st.cuda_stream)
     pairs = sum(s.pairs() for s in systems)
+    bf, bo = ctypes.c_int(), ctypes.c_int()
+    ms = (ctypes.c_float * (2 * len(lenssim.BATCH_FORMS)))()
+    rc = L.lens_sim_autotune_batch(sim.h, arr, n_sys, ptrs, 1, ctypes.byref(bf), ctypes.byref(bo), ms, sp)
+    if rc:
+        raise lenssim.LensSimError(rc, sim.last_error())
+    schedule = {"chosen": f"{lenssim.BATCH_FORMS[bf.value]}/{lenssim.BATCH_ORDERS[bo.value]}",
+                "ms": {f"{lenssim.BATCH_FORMS[f]}/{lenssim.BATCH_ORDERS[o]}": float(ms[2 * f + o])
+                       for f in range(len(lenssim.BATCH_FORMS)) for o in range(2)}}
 
     def batched():
         rc = L.lens_sim_image(sim.h, arr, n_sys, ptrs, sp)
         if rc:
             raise lenssim.LensSimError(rc, sim.last_error())
 
-    batched()  # capture + warm
+    batched()  # warm
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
@@ -451,12 +463,17 @@ def batched_extra(sim, lenssim, W, dev, n_sys: int, small: bool = False):
             raise lenssim.LensSimError(rc, sim.last_error())
         st.synchronize()
     t_plain = time.perf_counter() - t0
-    return {"systems": n_sys, "images_per_s": n_sys / t_batch, "plain_images_per_s": n_sys / t_plain,
-            "speedup_vs_plain": t_plain / t_batch, "pairs_per_s": pairs / t_batch,
-            "batch_s": t_batch, "plain_s": t_plain,
-            "workload": ("grids 64^2, s in {1,2,3}, subhalos log-uniform in [0,100], PSF 5..31" if small else
-                         "grids {64,100,128,200,256}^2, s in {1,2,3}, subhalos log-uniform in [0,20000], PSF 5..31")
-                        + "; one graph launch vs per-image calls with a sync each"}
+    out = {"systems": n_sys, "images_per_s": n_sys / t_batch, "plain_images_per_s": n_sys / t_plain,
+           "speedup_vs_plain": t_plain / t_batch, "pairs_per_s": pairs / t_batch,
+           "plain_pairs_per_s": pairs / t_plain, "batch_s": t_batch, "plain_s": t_plain, "schedule": schedule,
+           "workload": ("grids 64^2, s in {1,2,3}, subhalos log-uniform in [0,100], PSF 5..31" if small else
+                        "grids {64,100,128,200,256}^2, s in {1,2,3}, subhalos log-uniform in [0,20000], PSF 5..31")
+                       + "; one graph launch vs per-image calls with a sync each"}
+    if single_pairs_per_s > 0:
+        ceiling = n_sys * single_pairs_per_s / pairs
+        out["pair_rate_ceiling"] = {"images_per_s": ceiling, "speedup_vs_plain": ceiling * t_plain / n_sys,
+                                    "single_image_pairs_per_s": single_pairs_per_s}
+    return out
 
 
 def _rel_linf(a, b) -> float:

@@ -187,6 +187,21 @@ int lens_sim_autotune(lens_sim* sim, const lens_system* sample, int reps, int* b
                       float* ms_per_variant, int n_ms, void* stream);
 int lens_sim_set_variant(lens_sim* sim, int variant);
 
+/* Schedule of the batched launch (lens_sim_image with n_sys > 1; the batched configuration of
+ * the paper's workloads): `form` is the persistent trace kernel (0: CTAs of 4 warps summing a
+ * unit's 8 subhalo slices in two passes; 1: CTAs of 8 warps; 2: clusters of 2 CTAs x 4 warps),
+ * `order` the unit queue (0: systems by per-unit cost, largest first; 1: as given).  Every
+ * schedule gives bitwise-identical images.  lens_sim_autotune_batch runs the batch once per
+ * schedule to warm it up, then times `reps` calls (CUDA events on `stream`, synchronising it),
+ * makes the fastest the handle's schedule and returns it; `ms` (may be NULL) receives the mean
+ * milliseconds per call of the 2 * LENS_BATCH_FORMS schedules, indexed form * 2 + order.  The
+ * outputs receive the batch's images.  Needs n_sys >= 2; on an error the schedule is left as it
+ * was. */
+#define LENS_BATCH_FORMS 3
+int lens_sim_set_batch_schedule(lens_sim* sim, int form, int order);
+int lens_sim_autotune_batch(lens_sim* sim, const lens_system* systems, int n_sys, float* const* out_images,
+                            int reps, int* best_form, int* best_order, float* ms, void* stream);
+
 /* PSF method of lens_sim_image (single system) and lens_sim_convolve.  LENS_CONV_DIRECT: tiled
  * direct convolution.  LENS_CONV_FFT: FFT convolution (the paper's method for large kernels):
  * radix-2 transforms on a grid padded to powers of two >= (n + (k-1)/2) in each direction,

@@ -53,7 +53,8 @@ int capture_batch_graph(lens_sim* s, int kmax) {
   if (e != cudaSuccess) return cuda_fail(s, e, "begin capture");
   prep_batch_meta_kernel<<<s->sm_count * 4, 256, 0, s->cap_stream>>>(meta);
   cudaError_t e1 = cudaGetLastError();
-  cudaError_t e2 = launch_trace_batch_meta(meta, trace_batch_grid(s->sm_count), s->cap_stream);
+  cudaError_t e2 = launch_trace_batch_meta(meta, s->batch_form, trace_batch_grid(s->sm_count, s->batch_form),
+                                           s->cap_stream);
   cudaError_t e3 = launch_conv_batch_meta(meta, kmax, conv_batch_grid(s->sm_count, kmax), s->cap_stream);
   e = cudaStreamEndCapture(s->cap_stream, &graph);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e != cudaSuccess) {
@@ -69,6 +70,7 @@ int capture_batch_graph(lens_sim* s, int kmax) {
   }
   s->graph_meta = s->batch_meta.p;
   s->graph_kmax = kmax;
+  s->graph_form = s->batch_form;
   return LENS_OK;
 }
 
@@ -101,7 +103,8 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
   }
   kmax = std::max(kmax, s->res->kmax());  // graph smem covers every registered PSF
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  if (s->batch_order == 0)  // the longest units first (otherwise the queue keeps the given order)
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
 
   // ---- device workspace (metadata block, tables, raw copies, unconvolved images, staging)
   const size_t meta_bytes = align256(sizeof(BatchMeta)) + align256(sizeof(DevSystem) * n) +
@@ -227,7 +230,7 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
   if (e != cudaSuccess) return cuda_fail(s, e, "record staging event");
 
   // ---- launch the captured graph (re-captured if the workspace moved or a PSF grew)
-  if (!s->graph_exec || s->graph_meta != s->batch_meta.p || s->graph_kmax < kmax) {
+  if (!s->graph_exec || s->graph_meta != s->batch_meta.p || s->graph_kmax < kmax || s->graph_form != s->batch_form) {
     if ((rc = capture_batch_graph(s, std::max(kmax, s->graph_kmax)))) return rc;
   }
   e = cudaGraphLaunch(s->graph_exec, st);
@@ -250,3 +253,68 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
 }
 
 }  // namespace ls
+
+extern "C" {
+
+int lens_sim_set_batch_schedule(lens_sim* s, int form, int order) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (form < 0 || form >= ls::kBatchForms || order < 0 || order > 1)
+    return ls::fail(s, LENS_ERR_INVALID_ARG, "batch schedule (%d, %d) not in [0, %d) x [0, 1]", form, order,
+                    ls::kBatchForms);
+  s->batch_form = form;
+  s->batch_order = order;
+  return LENS_OK;
+}
+
+int lens_sim_autotune_batch(lens_sim* s, const lens_system* systems, int n_sys, float* const* out_images, int reps,
+                            int* best_form, int* best_order, float* ms, void* stream) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (!systems || !out_images || !best_form || !best_order || n_sys < 2 || reps < 1 || reps > 1000)
+    return ls::fail(s, LENS_ERR_INVALID_ARG, "bad batch autotune arguments (at least 2 systems)");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return ls::cuda_fail(s, cudaGetLastError(), "create event");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ls::cuda_fail(s, cudaGetLastError(), "create event");
+  }
+  const int form0 = s->batch_form, order0 = s->batch_order;
+  float best = 3.0e38f;
+  int bf = form0, bo = order0, rc = LENS_OK;
+  for (int f = 0; f < ls::kBatchForms && rc == LENS_OK; ++f) {
+    for (int o = 0; o < 2 && rc == LENS_OK; ++o) {
+      s->batch_form = f;
+      s->batch_order = o;
+      rc = lens_sim_image(s, systems, n_sys, out_images, stream);  // warm-up (captures the graph)
+      if (rc) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == LENS_OK; ++r) rc = lens_sim_image(s, systems, n_sys, out_images, stream);
+      cudaEventRecord(e1, st);
+      if (rc) break;
+      cudaError_t e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e != cudaSuccess) {
+        rc = ls::cuda_fail(s, e, "batch autotune timing");
+        break;
+      }
+      t /= (float)reps;
+      if (ms) ms[f * 2 + o] = t;
+      if (t < best) {
+        best = t;
+        bf = f;
+        bo = o;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->batch_form = rc ? form0 : bf;
+  s->batch_order = rc ? order0 : bo;
+  if (rc) return rc;
+  *best_form = bf;
+  *best_order = bo;
+  return LENS_OK;
+}
+
+}  // extern "C"

@@ -38,24 +38,14 @@ struct BatchMeta {
   const ConvJob* conv;       // [n_conv + 1], the last entry's tile0 = total tiles
 };
 
-// Launch shape of the fused trace kernel: `nw` warps per CTA split the subhalo list of one
-// unit; `pts` samples per lane.
-struct TraceShape {
-  int nw;
-  int pts;
-};
-
-TraceShape choose_trace_shape(int nx, int ny, int s, int n_sub, int sm_count);
-
 // Per-subhalo constants from a SoA [5][ld] table (cx, cy, Rs, alpha_Rs, r_t).
 cudaError_t launch_tnfw_prep(const float* soa, int n, int ld, float4* table, cudaStream_t st);
 
 // Trace units of a system (one CTA per unit in the single-system launch).
 int unit_count(int nx, int ny, int s);
 
-// Fused ray-trace + subhalo sum + Sersic + supersample bin-down of one system into sys.out.
-cudaError_t launch_trace(const DevSystem& sys, TraceShape shape, cudaStream_t st);
-// The same with an explicit launch variant (all variants give bitwise-identical images):
+// Fused ray-trace + subhalo sum + Sersic + supersample bin-down of one system into sys.out, by
+// launch variant (all variants give bitwise-identical images):
 // 0 one CTA of 8 warps per unit, 1 one CTA of 4 warps summing the 8 slices in two passes,
 // 2 a cluster of 2 CTAs x 4 warps per unit, 3 a cluster of 4 CTAs x 2 warps per unit,
 // 4 a cluster of 8 single-warp CTAs per unit.
@@ -64,9 +54,13 @@ cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t
 const char* trace_variant_name(int v);
 
 // Persistent batched trace over device descriptors; units are numbered by unit_prefix
-// ([n_sys + 1] ints) and handed out through *counter (zeroed before the launch).
-int trace_batch_grid(int sm_count);
-cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int grid, cudaStream_t st);
+// ([n_sys + 1] ints) and handed out through the header's counter (zeroed by each call's header
+// copy).  Forms (bitwise-identical images): 0 CTAs of 4 warps in two passes, 1 CTAs of 8 warps,
+// 2 clusters of 2 CTAs x 4 warps.
+constexpr int kBatchForms = 3;
+const char* batch_form_name(int form);
+int trace_batch_grid(int sm_count, int form);
+cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int form, int grid, cudaStream_t st);
 
 // Summed subhalo deflection at every sample of the grid (main deflectors excluded), in the
 // order ((row * nx + column) * s + sub-row) * s + sub-column; the same sum as the image kernels.

@@ -114,6 +114,8 @@ struct lens_sim {
   int max_batch = 4096;
   int sm_count = 0;
   int trace_variant = 0;  // launch variant of the single-system trace kernel
+  int batch_form = 0;     // persistent trace kernel of the batched launch (kBatchForms)
+  int batch_order = 0;    // unit queue: 0 systems by per-unit cost (largest first), 1 as given
   int conv_method = 0;    // LENS_CONV_AUTO / _DIRECT / _FFT
   int* wait_flag_h = nullptr;  // host-mapped flag raised by an expired bounded device wait
   int* wait_flag_d = nullptr;
@@ -151,4 +153,5 @@ struct lens_sim {
   cudaGraphExec_t graph_exec = nullptr;
   void* graph_meta = nullptr;
   int graph_kmax = 0;
+  int graph_form = -1;
 };

@@ -430,9 +430,23 @@ trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
   cluster.sync();  // peers keep their shared memory alive until the leader has read it
 }
 
-// Persistent form: CTAs pull unit tickets from the header's counter; ticket u belongs to the
-// system whose prefix range [unit_prefix[i], unit_prefix[i+1]) contains it.  Systems arrive
-// ordered by per-unit cost (largest first), so the queue hands out the longest units first.
+// Persistent forms of the batched launch: CTAs (or clusters) pull unit tickets from the
+// header's counter; ticket u belongs to the system whose prefix range [unit_prefix[i],
+// unit_prefix[i+1]) contains it.  Every form sums a unit's 8 slices with the same warps' code and
+// reduces them in slice order, so a system's image is bitwise that of its single-system call.
+//   form 0: CTAs of 4 warps summing the 8 slices in two passes (4 CTAs per SM);
+//   form 1: CTAs of 8 warps, one slice each (2 CTAs per SM);
+//   form 2: clusters of 2 CTAs x 4 warps, the leader finishing the unit through distributed
+//           shared memory (the single-image cluster2x4 form made persistent).
+__device__ __forceinline__ int batch_system_of(const int* __restrict__ unit_prefix, int n_sys, int u) {
+  int lo = 0, hi = n_sys;  // largest i with unit_prefix[i] <= u
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (unit_prefix[mid] <= u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_batch_kernel(BatchMeta* __restrict__ meta) {
   __shared__ TraceSmem<kTraceWarps> sm;
   __shared__ int s_ticket;
@@ -446,23 +460,61 @@ __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_batch_kernel(BatchMe
     const int u = s_ticket;
     __syncthreads();
     if (u >= total) return;
-    int lo = 0, hi = n_sys;  // largest i with unit_prefix[i] <= u
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (unit_prefix[mid] <= u) lo = mid; else hi = mid;
-    }
-    trace_unit_2pass(systems[lo], u - unit_prefix[lo], sm);
+    const int i = batch_system_of(unit_prefix, n_sys, u);
+    trace_unit_2pass(systems[i], u - unit_prefix[i], sm);
   }
 }
 
-TraceShape choose_trace_shape(int nx, int ny, int s, int n_sub, int sm_count) {
-  (void)nx; (void)ny; (void)s; (void)n_sub; (void)sm_count;
-  // The subhalo split (kTraceWarps slices) is the same for every system and launch form, so a
-  // system's image does not depend on the variant, the launch form or the rest of a batch.
-  TraceShape sh;
-  sh.nw = kTraceWarps;
-  sh.pts = kUnitPts;
-  return sh;
+__global__ void __launch_bounds__(32 * kTraceWarps, 2) trace_batch8_kernel(BatchMeta* __restrict__ meta) {
+  __shared__ TraceSmem<kTraceWarps> sm;
+  __shared__ int s_ticket;
+  const int n_sys = meta->n_sys;
+  const int* __restrict__ unit_prefix = meta->unit_prefix;
+  const DevSystem* __restrict__ systems = meta->systems;
+  const int total = unit_prefix[n_sys];
+  for (;;) {
+    if (threadIdx.x == 0) s_ticket = (int)atomicAdd(&meta->trace_counter, 1u);
+    __syncthreads();
+    const int u = s_ticket;
+    __syncthreads();
+    if (u >= total) return;
+    const int i = batch_system_of(unit_prefix, n_sys, u);
+    trace_unit(systems[i], u - unit_prefix[i], sm);
+  }
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * kHalfWarps, 4)
+trace_batch_cluster_kernel(BatchMeta* __restrict__ meta) {
+  constexpr int NWC = kHalfWarps;
+  __shared__ TraceSmem<NWC> sm;
+  __shared__ int s_ticket;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int* leader_ticket = cluster.map_shared_rank(&s_ticket, 0);
+  const int n_sys = meta->n_sys;
+  const int* __restrict__ unit_prefix = meta->unit_prefix;
+  const DevSystem* __restrict__ systems = meta->systems;
+  const int total = unit_prefix[n_sys];
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) s_ticket = (int)atomicAdd(&meta->trace_counter, 1u);
+    cluster.sync();
+    const int u = *leader_ticket;
+    cluster.sync();  // both CTAs hold the ticket before the leader takes the next one
+    if (u >= total) return;
+    const int i = batch_system_of(unit_prefix, n_sys, u);
+    const DevSystem& sys = systems[i];
+    const UnitGeom g = unit_geom(sys, u - unit_prefix[i]);
+    unit_partials<NWC>(sys, g, rank * NWC, sm);
+    cluster.sync();
+    if (rank == 0) {
+      const TraceSmem<NWC>* peers[2] = {cluster.map_shared_rank(&sm, 0), cluster.map_shared_rank(&sm, 1)};
+      unit_finalize(sys, g, sm.I, 32 * NWC,
+                    [&](int sl, int k, int l) { return peers[sl / NWC]->wa[sl % NWC].part[k][l]; });
+      __syncthreads();
+      unit_bin_down(sys, g, sm.I, 32 * NWC);
+    }
+    cluster.sync();  // the peer keeps its partials until the leader has read them
+  }
 }
 
 const char* trace_variant_name(int v) {
@@ -493,25 +545,42 @@ cudaError_t launch_subhalo_field(const DevSystem& sys, float2* out, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace(const DevSystem& sys, TraceShape shape, cudaStream_t st) {
-  (void)shape;
-  return launch_trace_variant(sys, 0, st);
-}
 
-int trace_batch_grid(int sm_count) {
-  static int blocks_per_sm = 0;
-  if (!blocks_per_sm) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, trace_batch_kernel,
-                                                      32 * kHalfWarps, 0) != cudaSuccess || blocks_per_sm < 1) {
-      cudaGetLastError();
-      blocks_per_sm = 1;
-    }
+const char* batch_form_name(int form) {
+  switch (form) {
+    case 0: return "cta4x2pass";
+    case 1: return "cta8";
+    case 2: return "cluster2x4";
+    default: return "?";
   }
-  return sm_count * blocks_per_sm;
 }
 
-cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int grid, cudaStream_t st) {
-  trace_batch_kernel<<<grid, 32 * kHalfWarps, 0, st>>>(const_cast<BatchMeta*>(meta));
+int trace_batch_grid(int sm_count, int form) {
+  static int per_sm[kBatchForms] = {0, 0, 0};
+  if (form < 0 || form >= kBatchForms) form = 0;
+  if (!per_sm[form]) {
+    int v = 0;
+    cudaError_t e = cudaSuccess;
+    if (form == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch_kernel, 32 * kHalfWarps, 0);
+    if (form == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch8_kernel, 32 * kTraceWarps, 0);
+    if (form == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch_cluster_kernel, 32 * kHalfWarps, 0);
+    if (e != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = form == 1 ? 1 : 2;
+    }
+    if (form == 2) v &= ~1;  // whole clusters
+    per_sm[form] = v < 1 ? 2 : v;
+  }
+  return sm_count * per_sm[form];
+}
+
+cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int form, int grid, cudaStream_t st) {
+  BatchMeta* m = const_cast<BatchMeta*>(meta);
+  switch (form) {
+    case 1: trace_batch8_kernel<<<grid, 32 * kTraceWarps, 0, st>>>(m); break;
+    case 2: trace_batch_cluster_kernel<<<grid, 32 * kHalfWarps, 0, st>>>(m); break;
+    default: trace_batch_kernel<<<grid, 32 * kHalfWarps, 0, st>>>(m); break;
+  }
   return cudaGetLastError();
 }
 

@@ -32,11 +32,14 @@ MAX_DEFLECTORS = 8
 CONV_METHODS = {"auto": 0, "direct": 1, "fft": 2}
 CONV_FFT_MIN_K = 33   # LENS_CONV_FFT_MIN_K: auto takes the FFT from this kernel size on
 TRACE_VARIANTS = ("cta8", "cta4x2pass", "cluster2x4", "cluster4x2", "cluster8x1")
+BATCH_FORMS = ("cta4x2pass", "cta8", "cluster2x4")   # LENS_BATCH_FORMS persistent trace kernels
+BATCH_ORDERS = ("cost_desc", "given")
 _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
             "lens_sim_register_subhalos", "lens_sim_image", "lens_sim_deflection", "lens_sim_convolve",
-            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_set_conv_method", "lens_sim_grad",
+            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_set_batch_schedule", "lens_sim_autotune_batch",
+            "lens_sim_set_conv_method", "lens_sim_grad",
             "lens_sim_linear_amp",
             "lens_sim_image_noalloc", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
             "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats", "lens_serve_last_error",
@@ -121,6 +124,9 @@ def lib():
             L.lens_sim_autotune.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(ip),
                                             ctypes.POINTER(fp), ip, vp]
             L.lens_sim_set_variant.argtypes = [vp, ip]
+            L.lens_sim_set_batch_schedule.argtypes = [vp, ip, ip]
+            L.lens_sim_autotune_batch.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(vp), ip,
+                                                  ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(fp), vp]
             L.lens_sim_set_conv_method.argtypes = [vp, ctypes.c_int]
             L.lens_sim_image_noalloc.argtypes = [ctypes.POINTER(LensSystemC), vp, ip, vp, vp]
             L.lens_sim_linear_amp.argtypes = [vp, ctypes.POINTER(LensSystemC), vp, fp, fp, vp, ip, vp, vp, vp]
@@ -304,6 +310,56 @@ class Simulator:
                                               len(TRACE_VARIANTS), _stream_ptr(stream)))
         entry = {"variant": best.value, "name": TRACE_VARIANTS[best.value],
                  "ms": {TRACE_VARIANTS[i]: float(ms[i]) for i in range(len(TRACE_VARIANTS))}}
+        if use_cache:
+            cache[key] = entry
+            os.makedirs(os.path.dirname(_TUNE_CACHE), exist_ok=True)
+            tmp = _TUNE_CACHE + f".tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(cache, fh, indent=1)
+            os.replace(tmp, _TUNE_CACHE)
+        return entry
+
+    def set_batch_schedule(self, form: int, order: int = 0) -> None:
+        """Persistent trace kernel form (BATCH_FORMS index) and unit-queue order of batched calls."""
+        self._check(self._L.lens_sim_set_batch_schedule(self.h, int(form), int(order)))
+
+    def autotune_batch(self, systems, out: Optional[List] = None, reps: int = 3, use_cache: bool = True,
+                       stream=None):
+        """Pick the fastest schedule of the batched launch for batches shaped like `systems`.
+
+        Results are cached per GPU name and batch bucket (system count and mean pair count, each
+        rounded to a power of two, the largest grid and supersampling) in _build/autotune.json."""
+        import json
+        n = len(systems)
+        pairs = sum(s_.pairs() for s_ in systems) / max(n, 1)
+        bucket = (f"batch/n{1 << max(n, 1).bit_length()}/pairs{1 << int(max(pairs, 1)).bit_length()}"
+                  f"/nx{max(s_.grid.nx for s_ in systems)}/s{max(s_.grid.s for s_ in systems)}")
+        key = f"{torch.cuda.get_device_name(self.device)}|{bucket}"
+        cache = {}
+        if use_cache and os.path.exists(_TUNE_CACHE):
+            try:
+                cache = json.load(open(_TUNE_CACHE))
+            except (OSError, ValueError):
+                cache = {}
+        if use_cache and key in cache:
+            self.set_batch_schedule(cache[key]["form"], cache[key]["order"])
+            return cache[key]
+        keep: list = []
+        arr = (LensSystemC * n)()
+        for i, s_ in enumerate(systems):
+            arr[i] = self.system_struct(s_, keep)
+        if out is None:
+            out = [torch.empty((s_.grid.ny, s_.grid.nx), dtype=torch.float32, device=f"cuda:{self.device}")
+                   for s_ in systems]
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in out])
+        bf, bo = ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_float * (2 * len(BATCH_FORMS)))()
+        self._check(self._L.lens_sim_autotune_batch(self.h, arr, n, ptrs, int(reps), ctypes.byref(bf),
+                                                    ctypes.byref(bo), ms, _stream_ptr(stream)))
+        entry = {"form": bf.value, "order": bo.value,
+                 "name": f"{BATCH_FORMS[bf.value]}/{BATCH_ORDERS[bo.value]}",
+                 "ms": {f"{BATCH_FORMS[f]}/{BATCH_ORDERS[o]}": float(ms[2 * f + o])
+                        for f in range(len(BATCH_FORMS)) for o in range(2)}}
         if use_cache:
             cache[key] = entry
             os.makedirs(os.path.dirname(_TUNE_CACHE), exist_ok=True)

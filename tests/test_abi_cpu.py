@@ -75,6 +75,9 @@ def test_binding_constants_match_the_header():
     assert _define(text, "LENS_CONV_FFT_MIN_K") == lenssim.CONV_FFT_MIN_K
     kern = open(os.path.join(ROOT, "paper_2606_01547_gb300", "csrc", "kernels.h")).read()
     assert int(re.search(r"kTraceVariants\s*=\s*(\d+)", kern).group(1)) == len(lenssim.TRACE_VARIANTS)
+    assert _define(text, "LENS_TRACE_VARIANTS") == len(lenssim.TRACE_VARIANTS)
+    assert int(re.search(r"kBatchForms\s*=\s*(\d+)", kern).group(1)) == len(lenssim.BATCH_FORMS)
+    assert _define(text, "LENS_BATCH_FORMS") == len(lenssim.BATCH_FORMS)
     # every profile the library takes has a parameter layout in the input generators
     for name in list(lenssim.LENS_TYPES) + list(lenssim.LIGHT_TYPES):
         assert name in workloads.N_PARAMS, name

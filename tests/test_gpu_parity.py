@@ -506,6 +506,34 @@ def test_batched_largest_system_matches_oracle_rows(sim):
         assert np.abs(got[row] - ref[0]).max() / np.abs(ref).max() <= max(1e-5, 2 * fl)
 
 
+def test_every_batch_schedule_gives_the_same_images_and_autotune_picks_one(sim):
+    # each persistent kernel form and unit-queue order of the batched launch, on an uneven batch
+    # with every unit shape (s = 1..3, ragged grids, systems without subhalos or PSF): bitwise
+    # equal images, equal to single-system calls; the autotuner times all six and keeps one
+    from paper_2606_01547_gb300 import lenssim
+    systems = W.batched_systems(77, count=9, max_sub=1500, grids=(24, 37, 64))
+    systems.append(W.LensSystem(W.Grid(30, 22, 2, 0.04), systems[0].deflectors, np.zeros((5, 0), np.float32),
+                                systems[0].source, None))
+    single = [gpu_image(sim, y) for y in systems]
+    for form in range(len(lenssim.BATCH_FORMS)):
+        for order in range(2):
+            sim.set_batch_schedule(form, order)
+            outs = sim.image(systems)
+            torch.cuda.synchronize()
+            for got, ref in zip(outs, single):
+                np.testing.assert_array_equal(got.cpu().numpy(), ref)
+    entry = sim.autotune_batch(systems, reps=1, use_cache=False)
+    assert entry["name"].split("/")[0] in lenssim.BATCH_FORMS and all(v > 0 for v in entry["ms"].values())
+    outs = sim.image(systems)
+    torch.cuda.synchronize()
+    for got, ref in zip(outs, single):
+        np.testing.assert_array_equal(got.cpu().numpy(), ref)
+    with pytest.raises(lenssim.LensSimError) as ei:
+        sim.set_batch_schedule(len(lenssim.BATCH_FORMS), 0)
+    assert ei.value.code == lenssim.LENS_ERR_INVALID_ARG
+    sim.set_batch_schedule(0, 0)
+
+
 def test_invalid_arguments_are_rejected(sim):
     from paper_2606_01547_gb300 import lenssim
     base = W.plain_system()
