@@ -77,13 +77,19 @@ cudaError_t launch_conv(const float* in, float* out, int n_img, int ny, int nx, 
 // TMA form of the convolution for batches of equal-size images (odd k <= 31, nx % 4 == 0,
 // 16-byte aligned buffers).  `err` is a host-mapped flag raised if a bounded wait expires.
 bool conv_tma_supported(const float* in, const float* out, int ny, int nx, int k);
-// FFT convolution (psf_fft.cu): padded sizes (false if beyond 1024), workspace per image,
-// kernel spectrum (work: k * Mx float2; Kf: My * Mx float2), convolution (A, B: n_img * ny * Mx float2).
+// FFT convolution (psf_fft.cu): padded sizes (false if beyond 1024); the central core x core taps
+// the caller convolves directly for large kernels (0: none); workspace per image (the images' half
+// spectra); the kernel's spectrum (its wings' half spectrum, then the core taps) and the work
+// space that computes it; the convolution, added to `out` when accumulate is set.
 bool conv_fft_sizes(int ny, int nx, int k, int* My, int* Mx);
+int conv_fft_core(int k);
 size_t conv_fft_bytes_per_image(int ny, int Mx);
-cudaError_t launch_fft_spectrum(const float* K, int k, int My, int Mx, float2* work, float2* Kf, cudaStream_t st);
+size_t conv_fft_spectrum_bytes(int My, int Mx, int k);
+size_t conv_fft_spectrum_work_bytes(int Mx, int k);
+cudaError_t launch_fft_spectrum(const float* K, int k, int My, int Mx, void* work, void* spec, cudaStream_t st);
+const float* conv_fft_core_kernel(const void* spec, int My, int Mx);
 cudaError_t launch_conv_fft(const float* in, float* out, int n_img, int ny, int nx, int k, int My, int Mx,
-                            const float2* Kf, float2* A, float2* B, cudaStream_t st);
+                            const void* spec, float2* A, int accumulate, cudaStream_t st);
 cudaError_t launch_conv_tma(const float* in, float* out, int n_img, int ny, int nx, const float* K, int k, int* err,
                             int sm_count, cudaStream_t st);
 

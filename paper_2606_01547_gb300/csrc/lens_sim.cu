@@ -340,26 +340,35 @@ int psf_apply(lens_sim* s, const float* in, float* out, int n_img, int ny, int n
     for (auto& f : s->spectra)
       if (f.psf_id == psf_id && f.My == My && f.Mx == Mx) spec = &f;
     const size_t per_img = conv_fft_bytes_per_image(ny, Mx);
-    const size_t want_ws = std::max(per_img * (size_t)std::min(n_img, 64), sizeof(float2) * (size_t)p.k * Mx);
+    const size_t want_ws = std::max(per_img * (size_t)std::min(n_img, 64), conv_fft_spectrum_work_bytes(Mx, p.k));
     int rc;
     if ((rc = ensure(s, s->fft_ws, want_ws))) return rc;
     if (!spec) {
       s->spectra.push_back({psf_id, My, Mx, DevBuffer{}});
       spec = &s->spectra.back();
-      if ((rc = ensure(s, spec->buf, sizeof(float2) * (size_t)My * Mx))) {
+      if ((rc = ensure(s, spec->buf, conv_fft_spectrum_bytes(My, Mx, p.k)))) {
         s->spectra.pop_back();
         return rc;
       }
-      e = launch_fft_spectrum(p.d, p.k, My, Mx, (float2*)s->fft_ws.p, (float2*)spec->buf.p, st);
+      e = launch_fft_spectrum(p.d, p.k, My, Mx, s->fft_ws.p, spec->buf.p, st);
       if (e != cudaSuccess) return cuda_fail(s, e, "FFT spectrum of the PSF");
+    }
+    // large kernels: the central core directly (exact-order sum), the wings by FFT, added
+    const int core = conv_fft_core(p.k);
+    if (core > 0) {
+      const float* kc = conv_fft_core_kernel(spec->buf.p, My, Mx);
+      if (allow_tma && conv_tma_supported(in, out, ny, nx, core))
+        e = launch_conv_tma(in, out, n_img, ny, nx, kc, core, s->wait_flag_d, s->sm_count, st);
+      else
+        e = launch_conv(in, out, n_img, ny, nx, kc, core, 1, st);
+      if (e != cudaSuccess) return cuda_fail(s, e, "PSF core launch");
     }
     const int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_img, s->fft_ws.cap / per_img));
     float2* A = (float2*)s->fft_ws.p;
-    float2* B = A + (size_t)chunk * ny * Mx;
     for (int i0 = 0; i0 < n_img; i0 += chunk) {
       const int n = std::min(chunk, n_img - i0);
       e = launch_conv_fft(in + (size_t)i0 * ny * nx, out + (size_t)i0 * ny * nx, n, ny, nx, p.k, My, Mx,
-                          (const float2*)spec->buf.p, A, B, st);
+                          spec->buf.p, A, core > 0 ? 1 : 0, st);
       if (e != cudaSuccess) return cuda_fail(s, e, "FFT convolution launch");
     }
     return LENS_OK;
