@@ -17,6 +17,7 @@ the data path); the timed region is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import math
@@ -302,6 +303,17 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
             dist.barrier()
     step_ms = [e0.elapsed_time(e2) for e0, e1, e2 in ev]
     trace_ms = [e0.elapsed_time(e1) for e0, e1, e2 in ev]
+    # The timed region (K steps of ~2 ms) is shorter than the 200 ms sampling period, so the
+    # clocks are also sampled over an untimed repeat of the same step lasting --clock-soak-s.
+    soak_steps = 0
+    with ClockSampler(local_rank) as clk_soak:
+        t_end = time.perf_counter() + args.clock_soak_s
+        while time.perf_counter() < t_end:
+            for _ in range(25):
+                step(soak_steps)
+                conv()
+                soak_steps += 1
+            torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(step_ms), dev, world)
     value = throughput(args.steps, world, total_ms / 1000.0)
 
@@ -311,6 +323,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     clocks = clk.summary()
+    clocks["soak"] = dict(clk_soak.summary(), steps=soak_steps, seconds=args.clock_soak_s)
     max_mhz = clocks["sm_max_mhz"] or 2070.0
     peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
     census = pair_census(systems[0])
@@ -820,15 +833,21 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
             inputs.append((np.zeros((g.ny, g.nx), np.float32), p))
             outs.append([(np.empty(1, np.float32), np.empty(15, np.float32)) for _ in range(out_sets)])
 
-    def submit(srv, j, c):
-        rq, b, o = pool[j], inputs[j], outs[j][c]
-        if rq.kind == 0:
-            return srv.submit_image(rq.system, o[0])
-        return srv.submit_loglike(rq.system, b[0], 0.01, 1000.0, b[1], o[0], o[1])
-
     srv = lenssim.Server(device=0)
     for rq in pool:
         srv.sim.register_psf(rq.system.psf)
+    # every request is marshalled before the arrivals start, so that the open-loop client does
+    # no more per arrival than one submit call (a Python client that built each request on the
+    # fly fell up to 90 ms behind its schedule and then submitted in bursts)
+    prepared = []
+    for j, rq in enumerate(pool):
+        b = inputs[j]
+        prepared.append([srv.prepare_image(rq.system, outs[j][c][0]) if rq.kind == 0 else
+                         srv.prepare_loglike(rq.system, b[0], 0.01, 1000.0, b[1], outs[j][c][0], outs[j][c][1])
+                         for c in range(out_sets)])
+
+    def submit(srv, j, c):
+        return srv.submit_prepared(prepared[j][c])
     t0 = time.perf_counter()
     warm = [submit(srv, j, 0) for j in range(min(warmup_requests, pool_size))]
     for t in warm:
@@ -844,6 +863,9 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
         pending = {}
         rejected = blocked = 0
         late = 0.0
+        gc.collect()
+        gc.disable()  # no collector pauses inside the arrival schedule
+        time.sleep(0.2)
         t0 = time.perf_counter()
         for i, ta in enumerate(arrivals):
             delay = ta - (time.perf_counter() - t0)
@@ -870,6 +892,7 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
         for t in pending.values():
             codes[srv.wait(t, 600000)] += 1
         t_all = time.perf_counter() - t0
+        gc.enable()
         st = srv.stats()
         rec = {"rate_req_per_s": rate, "seconds": seconds, "offered": int(len(arrivals)),
                "submit_seconds": t_submit, "max_submit_lag_s": late, "rejected_busy": rejected,
@@ -910,6 +933,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--clock-soak-s", type=float, default=1.5,
+                    help="seconds of untimed repeats of the step during which clocks are sampled as well")
     ap.add_argument("--ref-budget-s", type=float, default=90.0,
                     help="reference arm: seconds of oracle work for the whole run, split over its steps")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, gradient and serving lines")

@@ -57,7 +57,7 @@ typedef enum {
 #define LENS_MAX_SHAPELET_NMAX 10    /* SHAPELETS order limit: at most 66 amplitudes */
 #define LENS_MAX_SHAPELET_COEFFS ((LENS_MAX_SHAPELET_NMAX + 1) * (LENS_MAX_SHAPELET_NMAX + 2) / 2)
 #define LENS_MAX_MULTIPOLE_ORDER 32
-#define LENS_MAX_MULTIPOLE_ELL_ORDER 8   /* elliptical multipoles (LENS_MULTIPOLE_ELL) */
+#define LENS_MAX_MULTIPOLE_ELL_ORDER 32  /* elliptical multipoles (LENS_MULTIPOLE_ELL) */
 
 /* Deflector profile types and their parameter layouts p[] (deflection table rows). */
 typedef enum {
@@ -89,8 +89,9 @@ typedef enum {
                          * r_E a_m cos(m (varphi - phi_m)) / (2 R) in the frame of an ellipse of
                          * axis ratio q and angle phi_e, R^2 = q x''^2 + y''^2/q, varphi =
                          * atan2(y''/sqrt(q), x'' sqrt(q)); m an integer in [1, LENS_MAX_MULTIPOLE_ELL_ORDER],
-                         * q in [0.4, 1], r_E > 0, at most one per system.  Evaluated from the
-                         * Fourier series of 2 kappa r (its coefficients computed once per call). */
+                         * q in [0.2, 1], r_E > 0, at most one per system.  Evaluated from the
+                         * Fourier series of 2 kappa r (its up to 321 coefficients computed on the
+                         * host once per call and copied to the device beside the system). */
 } lens_profile_type;
 
 /* Source light profile types (light table rows). I = amp exp(-b_n [(R/R_s)^(1/n) - 1]),
@@ -247,9 +248,11 @@ int lens_sim_linear_amp(lens_sim* sim, const lens_system* sys, const float* data
  * (subhalo constants and the fused trace kernel) and always the direct PSF convolution (where
  * lens_sim_image's automatic choice takes the FFT for k >= LENS_CONV_FFT_MIN_K; both compute
  * the same convolution, within the image tolerance).  It takes no handle and calls no
- * cudaMalloc, cudaFree or allocating library routine.  Its scratch (per-subhalo constants and
- * the unconvolved image) is one fixed array of LENS_NOALLOC_SCRATCH_BYTES of device memory
- * that every GPU loading the library holds until the process exits.
+ * cudaMalloc, cudaFree or allocating library routine.  Its scratch (per-subhalo constants, the
+ * unconvolved image and an elliptical multipole's harmonics) is one fixed array of
+ * LENS_NOALLOC_SCRATCH_BYTES of device memory that every GPU loading the library holds until
+ * the process exits.  A system with an elliptical multipole costs one copy of its harmonics
+ * from pageable host memory, which waits for the stream's earlier work.
  *  - It runs on the CURRENT device.  sys: grid (as for lens_sim_image: 1..16384 pixels per
  *    side, a finite positive pixel scale, a finite centre), HOST deflector list, source;
  *    subhalos in device memory (SoA [5][n]); subhalo_table must be -1; psf_id is ignored.
@@ -268,7 +271,7 @@ int lens_sim_linear_amp(lens_sim* sim, const lens_system* sys, const float* data
  *    threads) race on the array: serialise them on one stream. */
 #define LENS_NOALLOC_MAX_SUBHALOS 20000
 #define LENS_NOALLOC_MAX_PIXELS (512 * 512)
-#define LENS_NOALLOC_SCRATCH_BYTES (LENS_NOALLOC_MAX_SUBHALOS * 176 + LENS_NOALLOC_MAX_PIXELS * 4)
+#define LENS_NOALLOC_SCRATCH_BYTES (LENS_NOALLOC_MAX_SUBHALOS * 176 + LENS_NOALLOC_MAX_PIXELS * 4 + 642 * 4)
 int lens_sim_image_noalloc(const lens_system* sys, const float* psf, int k, float* out_image, void* stream);
 
 /* ---------------------------------------------------------------- serving

@@ -107,13 +107,17 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
 
   // ---- device workspace (metadata block, tables, raw copies, unconvolved images, staging)
+  // systems with an elliptical multipole carry their harmonics in a side region of the block
+  int n_ell = 0;
+  for (int i = 0; i < n; ++i) n_ell += count_deflectors(systems[i], LENS_MULTIPOLE_ELL) > 0;
+  const size_t ell_bytes = align256(sizeof(float) * kEllTableFloats * (size_t)n_ell);
   const size_t meta_bytes = align256(sizeof(BatchMeta)) + align256(sizeof(DevSystem) * n) +
                             align256(sizeof(int) * (n + 1)) + align256(sizeof(PrepJob) * (n + 1)) +
-                            align256(sizeof(ConvJob) * (n + 1));
+                            align256(sizeof(ConvJob) * (n + 1)) + ell_bytes;
   int rc;
-  const size_t meta_cap = align256(sizeof(BatchMeta)) + align256(sizeof(DevSystem) * s->max_batch) +
+  const size_t meta_cap = std::max(meta_bytes, align256(sizeof(BatchMeta)) + align256(sizeof(DevSystem) * s->max_batch) +
                           align256(sizeof(int) * (s->max_batch + 1)) + align256(sizeof(PrepJob) * (s->max_batch + 1)) +
-                          align256(sizeof(ConvJob) * (s->max_batch + 1));
+                          align256(sizeof(ConvJob) * (s->max_batch + 1)));
   if ((rc = ensure(s, s->batch_meta, meta_cap))) return rc;
   if ((rc = ensure(s, s->batch_data, std::max<size_t>(256, tab_total + raw_total + pix_total + stage_total)))) return rc;
   if (!s->pinned || s->pinned_cap < meta_bytes) {
@@ -181,6 +185,7 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
   size_t o_pre = o_sys + align256(sizeof(DevSystem) * n);
   size_t o_prep = o_pre + align256(sizeof(int) * (n + 1));
   size_t o_conv = o_prep + align256(sizeof(PrepJob) * (n + 1));
+  size_t o_ell = o_conv + align256(sizeof(ConvJob) * (n + 1));
   BatchMeta* hm = (BatchMeta*)(hb + o_hdr);
   DevSystem* hsys = (DevSystem*)(hb + o_sys);
   int* hpre = (int*)(hb + o_pre);
@@ -193,6 +198,11 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
     const lens_system& y = systems[i];
     DevSystem& d = hsys[r];
     fill_dev_system(y, d);
+    if (count_deflectors(y, LENS_MULTIPOLE_ELL) > 0) {
+      d.ell_K = ell_table(y, (float*)(hb + o_ell));
+      d.ell_c = (const float*)(db + o_ell);
+      o_ell += sizeof(float) * kEllTableFloats;
+    }
     if (y.subhalo_table >= 0) {
       SubTable t;
       s->res->table(y.subhalo_table, &t);

@@ -33,8 +33,9 @@ struct DevProfile {
 // (kTableStride float4 per subhalo, see tnfw_write_table); `out` receives the binned,
 // unconvolved image.
 // Harmonics kept for the elliptical multipole (enough for 1e-8 of the largest coefficient at
-// m <= 8, q >= 0.4, where the series needs at most 74).
-constexpr int kEllMaxK = 80;
+// m <= 32, q >= 0.2, where the series needs at most 314).
+constexpr int kEllMaxK = 320;
+constexpr int kEllTableFloats = 2 * (kEllMaxK + 1);
 
 struct DevSystem {
   int nx, ny, s, n_defl;
@@ -42,8 +43,9 @@ struct DevSystem {
   int src_type;
   float src[8];
   float src_coef[LENS_MAX_SHAPELET_COEFFS];  // SHAPELETS amplitudes
-  int ell_K;                                 // LENS_MULTIPOLE_ELL: harmonics 0..ell_K of 2 kappa r,
-  float ell_c[2 * (kEllMaxK + 1)];           // (Re, Im) pairs scaled by a_m r_E (0 if none)
+  int ell_K;                                 // LENS_MULTIPOLE_ELL: harmonics 0..ell_K of 2 kappa r
+  const float* ell_c;                        // in device memory, (Re, Im) pairs scaled by a_m r_E
+                                             // (nullptr without the profile)
   DevProfile defl[LENS_MAX_DEFLECTORS];
   int n_sub;
   int pad_;
@@ -714,6 +716,14 @@ __device__ __forceinline__ void alpha_multipole_ell(const float* p, const float*
     const float nr = zr * ct - zi * st, ni = zr * st + zi * ct;
     zr = nr;
     zi = ni;
+    // (ct, st) is a unit vector only to FP32 rounding, and its k-th power drifts in magnitude
+    // by about k/2 of that (1e-5 at the 300th harmonic): every fourth power is scaled back to
+    // unit magnitude, 1/|z| ~ 1.5 - |z|^2 / 2 to second order
+    if ((k & 3) == 0) {
+      const float g = fmaf(-0.5f, fmaf(zr, zr, zi * zi), 1.5f);
+      zr *= g;
+      zi *= g;
+    }
     const float w = 2.f / (1.f - (float)(k * k));
     const float pr = c[2 * k] * zr - c[2 * k + 1] * zi, pim = c[2 * k] * zi + c[2 * k + 1] * zr;
     F = fmaf(w, pr, F);

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -135,8 +136,8 @@ int validate_profile(lens_sim* s, const lens_profile& p) {
       if (!is_integer_in(p.p[0], 1, LENS_MAX_MULTIPOLE_ELL_ORDER))
         return fail(s, LENS_ERR_INVALID_ARG, "elliptical multipole order m=%g not an integer in [1, %d]", p.p[0],
                     LENS_MAX_MULTIPOLE_ELL_ORDER);
-      if (!(p.p[3] >= 0.4f && p.p[3] <= 1.f))
-        return fail(s, LENS_ERR_INVALID_ARG, "elliptical multipole q=%g not in [0.4, 1]", p.p[3]);
+      if (!(p.p[3] >= 0.2f && p.p[3] <= 1.f))
+        return fail(s, LENS_ERR_INVALID_ARG, "elliptical multipole q=%g not in [0.2, 1]", p.p[3]);
       if (!(p.p[7] > 0.f)) return fail(s, LENS_ERR_INVALID_ARG, "elliptical multipole r_E must be > 0");
       return LENS_OK;
     case LENS_NFW_ELLIPSE_CSE:
@@ -266,22 +267,29 @@ int count_deflectors(const lens_system& y, int type) {
 
 // LENS_MULTIPOLE_ELL: the Fourier coefficients c_k of 2 kappa r / (a_m r_E), a function of the
 // polar angle alone, by the trapezoid rule on 1024 points (geometric convergence for this
-// analytic periodic function), kept up to the last harmonic above 1e-8 of the largest (at most
-// kEllMaxK) and stored scaled by a_m r_E as (Re, Im) pairs.
-static void ell_coefficients(const float* p, DevSystem& d) {
+// analytic periodic function; 1024 points resolve the at most 320 harmonics kept without
+// aliasing), kept up to the last harmonic above 1e-8 of the largest (at most kEllMaxK) and stored
+// scaled by a_m r_E as (Re, Im) pairs.  Host FP64; the cosine and sine tables are computed once.
+static int ell_coefficients(const float* p, float* out) {
   constexpr int N = 1024;
   constexpr double kTwoPi = 6.283185307179586476925;
+  static double cs[N], sn[N];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int j = 0; j < N; ++j) {
+      cs[j] = std::cos(kTwoPi * j / N);
+      sn[j] = std::sin(kTwoPi * j / N);
+    }
+  });
   const int m = (int)std::lround(p[0]);
   const double q = p[3], dphi = (double)p[2] - (double)p[4], scale = (double)p[1] * (double)p[7];
   const double sq = std::sqrt(q);
-  double h[N], cs[N], sn[N];  // on the stack: no allocation (the allocation-free entry uses this too)
+  std::vector<double> h(N), re(kEllMaxK + 1), im(kEllMaxK + 1);
   for (int j = 0; j < N; ++j) {
-    cs[j] = std::cos(kTwoPi * j / N);
-    sn[j] = std::sin(kTwoPi * j / N);
     const double g = std::sqrt(q * cs[j] * cs[j] + sn[j] * sn[j] / q);  // R / r
     h[j] = std::cos(m * (std::atan2(sn[j] / sq, sq * cs[j]) - dphi)) / g;
   }
-  double re[kEllMaxK + 1], im[kEllMaxK + 1], amax = 0.0;
+  double amax = 0.0;
   for (int k = 0; k <= kEllMaxK; ++k) {
     double sr = 0.0, si = 0.0;
     for (int j = 0; j < N; ++j) {
@@ -296,11 +304,43 @@ static void ell_coefficients(const float* p, DevSystem& d) {
   int K = 1;
   for (int k = 2; k <= kEllMaxK; ++k)
     if (std::hypot(re[k], im[k]) > 1e-8 * amax) K = k;
-  d.ell_K = K;
-  for (int k = 0; k <= K; ++k) {
-    d.ell_c[2 * k] = (float)(scale * re[k]);
-    d.ell_c[2 * k + 1] = (float)(scale * im[k]);
+  for (int k = 0; k <= kEllMaxK; ++k) {
+    out[2 * k] = k <= K ? (float)(scale * re[k]) : 0.f;
+    out[2 * k + 1] = k <= K ? (float)(scale * im[k]) : 0.f;
   }
+  return K;
+}
+
+int ell_table(const lens_system& y, float* host) {
+  for (int k = 0; k < y.n_deflectors; ++k)
+    if (y.deflectors[k].type == LENS_MULTIPOLE_ELL) return ell_coefficients(y.deflectors[k].p, host);
+  return 0;
+}
+
+int upload_ell_table(lens_sim* s, const lens_system& y, DevSystem& d, cudaStream_t st) {
+  d.ell_K = 0;
+  d.ell_c = nullptr;
+  if (count_deflectors(y, LENS_MULTIPOLE_ELL) == 0) return LENS_OK;
+  int rc = ensure(s, s->ell_dev, sizeof(float) * kEllTableFloats);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (!s->ell_pinned) {
+    e = cudaMallocHost((void**)&s->ell_pinned, sizeof(float) * kEllTableFloats);
+    if (e != cudaSuccess) {
+      s->ell_pinned = nullptr;
+      return fail(s, LENS_ERR_OOM, "pinned staging: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaEventCreateWithFlags(&s->ell_ready, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(s, e, "create event");
+  } else if ((e = cudaEventSynchronize(s->ell_ready)) != cudaSuccess) {  // the last copy has read it
+    return cuda_fail(s, e, "staging event");
+  }
+  d.ell_K = ell_table(y, s->ell_pinned);
+  e = cudaMemcpyAsync(s->ell_dev.p, s->ell_pinned, sizeof(float) * kEllTableFloats, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(s->ell_ready, st);
+  if (e != cudaSuccess) return cuda_fail(s, e, "copy elliptical-multipole table");
+  d.ell_c = (const float*)s->ell_dev.p;
+  return LENS_OK;
 }
 
 void fill_dev_system(const lens_system& y, DevSystem& d) {
@@ -315,7 +355,6 @@ void fill_dev_system(const lens_system& y, DevSystem& d) {
   for (int k = 0; k < y.n_deflectors; ++k) {
     d.defl[k].type = y.deflectors[k].type;
     for (int q = 0; q < LENS_PROFILE_PARAMS; ++q) d.defl[k].p[q] = y.deflectors[k].p[q];
-    if (y.deflectors[k].type == LENS_MULTIPOLE_ELL) ell_coefficients(y.deflectors[k].p, d);
   }
   d.src_type = y.source.type;
   for (int q = 0; q < 8; ++q) d.src[q] = y.source.p[q];
@@ -454,6 +493,9 @@ void lens_sim_destroy(lens_sim* s) {
     release(s, s->raw_sub);
     release(s, s->tab);
     release(s, s->img);
+    release(s, s->ell_dev);
+    if (s->ell_ready) cudaEventDestroy(s->ell_ready);
+    if (s->ell_pinned) cudaFreeHost(s->ell_pinned);
     release(s, s->stage);
     release(s, s->grad_ws);
     release(s, s->fft_ws);
@@ -552,6 +594,7 @@ int lens_sim_image(lens_sim* s, const lens_system* systems, int n_sys, float* co
     const lens_system& y = systems[i];
     DevSystem d;
     fill_dev_system(y, d);
+    if ((rc = upload_ell_table(s, y, d, st))) return rc;
     if ((rc = prepare_subhalos(s, y, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
     const bool dev_out = is_device_ptr(out_images[i]);
     float* final_dst = dev_out ? out_images[i] : (float*)s->stage.p;
@@ -593,6 +636,7 @@ int lens_sim_deflection(lens_sim* s, const lens_system* sys, const float* x, con
   lens_system tmp = *sys;
   tmp.grid = lens_grid{1, 1, 1, 1.f, 0.f, 0.f};
   fill_dev_system(tmp, d);
+  if ((rc = upload_ell_table(s, tmp, d, st))) return rc;
   if ((rc = prepare_subhalos(s, *sys, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
   cudaError_t e = launch_deflection(d, x, y, n, ax, ay, st);
   if (e != cudaSuccess) return cuda_fail(s, e, "deflection kernel launch");
@@ -644,6 +688,7 @@ int lens_sim_autotune(lens_sim* s, const lens_system* sample, int reps, int* bes
   }
   DevSystem d;
   fill_dev_system(*sample, d);
+  if ((rc = upload_ell_table(s, *sample, d, st))) return rc;
   if ((rc = prepare_subhalos(s, *sample, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
   d.out = (float*)s->img.p;
   cudaEvent_t e0, e1;

@@ -5,9 +5,10 @@
 // latency-critical loops that forbid allocation after start-up because cudaMalloc/cudaFree can
 // synchronise the whole device.  This entry point serves them.  It runs the single-system
 // kernels of lens_sim_image (subhalo constants, the fused trace kernel, and the direct PSF
-// convolution for every k) with no handle: its scratch -- the per-subhalo constants and the
-// unconvolved image -- lives in one fixed file-scope device array instead of a handle's
-// workspace.  It calls no cudaMalloc, cudaFree or allocating library routine.
+// convolution for every k) with no handle: its scratch -- the per-subhalo constants, the
+// unconvolved image and an elliptical multipole's harmonics -- lives in one fixed file-scope
+// device array instead of a handle's workspace.  It calls no cudaMalloc, cudaFree or allocating
+// library routine.
 #include "kernels.h"
 #include "lens_sim.h"
 #include "sim_internal.h"
@@ -21,7 +22,8 @@ namespace {
 
 constexpr size_t kTableBytes = (size_t)LENS_NOALLOC_MAX_SUBHALOS * ls::kTableStride * sizeof(float4);
 constexpr size_t kImageBytes = (size_t)LENS_NOALLOC_MAX_PIXELS * sizeof(float);
-static_assert(kTableBytes + kImageBytes == LENS_NOALLOC_SCRATCH_BYTES, "scratch size mismatch");
+constexpr size_t kEllBytes = (size_t)ls::kEllTableFloats * sizeof(float);  // elliptical-multipole harmonics
+static_assert(kTableBytes + kImageBytes + kEllBytes == LENS_NOALLOC_SCRATCH_BYTES, "scratch size mismatch");
 
 // The scratch array: every device that loads the library holds one copy until the process
 // exits.  Host code must not pass `g_scratch` itself to a kernel (on the host it names a
@@ -77,9 +79,21 @@ extern "C" int lens_sim_image_noalloc(const lens_system* sys, const float* psf, 
   cudaStream_t st = (cudaStream_t)stream;
 
   // Every byte read below is written first by this call: the table by the constants kernel,
-  // the unconvolved image by the trace kernel.  Nothing needs clearing.
+  // the unconvolved image by the trace kernel, the harmonics by the copy.  Nothing needs clearing.
   DevSystem d;
   fill_dev_system(y, d);
+  if (count_deflectors(y, LENS_MULTIPOLE_ELL) > 0) {
+    // the harmonics go to the scratch from pageable host memory: the copy waits for the
+    // stream's earlier work, and the host buffer is free again when the call returns
+    float host_ell[kEllTableFloats];
+    d.ell_K = ell_table(y, host_ell);
+    float* ell = (float*)((char*)base + kTableBytes + kImageBytes);
+    if (cudaMemcpyAsync(ell, host_ell, kEllBytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cudaGetLastError();
+      return LENS_ERR_CUDA;
+    }
+    d.ell_c = ell;
+  }
   d.sub = table;
   d.n_sub = y.n_subhalos;
   d.out = with_psf ? raw : out_image;

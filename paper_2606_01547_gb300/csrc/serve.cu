@@ -238,8 +238,10 @@ void CUDART_CB slot_done_cb(void* arg) {
   cb->srv->cv_work.notify_all();
 }
 
-// Completion of a slot (worker thread, lock held): results to the caller, latency, budget.
-void finish(lens_server* srv, Slot* sl) {
+// Completion of a slot (worker thread, lock held on entry and exit): results to the caller,
+// latency, budget.  The copies to the callers' buffers run with the lock released, so that
+// submits and waits are not held up by them (only the worker touches a running batch).
+void finish(lens_server* srv, Slot* sl, std::unique_lock<std::mutex>& lk) {
   // The host callback ran after every earlier operation of the stream completed; while the
   // callback itself retires the stream may still report "not ready", which is no error.
   cudaError_t e = cudaStreamQuery(sl->stream);
@@ -247,8 +249,8 @@ void finish(lens_server* srv, Slot* sl) {
     cudaGetLastError();  // "not ready" must not linger as this thread's last error
     e = cudaSuccess;
   }
-  const auto now = Clock::now();
   if (e != cudaSuccess) note_error(srv, cudaGetErrorString(e));
+  lk.unlock();
   for (Req* q : sl->batch) {
     if (q->status == LENS_OK && e != cudaSuccess) q->status = LENS_ERR_CUDA;
     if (q->status == LENS_OK) {
@@ -259,6 +261,10 @@ void finish(lens_server* srv, Slot* sl) {
         if (q->r.out_grad) std::memcpy(q->r.out_grad, sl->h_out + q->out_off + 1, LENS_N_FREE_PARAMS * sizeof(float));
       }
     }
+  }
+  lk.lock();
+  const auto now = Clock::now();
+  for (Req* q : sl->batch) {
     q->state = q->status == LENS_OK ? kDone : kFailed;
     q->t_done = now;
     srv->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - q->t_submit).count());
@@ -279,7 +285,7 @@ void worker_main(lens_server* srv) {
   std::unique_lock<std::mutex> lk(srv->mu);
   while (!srv->stop.load()) {
     for (Slot* sl : srv->slots)
-      if (sl->busy && sl->complete) finish(srv, sl);
+      if (sl->busy && sl->complete) finish(srv, sl, lk);
     bool issued = false;
     if (!srv->paused) {
       for (size_t si = 0; si < srv->slots.size() && !srv->queue.empty(); ++si) {
@@ -313,7 +319,7 @@ void worker_main(lens_server* srv) {
       cudaStreamSynchronize(sl->stream);
       lk.lock();
       if (!sl->complete) sl->complete = true;
-      finish(srv, sl);
+      finish(srv, sl, lk);
     }
 }
 

@@ -59,6 +59,12 @@ int sub_count(lens_sim* s, const lens_system& y);
 int prepare_subhalos(lens_sim* s, const lens_system& y, float4* tab_buf, float* raw_buf, const float4** out_tab,
                      int* out_n, cudaStream_t st);
 void fill_dev_system(const lens_system& y, DevSystem& d);
+// The elliptical-multipole harmonics of a system into `host` (kEllTableFloats floats); returns
+// the highest harmonic K (0 if the system has no LENS_MULTIPOLE_ELL).
+int ell_table(const lens_system& y, float* host);
+// For the single-system launches of a handle: the table copied to the handle's device buffer
+// (from its pinned staging, on the stream) and d.ell_c / d.ell_K set; no-op without the profile.
+int upload_ell_table(lens_sim* s, const lens_system& y, DevSystem& d, cudaStream_t st);
 // Deflectors of the given type in a system.
 int count_deflectors(const lens_system& y, int type);
 int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const* outs, cudaStream_t st);
@@ -125,6 +131,9 @@ struct lens_sim {
   ls::DevBuffer raw_sub;  // device copy of a host subhalo SoA
   ls::DevBuffer tab;      // per-call subhalo constants
   ls::DevBuffer img;      // unconvolved (binned) image
+  ls::DevBuffer ell_dev;  // elliptical-multipole harmonics of the current single-system call
+  float* ell_pinned = nullptr;        // their host staging
+  cudaEvent_t ell_ready = nullptr;    // recorded after the staging's last copy
   ls::DevBuffer stage;    // device staging of host outputs
   ls::DevBuffer grad_ws;  // likelihood / adjoint workspace
   ls::DevBuffer fft_ws;   // FFT convolution workspace (row and column spectra of a chunk of images)

@@ -492,15 +492,24 @@ class Server:
             pass
 
     def submit_image(self, system: W.LensSystem, out: np.ndarray) -> int:
+        return self.submit_prepared(self.prepare_image(system, out))
+
+    def submit_loglike(self, system: W.LensSystem, data: np.ndarray, sigma_bkg: float, t_exp: float,
+                       params: np.ndarray, out: np.ndarray, out_grad: Optional[np.ndarray]) -> int:
+        return self.submit_prepared(self.prepare_loglike(system, data, sigma_bkg, t_exp, params, out, out_grad))
+
+    def prepare_image(self, system: W.LensSystem, out: np.ndarray):
+        """The marshalled request (struct and the objects it points into), for submit_prepared."""
         keep: list = [out]
         req = LensRequest()
         req.kind = 0
         req.sys = self.sim.system_struct(system, keep)
         req.out = out.ctypes.data
-        return self._submit(req, keep)
+        keep.append(req)
+        return req, keep
 
-    def submit_loglike(self, system: W.LensSystem, data: np.ndarray, sigma_bkg: float, t_exp: float,
-                       params: np.ndarray, out: np.ndarray, out_grad: Optional[np.ndarray]) -> int:
+    def prepare_loglike(self, system: W.LensSystem, data: np.ndarray, sigma_bkg: float, t_exp: float,
+                        params: np.ndarray, out: np.ndarray, out_grad: Optional[np.ndarray]):
         data = np.ascontiguousarray(data, np.float32)
         params = np.ascontiguousarray(params, np.float32)
         keep: list = [data, params, out, out_grad]
@@ -513,14 +522,17 @@ class Server:
         req.params = params.ctypes.data
         req.out = out.ctypes.data
         req.out_grad = None if out_grad is None else out_grad.ctypes.data
-        return self._submit(req, keep)
+        keep.append(req)
+        return req, keep
 
-    def _submit(self, req, keep) -> int:
+    def submit_prepared(self, prepared) -> int:
+        """Submit a request from prepare_image / prepare_loglike; the buffers it references must
+        stay alive (the server keeps them referenced until wait/poll reports the result)."""
+        req, keep = prepared
         t = ctypes.c_ulonglong()
         rc = self._L.lens_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t))
         if rc != 0:
             raise LensSimError(rc, "lens_serve_submit")
-        keep.append(req)
         self._keep[t.value] = keep
         return t.value
 

@@ -1,5 +1,7 @@
 """Fitting clients of the batched likelihood: L-BFGS reaches the optimum that SciPy's L-BFGS-B
-finds on the FP64 oracle from the same start; the particle swarm improves monotonically."""
+finds on the FP64 oracle from the same start; the particle swarm, started in a box around a
+guess as lens-model fits start it, reaches that optimum's region, and L-BFGS from its best point
+reaches the optimum itself."""
 import numpy as np
 import pytest
 
@@ -50,16 +52,37 @@ def test_lbfgs_reaches_the_oracle_optimum(sim):
     assert res.logL[0] >= oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, start[None], grad=False)[0]
 
 
-def test_particle_swarm_improves_monotonically(sim):
+def _oracle_optimum(pb, data, start):
+    def f(p):
+        L, G = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, p[None])
+        return -L[0], -G[0]
+
+    ref = scipy_opt.minimize(f, np.asarray(start, np.float64), jac=True, method="L-BFGS-B",
+                             options={"maxiter": 2000, "ftol": 1e-15, "gtol": 1e-10})
+    return ref
+
+
+def test_particle_swarm_reaches_the_oracle_optimum_region(sim):
     from paper_2606_01547_gb300 import fitting
     pb, data = _problem()
-    res = fitting.pso_fit(sim, pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp, n_particles=128,
-                          iters=40, seed=5)
-    h = np.array(res.history)
-    assert np.all(np.diff(h) >= 0)
-    assert h[-1] > h[0]
-    assert res.evaluations == 128 * 41
+    ref = _oracle_optimum(pb, data, pb.truth)
+    L_opt = -ref.fun
+    # the swarm searches a box of +-5 % of the prior widths around the truth (a guess), 256
+    # particles for 200 iterations; measured gaps to the optimum over seeds 5..10: 1.7 .. 6.9 in
+    # logL (-283 at the optimum, 576 pixels)
+    width = fitting.PRIOR_HI - fitting.PRIOR_LO
+    lo = np.maximum(fitting.PRIOR_LO, pb.truth - 0.05 * width)
+    hi = np.minimum(fitting.PRIOR_HI, pb.truth + 0.05 * width)
+    dd = torch.from_numpy(data).cuda()
+    res = fitting.pso_fit(sim, pb.system, dd, pb.sigma_bkg, pb.t_exp, n_particles=256, iters=200, seed=7,
+                          lo=lo, hi=hi)
+    assert res.evaluations == 256 * 201
+    L_pso = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, res.params.astype(np.float64), grad=False)[0]
+    assert L_pso >= L_opt - 0.03 * abs(L_opt), (L_pso, L_opt)
     # the reported best is the likelihood of the reported parameters
-    L = sim.grad(pb.system, torch.from_numpy(data).cuda(), pb.sigma_bkg, pb.t_exp,
-                 torch.from_numpy(res.params).cuda(), want_grad=False)
+    L = sim.grad(pb.system, dd, pb.sigma_bkg, pb.t_exp, torch.from_numpy(res.params).cuda(), want_grad=False)
     assert abs(L.item() - res.logL[0]) <= 1e-6 * abs(res.logL[0])
+    # L-BFGS from the swarm's best point reaches the optimum within the FP32 objective's noise
+    pol = fitting.lbfgs_fit(sim, pb.system, dd, pb.sigma_bkg, pb.t_exp, res.params, iters=100, restarts=20)
+    L_pol = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pol.params.astype(np.float64), grad=False)[0]
+    assert abs(L_pol - L_opt) <= 5e-5 * abs(L_opt), (L_pol, L_opt)

@@ -162,8 +162,9 @@ def test_elliptical_multipole_image_matches_oracle(sim):
     (_, epl), shear = base.deflectors
     th, g, q, phi = epl[:4]
     e = [("EPL", epl), ("MULTIPOLE_ELL", [4, 0.02, phi + 0.1, q, phi, 0.0, 0.0, th]),
-         ("MULTIPOLE_ELL", [3, 0.01, 0.7, q, phi, 0.0, 0.0, th])]
-    for defl in ([e[0], e[1], shear], [e[0], e[2], shear]):
+         ("MULTIPOLE_ELL", [3, 0.01, 0.7, q, phi, 0.0, 0.0, th]),
+         ("MULTIPOLE_ELL", [32, 0.004, 0.3, 0.2, phi, 0.0, 0.0, th])]
+    for defl in ([e[0], e[1], shear], [e[0], e[2], shear], [e[0], e[3], shear]):
         system = W.LensSystem(W.Grid(40, 40, 2, W.f32(0.06)), [(n, [W.f32(v) for v in p]) for n, p in defl],
                               base.subhalos, base.source, base.psf)
         ref = oracle.image(system)
@@ -176,8 +177,9 @@ def test_elliptical_multipole_limits_are_refused(sim):
     from paper_2606_01547_gb300 import lenssim
     base = W.plain_system()
     ok = ("MULTIPOLE_ELL", [4, 0.02, 0.1, 0.7, 0.3, 0.0, 0.0, 1.0])
-    bad = [[("MULTIPOLE_ELL", [9, 0.02, 0.1, 0.7, 0.3, 0.0, 0.0, 1.0])],
-           [("MULTIPOLE_ELL", [4, 0.02, 0.1, 0.3, 0.3, 0.0, 0.0, 1.0])],
+    bad = [[("MULTIPOLE_ELL", [33, 0.02, 0.1, 0.7, 0.3, 0.0, 0.0, 1.0])],
+           [("MULTIPOLE_ELL", [4, 0.02, 0.1, 0.15, 0.3, 0.0, 0.0, 1.0])],
+           [("MULTIPOLE_ELL", [4.5, 0.02, 0.1, 0.7, 0.3, 0.0, 0.0, 1.0])],
            [("MULTIPOLE_ELL", [4, 0.02, 0.1, 0.7, 0.3, 0.0, 0.0, 0.0])],
            [ok, ok]]
     for d in bad:
@@ -284,7 +286,11 @@ PROFILES = [("SIS", [1.1, 0.05, -0.02]), ("SIE", [1.0, 0.8, 0.3, 0.0, 0.0]),
             ("MULTIPOLE_ELL", [2, 0.05, 0.3, 1.0, 0.0, 0.0, 0.0, 1.0]),
             ("MULTIPOLE_ELL", [3, 0.03, 1.1, 0.8, 0.5, 0.05, 0.02, 1.3]),
             ("MULTIPOLE_ELL", [4, 0.02, 0.2, 0.45, 1.0, 0.0, 0.0, 0.9]),
-            ("MULTIPOLE_ELL", [8, 0.01, 2.0, 0.4, 0.3, 0.1, 0.1, 1.1])]
+            ("MULTIPOLE_ELL", [8, 0.01, 2.0, 0.4, 0.3, 0.1, 0.1, 1.1]),
+            ("MULTIPOLE_ELL", [13, 0.01, 0.9, 0.55, 0.1, 0.0, 0.0, 1.0]),
+            ("MULTIPOLE_ELL", [16, 0.01, 0.5, 0.25, 0.2, 0.0, 0.0, 1.0]),
+            ("MULTIPOLE_ELL", [24, 0.01, 0.2, 0.3, 0.7, -0.05, 0.0, 0.9]),
+            ("MULTIPOLE_ELL", [32, 0.005, 1.3, 0.2, -0.4, 0.02, -0.01, 1.1])]
 
 
 @pytest.mark.parametrize("name,params", PROFILES)
@@ -545,6 +551,11 @@ def test_every_batch_schedule_gives_the_same_images_and_autotune_picks_one(sim):
     systems = W.batched_systems(77, count=9, max_sub=1500, grids=(24, 37, 64))
     systems.append(W.LensSystem(W.Grid(30, 22, 2, 0.04), systems[0].deflectors, np.zeros((5, 0), np.float32),
                                 systems[0].source, None))
+    # two systems with elliptical multipoles, whose harmonics travel beside the descriptors
+    for m, q in ((4, 0.6), (32, 0.2)):
+        y = systems[m % 5]
+        systems.append(W.LensSystem(y.grid, y.deflectors + [("MULTIPOLE_ELL", [m, 0.01, 0.4, q, 0.2, 0.0, 0.0, 1.0])],
+                                    y.subhalos, y.source, y.psf))
     single = [gpu_image(sim, y) for y in systems]
     for form in range(len(lenssim.BATCH_FORMS)):
         for order in range(2):

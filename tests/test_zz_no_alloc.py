@@ -67,6 +67,11 @@ def test_noalloc_matches_lens_sim_image_on_two_calls_in_a_row(env):
     out_c = torch.empty((20, 20), device="cuda")
     assert _noalloc(L, sim, c, out_c) == lenssim.LENS_OK
     np.testing.assert_allclose(out_c.cpu().numpy(), sim.image(c)[0].cpu().numpy(), rtol=0, atol=0)
+    # an elliptical multipole: its harmonics travel through the fixed scratch as well
+    e = W.LensSystem(c.grid, c.deflectors + [("MULTIPOLE_ELL", [32, 0.01, 0.3, 0.2, 0.1, 0.0, 0.0, 1.0])],
+                     c.subhalos, c.source, None)
+    assert _noalloc(L, sim, e, out_c) == lenssim.LENS_OK
+    np.testing.assert_array_equal(out_c.cpu().numpy(), sim.image(e)[0].cpu().numpy())
     too_many = W.substructure_system(8, n_sub=20001, nx=8, s=1, k=3)
     assert _noalloc(L, sim, too_many, torch.empty((8, 8), device="cuda")) == lenssim.LENS_ERR_OOM
     too_big = W.LensSystem(W.Grid(600, 600, 1, 0.04), c.deflectors, c.subhalos, c.source, None)
