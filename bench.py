@@ -611,6 +611,16 @@ def per_config_extra(sim, lenssim, W, dev, cpu_budget_s: float = 10.0):
     oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pb.points[:n_cpu].astype(np.float64))
     t_grad = time.perf_counter() - t0
     _, Gf = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts, fp32=True)
+    # conditioning floor per component: the rounding mode's change, or the first-order change
+    # of the exact gradient under a one-ulp perturbation of each parameter, whichever is larger
+    lin = np.zeros_like(Gr)
+    for j in range(15):
+        d = np.zeros_like(pts)
+        d[:, j] = np.abs(pts[:, j]) * 2.0 ** -23
+        _, Gp = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts + d)
+        _, Gm = oracle.loglike(pb.system, data, pb.sigma_bkg, pb.t_exp, pts - d)
+        lin += 0.5 * np.abs(Gp - Gm)
+    floor = np.maximum(np.abs(Gf - Gr), lin)
     gmax = np.abs(Gr).max(axis=1, keepdims=True)
     scale = np.maximum(np.abs(Gr), 1e-3 * gmax)
     out["differentiation"] = {
@@ -618,7 +628,9 @@ def per_config_extra(sim, lenssim, W, dev, cpu_budget_s: float = 10.0):
         "logL_rel_err_max": float(np.max(np.abs(Lg - Lr) / np.abs(Lr))),
         "grad_normwise_err_max": float(np.max(np.abs(Gg - Gr).max(axis=1) / gmax[:, 0])),
         "grad_componentwise_err_max": float(np.max(np.abs(Gg - Gr) / scale)),
-        "grad_floor_componentwise_max": float(np.max(np.abs(Gf - Gr) / scale)),
+        "grad_rounding_floor_componentwise_max": float(np.max(np.abs(Gf - Gr) / scale)),
+        "grad_conditioning_floor_componentwise_max": float(np.max(floor / scale)),
+        "grad_err_over_bound_max": float(np.max((np.abs(Gg - Gr) / scale) / np.maximum(1e-4, 2.0 * floor / scale))),
         "cpu_oracle": {"gradients_per_s": n_cpu / t_grad, "cores": cores,
                        "sample": f"{n_cpu} of the 512 points, forward-mode dual numbers (15 tangents), "
                                  f"including the 10^7-pair subhalo field"}}
