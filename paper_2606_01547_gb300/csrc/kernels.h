@@ -9,7 +9,6 @@ namespace ls {
 
 constexpr int kUnitPts = 9;      // samples per lane in a trace unit (a unit is 32 x 9 samples)
 constexpr int kPackedPairs = 4;  // of a lane's samples, this many pairs run as FP32x2 instructions
-constexpr int kFuseSubhalos = 2;  // far-field subhalos evaluated per basic block (1, 2 or 4)
 constexpr int kTraceWarps = 8;   // warps per trace CTA, splitting the subhalo list
 
 // One system's subhalo constants for the batched preparation kernel.

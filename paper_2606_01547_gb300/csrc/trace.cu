@@ -53,15 +53,26 @@ int unit_count(int nx, int ny, int s) {
   return ((nx + bw - 1) / bw) * ((ny + bh - 1) / bh);
 }
 
+// A warp stages 32 subhalos at a time, record q in lane q's slot, and lists them by class -- 6-,
+// 4-, 3-term far-field series, then the marked near-field subhalos -- in subhalo order within
+// the class, so each class is a counted loop over consecutive list entries (whose loads the
+// compiler can issue ahead) rather than a scan of a ballot mask.  The first two classes start
+// on even list positions (one pad each at most), so a pair of entries loads as one int2.
+constexpr int kStageList = 34;
+constexpr int kFarRec = 4;                 // t0, t2, t3, t4: centre and series coefficients
+constexpr int kNearRec = 2 + kMidStride;   // t1, t6 and the annulus block
+static_assert(kUnitPts == 2 * kPackedPairs + 1, "a lane runs kPackedPairs sample pairs and one odd sample");
+
 template <int NW>
 struct TraceSmem {
-  // Per warp: the 32 staged subhalo records (and the annulus blocks of those the bounding-box
-  // test marked), reused for the warp's partials once its subhalo loop has ended (so a warp
-  // never overwrites what another warp is still reading).
+  // Per warp: the staged records of one stage, reused for the warp's partials once its subhalo
+  // loop has ended (so a warp never overwrites what another warp is still reading).
   union WarpArea {
     struct {
-      float4 sub[32][kSubStride];
-      float4 mid[32][kMidStride];
+      float4 sub[32][kFarRec];
+      float4 marked[32][kNearRec];
+      int list[kStageList];
+      float4 box;  // the unit's bounding box (kept here rather than in registers)
     };
     float2 part[kUnitPts][32];
   } wa[NW];
@@ -96,16 +107,13 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
 // kTraceWarps-way split of the subhalo list and writes its 288 partials to wa[area0 + w].part.
 //
 // A lane's first 2 kPackedPairs samples run as packed pairs (FP32x2 instructions, two samples
-// per issue slot), the rest as scalars; the two kinds run on different FP32 pipes.  The packed
-// operations are element-wise the same IEEE operations as the scalar ones, so every sample's
-// deflection is the same whichever kind it is.
+// per issue slot), the odd one as scalars; the two kinds run on different FP32 pipes.  The
+// packed operations are element-wise the same IEEE operations as the scalar ones, so every
+// sample's deflection is the same whichever kind it is.
 template <int NWC>
 __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGeom& g, int slice0,
                                               TraceSmem<NWC>& sm, int area0 = 0) {
   constexpr int kP = kPackedPairs;
-  constexpr int kS = kUnitPts - 2 * kP;
-  static_assert(kS >= 0, "more packed samples than samples");
-  constexpr int kPa = kP > 0 ? kP : 1, kSa = kS > 0 ? kS : 1;
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const int n = sys.n_sub;
@@ -116,8 +124,8 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   const float4* __restrict__ mid_tab = sys.sub + (size_t)kSubStride * n;
   auto& area = sm.wa[area0 + w];
 
-  float2 px2[kPa], py2[kPa], ax2[kPa], ay2[kPa];
-  float pxs[kSa], pys[kSa], axs[kSa], ays[kSa];
+  float2 px2[kP], py2[kP], ax2[kP], ay2[kP];
+  float po_x, po_y, ao_x = 0.f, ao_y = 0.f;  // the odd sample and its sums
   float xmin = 3.0e38f, xmax = -3.0e38f, ymin = 3.0e38f, ymax = -3.0e38f;
 #pragma unroll
   for (int k = 0; k < kUnitPts; ++k) {
@@ -127,9 +135,9 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     sample_xy(sys, g, q, x, y);
     xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
     ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
-    if (k >= 2 * kP) {
-      pxs[k - 2 * kP] = x;
-      pys[k - 2 * kP] = y;
+    if (k == 2 * kP) {
+      po_x = x;
+      po_y = y;
     } else if (k & 1) {
       px2[k >> 1].y = x;
       py2[k >> 1].y = y;
@@ -139,14 +147,9 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     }
   }
 #pragma unroll
-  for (int i = 0; i < kPa; ++i) {
+  for (int i = 0; i < kP; ++i) {
     ax2[i] = make_float2(0.f, 0.f);
     ay2[i] = make_float2(0.f, 0.f);
-  }
-#pragma unroll
-  for (int i = 0; i < kSa; ++i) {
-    axs[i] = 0.f;
-    ays[i] = 0.f;
   }
   // bounding box of the unit's samples (uniform across the warp)
 #pragma unroll
@@ -156,133 +159,151 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     ymin = fminf(ymin, __shfl_xor_sync(0xffffffffu, ymin, off));
     ymax = fmaxf(ymax, __shfl_xor_sync(0xffffffffu, ymax, off));
   }
-  // 32 subhalos per shared-memory stage.  While staging, each lane tests its subhalo against
-  // the unit's bounding box: subhalos some sample might see inside the far-field radius are
-  // marked (near); the others take the shortest far-field series whose range holds the whole
-  // box (6 terms from 7, 4 from 20, 3 from 40 max(tau, 1) Rs).  Marked subhalos let every
-  // sample pick its own form (the 6-term series again beyond the radius).  The stage is summed
-  // class by class (6-, 4-, 3-term, then marked), each in subhalo order: an order fixed by the
-  // unit, so every launch form gives the same sums.
+  if (lane == 0) area.box = make_float4(xmin, xmax, ymin, ymax);
+  __syncwarp();
+  // far-field series truncated after d_K for the record t of one subhalo: a packed sample pair
+  auto packed_pair = [&](const float4* t, auto Kc, float2 px, float2 py, float2& ax, float2& ay) {
+    constexpr int K = decltype(Kc)::value;
+    const float2 dx = __fadd2_rn(px, make_float2(t[0].x, t[0].y));
+    const float2 dy = __fadd2_rn(py, make_float2(t[0].z, t[0].w));
+    const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+    const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+    const float2 gg = tnfw_series2_k<K>(u, __fmul2_rn(u, u), t);
+    ax = __ffma2_rn(gg, dx, ax);
+    ay = __ffma2_rn(gg, dy, ay);
+  };
+  auto far_samples = [&](const float4* t, auto Kc) {
+#pragma unroll
+    for (int i = 0; i < kP; ++i) packed_pair(t, Kc, px2[i], py2[i], ax2[i], ay2[i]);
+  };
+  auto far_odd = [&](const float4* t, auto Kc) {  // the odd sample
+    constexpr int K = decltype(Kc)::value;
+    const float dx = po_x + t[0].x, dy = po_y + t[0].z;
+    const float u = rsqrt_ftz(fmaf(dx, dx, dy * dy));
+    const float gg = tnfw_series_k<K>(u, u * u, t);
+    ao_x = fmaf(gg, dx, ao_x);
+    ao_y = fmaf(gg, dy, ao_y);
+  };
+  auto load_far = [&](int q, float4* t) {
+    t[0] = area.sub[q][0];
+#pragma unroll
+    for (int c = 1; c < kFarRec; ++c) t[1 + c] = area.sub[q][c];
+  };
+  // a class of far subhalos at list positions [b, e), b even: two per basic block, so the
+  // scheduler overlaps one's reciprocal square roots and loads with the other's polynomial
+  auto far_class = [&](int b, int e, auto Kc) {
+    int q = b;
+#pragma unroll 1
+    for (; q + 1 < e; q += 2) {
+      float4 ta[5], tb[5];
+      const int2 qq = *reinterpret_cast<const int2*>(&area.list[q]);
+      load_far(qq.x, ta);
+      load_far(qq.y, tb);
+      far_samples(ta, Kc);
+      far_odd(ta, Kc);
+      far_samples(tb, Kc);
+      far_odd(tb, Kc);
+    }
+    if (q < e) {
+      float4 ta[5];
+      load_far(area.list[q], ta);
+      far_samples(ta, Kc);
+      far_odd(ta, Kc);
+    }
+  };
+  // subhalos the bounding-box test marked: series and annulus polynomial for every sample
+  // (packed, branch-free), each sample then keeps the form of its distance; only samples
+  // inside r_in call the closed forms
+  auto near_pairs = [&](const float4* t, const float4* m) {
+    const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
+    const float r_far2 = t[1].x, r_in2 = t[6].z;
+    auto pick = [&](float r2, float gs, float gm) {
+      if (r2 >= r_far2) return gs;
+      if (r2 >= r_in2) return gm;
+      return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[6].w);
+    };
+#pragma unroll
+    for (int i = 0; i < kP; ++i) {
+      const float2 dx = __fadd2_rn(px2[i], ncx), dy = __fadd2_rn(py2[i], ncy);
+      const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+      const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+      const float2 u2 = __fmul2_rn(u, u);
+      const float2 gs = tnfw_series2_u(u, u2, t);
+      const float2 gm = tnfw_mid2_u(u, u2, t, m);
+      const float2 gg = make_float2(pick(r2.x, gs.x, gm.x), pick(r2.y, gs.y, gm.y));
+      ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
+      ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
+    }
+    const float dx = po_x + t[0].x, dy = po_y + t[0].z;
+    const float r2 = fmaf(dx, dx, dy * dy);
+    const float u = rsqrt_ftz(r2), u2 = u * u;
+    const float gg = pick(r2, tnfw_series_u(u, u2, t), tnfw_mid_u(u, u2, t, m));
+    ao_x = fmaf(gg, dx, ao_x);
+    ao_y = fmaf(gg, dy, ao_y);
+  };
+  // While staging, each lane tests its subhalo against the unit's bounding box: subhalos some
+  // sample might see inside the far-field radius are marked (near); the others take the
+  // shortest far-field series whose range holds the whole box (6 terms from 7, 4 from 20, 3 from
+  // 40 max(tau, 1) Rs).  Marked subhalos let every sample pick its own form (the 6-term series
+  // again beyond the radius).  The stage is summed class by class (6-, 4-, 3-term, then marked),
+  // each in subhalo order: an order fixed by the unit, so every launch form gives the same sums.
   for (int base = lo; base < hi; base += 32) {
     const int idx = base + lane;
+    const bool alive = idx < hi;
     bool near = false;
     int tier = 0;  // 0: 6-term series, 1: 4-term, 2: 3-term
-    if (idx < hi) {
+    if (alive) {
       float4 st[kSubStride];
 #pragma unroll
-      for (int c = 0; c < kSubStride; ++c) {
-        st[c] = __ldg(tab + (size_t)kSubStride * idx + c);
-        area.sub[lane][c] = st[c];
-      }
+      for (int c = 0; c < kSubStride; ++c) st[c] = __ldg(tab + (size_t)kSubStride * idx + c);
+      area.sub[lane][0] = st[0];
+#pragma unroll
+      for (int c = 1; c < kFarRec; ++c) area.sub[lane][c] = st[1 + c];
       // st[0] holds the negated centre
+      const float4 bx = area.box;
+      const float xmin = bx.x, xmax = bx.y, ymin = bx.z, ymax = bx.w;
       const float ddx = fmaxf(fmaxf(xmin + st[0].x, -st[0].x - xmax), 0.f);
       const float ddy = fmaxf(fmaxf(ymin + st[0].z, -st[0].z - ymax), 0.f);
       const float d2 = fmaf(ddx, ddx, ddy * ddy);
       near = d2 < st[1].x;
       tier = d2 >= st[5].y ? 2 : (d2 >= st[5].x ? 1 : 0);
       if (near) {
+        area.marked[lane][0] = st[1];
+        area.marked[lane][1] = st[6];
 #pragma unroll
-        for (int c = 0; c < kMidStride; ++c) area.mid[lane][c] = __ldg(mid_tab + (size_t)kMidStride * idx + c);
+        for (int c = 0; c < kMidStride; ++c) area.marked[lane][2 + c] = __ldg(mid_tab + (size_t)kMidStride * idx + c);
       }
     }
-    const int cnt = min(32, hi - base);
-    const unsigned live = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
-    const unsigned near_mask = __ballot_sync(0xffffffffu, near);
-    const unsigned m3 = __ballot_sync(0xffffffffu, !near && tier == 2) & live;
-    const unsigned m4 = __ballot_sync(0xffffffffu, !near && tier == 1) & live;
-    const unsigned m6 = live & ~(near_mask | m3 | m4);
+    const unsigned mn = __ballot_sync(0xffffffffu, alive && near);
+    const unsigned m3 = __ballot_sync(0xffffffffu, alive && !near && tier == 2);
+    const unsigned m4 = __ballot_sync(0xffffffffu, alive && !near && tier == 1);
+    const unsigned m6 = __ballot_sync(0xffffffffu, alive && !near && tier == 0);
+    const int n6 = __popc(m6), n4 = __popc(m4), n3 = __popc(m3), nn = __popc(mn);
+    const int b4 = (n6 + 1) & ~1, b3 = b4 + ((n4 + 1) & ~1), bn = b3 + n3;
+    if (alive) {
+      const unsigned below = (1u << lane) - 1u;
+      const int pos = near ? bn + __popc(mn & below)
+                           : (tier == 2 ? b3 + __popc(m3 & below)
+                                        : (tier == 1 ? b4 + __popc(m4 & below) : __popc(m6 & below)));
+      area.list[pos] = lane;
+    }
     __syncwarp();
-    // far-field series truncated after d_K for subhalo record t, all samples of the lane
-    auto far_pairs = [&](const float4* t, auto Kc) {
-      constexpr int K = decltype(Kc)::value;
-      const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
-#pragma unroll
-      for (int i = 0; i < kP; ++i) {
-        const float2 dx = __fadd2_rn(px2[i], ncx), dy = __fadd2_rn(py2[i], ncy);
-        const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-        const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-        const float2 gg = tnfw_series2_k<K>(u, __fmul2_rn(u, u), t);
-        ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
-        ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < kS; ++i) {
-        const float dx = pxs[i] + t[0].x, dy = pys[i] + t[0].z;
-        const float u = rsqrt_ftz(fmaf(dx, dx, dy * dy));
-        const float gg = tnfw_series_k<K>(u, u * u, t);
-        axs[i] = fmaf(gg, dx, axs[i]);
-        ays[i] = fmaf(gg, dy, ays[i]);
-      }
-    };
-    // subhalos the bounding-box test marked: series and annulus polynomial for every sample
-    // (packed, branch-free), each sample then keeps the form of its distance; only samples
-    // inside r_in call the closed forms
-    auto near_pairs = [&](const float4* t, const float4* m) {
-      const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
-      const float r_far2 = t[1].x, r_in2 = t[6].z;
-      auto pick = [&](float r2, float gs, float gm) {
-        if (r2 >= r_far2) return gs;
-        if (r2 >= r_in2) return gm;
-        return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[6].w);
-      };
-#pragma unroll
-      for (int i = 0; i < kP; ++i) {
-        const float2 dx = __fadd2_rn(px2[i], ncx), dy = __fadd2_rn(py2[i], ncy);
-        const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-        const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-        const float2 u2 = __fmul2_rn(u, u);
-        const float2 gs = tnfw_series2_u(u, u2, t);
-        const float2 gm = tnfw_mid2_u(u, u2, t, m);
-        const float2 gg = make_float2(pick(r2.x, gs.x, gm.x), pick(r2.y, gs.y, gm.y));
-        ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
-        ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < kS; ++i) {
-        const float dx = pxs[i] + t[0].x, dy = pys[i] + t[0].z;
-        const float r2 = fmaf(dx, dx, dy * dy);
-        const float u = rsqrt_ftz(r2), u2 = u * u;
-        const float gg = pick(r2, tnfw_series_u(u, u2, t), tnfw_mid_u(u, u2, t, m));
-        axs[i] = fmaf(gg, dx, axs[i]);
-        ays[i] = fmaf(gg, dy, ays[i]);
-      }
-    };
-    // a class of far subhalos, kFuseSubhalos per basic block: the scheduler overlaps one's
-    // reciprocal square roots and loads with another's polynomial
-    auto far_class = [&](unsigned mask, auto Kc) {
-      constexpr int kRec = 5;  // t0..t4: centre and series coefficients
-      while (mask) {
-        const int q0 = __ffs(mask) - 1;
-        mask &= mask - 1u;
-        if (kFuseSubhalos > 1 && mask) {
-          const int q1 = __ffs(mask) - 1;
-          mask &= mask - 1u;
-          float4 ta[kRec], tb[kRec];
-#pragma unroll
-          for (int c = 0; c < kRec; ++c) {
-            ta[c] = area.sub[q0][c];
-            tb[c] = area.sub[q1][c];
-          }
-          far_pairs(ta, Kc);
-          far_pairs(tb, Kc);
-        } else {
-          float4 ta[kRec];
-#pragma unroll
-          for (int c = 0; c < kRec; ++c) ta[c] = area.sub[q0][c];
-          far_pairs(ta, Kc);
-        }
-      }
-    };
-    far_class(m6, std::integral_constant<int, kFarTerms>{});
-    far_class(m4, std::integral_constant<int, 4>{});
-    far_class(m3, std::integral_constant<int, 3>{});
-    for (unsigned mask = near_mask; mask; mask &= mask - 1u) {
-      const int q = __ffs(mask) - 1;
+    far_class(0, n6, std::integral_constant<int, kFarTerms>{});
+    far_class(b4, b4 + n4, std::integral_constant<int, 4>{});
+    far_class(b3, b3 + n3, std::integral_constant<int, 3>{});
+#pragma unroll 1
+    for (int i = bn; i < bn + nn; ++i) {
+      const int q = area.list[i];
       float4 t[kSubStride], m[kMidStride];
+      t[0] = area.sub[q][0];
+      t[1] = area.marked[q][0];
 #pragma unroll
-      for (int c = 0; c < kSubStride; ++c) t[c] = area.sub[q][c];
+      for (int c = 1; c < kFarRec; ++c) t[1 + c] = area.sub[q][c];
+      t[5] = make_float4(0.f, 0.f, 0.f, 0.f);
+      t[6] = area.marked[q][1];
+      t[7] = t[5];
 #pragma unroll
-      for (int c = 0; c < kMidStride; ++c) m[c] = area.mid[q][c];
+      for (int c = 0; c < kMidStride; ++c) m[c] = area.marked[q][2 + c];
       near_pairs(t, m);
     }
     __syncwarp();
@@ -293,8 +314,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     area.part[2 * i][lane] = make_float2(ax2[i].x, ay2[i].x);
     area.part[2 * i + 1][lane] = make_float2(ax2[i].y, ay2[i].y);
   }
-#pragma unroll
-  for (int i = 0; i < kS; ++i) area.part[2 * kP + i][lane] = make_float2(axs[i], ays[i]);
+  area.part[2 * kP][lane] = make_float2(ao_x, ao_y);
 }
 
 // Finalise a unit from its kTraceWarps slice partials (part(slice, k, lane) in slice order):
