@@ -73,6 +73,7 @@ struct TraceSmem {
       float4 marked[32][kNearRec];
       int list[kStageList];
       float4 box;  // the unit's bounding box (kept here rather than in registers)
+      float queue[kUnitPts * 32];  // closed-form arguments, then values, of one marked subhalo
     };
     float2 part[kUnitPts][32];
   } wa[NW];
@@ -211,17 +212,66 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       far_odd(ta, Kc);
     }
   };
+  // sample k's coordinates (k static) and its accumulators
+  auto sample_at = [&](int k, float& x, float& y) {
+    if (k == 2 * kP) { x = po_x; y = po_y; }
+    else if (k & 1) { x = px2[k >> 1].y; y = py2[k >> 1].y; }
+    else { x = px2[k >> 1].x; y = py2[k >> 1].x; }
+  };
+  auto accumulate_at = [&](int k, float g, float dx, float dy) {
+    if (k == 2 * kP) { ao_x = fmaf(g, dx, ao_x); ao_y = fmaf(g, dy, ao_y); }
+    else if (k & 1) { ax2[k >> 1].y = fmaf(g, dx, ax2[k >> 1].y); ay2[k >> 1].y = fmaf(g, dy, ay2[k >> 1].y); }
+    else { ax2[k >> 1].x = fmaf(g, dx, ax2[k >> 1].x); ay2[k >> 1].x = fmaf(g, dy, ay2[k >> 1].x); }
+  };
+  // The closed forms of a marked subhalo's samples inside r_in (bit k of `inner`), spread over
+  // the whole warp: the samples of a few lanes' pixels would otherwise run them one sample
+  // position at a time with the other lanes idle.  Each lane queues its samples' arguments in
+  // sample order, the warp evaluates the queue 32 at a time, and each lane adds its values
+  // where the pair loop left them out, so every accumulator sees the same sequence of FMAs.
+  auto near_inner = [&](const float4* t, unsigned inner) {
+    const int c = __popc(inner);
+    int pre = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, pre, off);
+      if (lane >= off) pre += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, pre, 31);
+    float* qv = area.queue;
+    int o = pre - c;
+#pragma unroll
+    for (int k = 0; k < kUnitPts; ++k) {
+      if ((inner >> k) & 1u) {
+        float x, y;
+        sample_at(k, x, y);
+        const float dx = x + t[0].x, dy = y + t[0].z;
+        qv[o++] = fmaf(dx, dx, dy * dy) * t[1].y;
+      }
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int e = lane; e < total; e += 32) qv[e] = tnfw_g_inner(qv[e], t[1].z, t[1].w, t[6].w);
+    __syncwarp();
+    o = pre - c;
+#pragma unroll
+    for (int k = 0; k < kUnitPts; ++k) {
+      if ((inner >> k) & 1u) {
+        float x, y;
+        sample_at(k, x, y);
+        const float dx = x + t[0].x, dy = y + t[0].z;
+        accumulate_at(k, qv[o++], dx, dy);
+      }
+    }
+    __syncwarp();  // the queue is free for the next subhalo
+  };
   // subhalos the bounding-box test marked: series and annulus polynomial for every sample
-  // (packed, branch-free), each sample then keeps the form of its distance; only samples
-  // inside r_in call the closed forms
+  // (packed, branch-free), each sample then keeps the form of its distance; samples inside
+  // r_in add nothing here and take the closed form through the queue
   auto near_pairs = [&](const float4* t, const float4* m) {
     const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
     const float r_far2 = t[1].x, r_in2 = t[6].z;
-    auto pick = [&](float r2, float gs, float gm) {
-      if (r2 >= r_far2) return gs;
-      if (r2 >= r_in2) return gm;
-      return tnfw_g_inner(r2 * t[1].y, t[1].z, t[1].w, t[6].w);
-    };
+    auto pick = [&](float r2, float gs, float gm) { return r2 >= r_far2 ? gs : (r2 >= r_in2 ? gm : 0.f); };
+    unsigned inner = 0u;
 #pragma unroll
     for (int i = 0; i < kP; ++i) {
       const float2 dx = __fadd2_rn(px2[i], ncx), dy = __fadd2_rn(py2[i], ncy);
@@ -231,6 +281,8 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       const float2 gs = tnfw_series2_u(u, u2, t);
       const float2 gm = tnfw_mid2_u(u, u2, t, m);
       const float2 gg = make_float2(pick(r2.x, gs.x, gm.x), pick(r2.y, gs.y, gm.y));
+      inner |= (r2.x < r_in2 ? 1u : 0u) << (2 * i);
+      inner |= (r2.y < r_in2 ? 1u : 0u) << (2 * i + 1);
       ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
       ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
     }
@@ -238,8 +290,10 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     const float r2 = fmaf(dx, dx, dy * dy);
     const float u = rsqrt_ftz(r2), u2 = u * u;
     const float gg = pick(r2, tnfw_series_u(u, u2, t), tnfw_mid_u(u, u2, t, m));
+    inner |= (r2 < r_in2 ? 1u : 0u) << (2 * kP);
     ao_x = fmaf(gg, dx, ao_x);
     ao_y = fmaf(gg, dy, ao_y);
+    if (__any_sync(0xffffffffu, inner != 0u)) near_inner(t, inner);
   };
   // While staging, each lane tests its subhalo against the unit's bounding box: subhalos some
   // sample might see inside the far-field radius are marked (near); the others take the
