@@ -816,14 +816,15 @@ def fitting_extra(sim, W, dev):
 
 
 def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_sets: int = 2,
-                  warmup_requests: int = 3000):
+                  warmup_requests: int = 6000):
     """Serving: open-loop Poisson arrivals at each rate for `seconds`, drawn from a pool of
     `pool_size` pre-generated requests of the serving mix (70 % image / 30 % likelihood +
     gradient, grids 64..256, subhalos 0..20,000, PSF 5..31) that is cycled.  One server serves
     every rate; its PSFs are registered up front, as a deployment would, and an untimed warm-up
-    (the first `warmup_requests` of the pool submitted back to back) lets its slots size their
-    workspaces and capture their batch graphs before the first measured rate, whose statistics
-    are then reset.  Each pool entry has `out_sets` sets of output buffers used in turn, so a
+    (the whole pool submitted back to back) lets its slots size their workspaces and capture
+    their batch graphs before the first measured rate, whose statistics are then reset (a
+    warm-up of half the pool left the first rate to meet the other half's largest requests, and
+    a workspace growth inside it held the client up by 85 ms).  Each pool entry has `out_sets` sets of output buffers used in turn, so a
     buffer set is reused only pool_size * out_sets arrivals later, after its previous request
     finished (a reuse that had to wait for it is counted in `blocked_reuses`); a submit refused
     with LENS_ERR_BUSY (more than max_inflight = 4096 requests admitted) counts as rejected.
@@ -861,7 +862,12 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
     def submit(srv, j, c):
         return srv.submit_prepared(prepared[j][c])
     t0 = time.perf_counter()
-    warm = [submit(srv, j, 0) for j in range(min(warmup_requests, pool_size))]
+    n_warm = min(warmup_requests, pool_size)
+    warm = collections.deque()
+    for j in range(n_warm):
+        if len(warm) >= 2048:  # stays below the server's max_inflight admission limit
+            srv.wait(warm.popleft(), 600000)
+        warm.append(submit(srv, j, 0))
     for t in warm:
         srv.wait(t, 600000)
     t_warm = time.perf_counter() - t0
@@ -930,7 +936,7 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
         torch.cuda.synchronize()
     plain = len(imgs) / (time.perf_counter() - t1)
     sim.close()
-    return {"rates": out, "pool": pool_size, "warmup_requests": len(warm), "warmup_seconds": t_warm,
+    return {"rates": out, "pool": pool_size, "warmup_requests": n_warm, "warmup_seconds": t_warm,
             "plain_images_per_s": plain, "plain_images": len(imgs),
             "mix": "70% image / 30% likelihood+gradient, grids 64..256 (even), s = 1, subhalos log-uniform "
                    "0..20000, PSF 5..31"}

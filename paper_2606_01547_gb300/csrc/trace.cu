@@ -61,7 +61,7 @@ int unit_count(int nx, int ny, int s) {
 constexpr int kStageList = 34;
 constexpr int kFarRec = 4;                 // t0, t2, t3, t4: centre and series coefficients
 constexpr int kNearRec = 2 + kMidStride;   // t1, t6 and the annulus block
-static_assert(kUnitPts == 2 * kPackedPairs + 1, "a lane runs kPackedPairs sample pairs and one odd sample");
+static_assert(kUnitPts > 2 * kPackedPairs, "a lane runs kPackedPairs sample pairs and at least one scalar sample");
 
 template <int NW>
 struct TraceSmem {
@@ -108,7 +108,7 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
 // kTraceWarps-way split of the subhalo list and writes its 288 partials to wa[area0 + w].part.
 //
 // A lane's first 2 kPackedPairs samples run as packed pairs (FP32x2 instructions, two samples
-// per issue slot), the odd one as scalars; the two kinds run on different FP32 pipes.  The
+// per issue slot), the rest as scalars; the two kinds run on different FP32 pipes.  The
 // packed operations are element-wise the same IEEE operations as the scalar ones, so every
 // sample's deflection is the same whichever kind it is.
 template <int NWC>
@@ -126,7 +126,8 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   auto& area = sm.wa[area0 + w];
 
   float2 px2[kP], py2[kP], ax2[kP], ay2[kP];
-  float po_x, po_y, ao_x = 0.f, ao_y = 0.f;  // the odd sample and its sums
+  constexpr int kS = kUnitPts - 2 * kP;  // scalar samples
+  float po_x[kS], po_y[kS], ao_x[kS], ao_y[kS];  // the scalar samples and their sums
   float xmin = 3.0e38f, xmax = -3.0e38f, ymin = 3.0e38f, ymax = -3.0e38f;
 #pragma unroll
   for (int k = 0; k < kUnitPts; ++k) {
@@ -136,9 +137,9 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     sample_xy(sys, g, q, x, y);
     xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
     ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
-    if (k == 2 * kP) {
-      po_x = x;
-      po_y = y;
+    if (k >= 2 * kP) {
+      po_x[k - 2 * kP] = x;
+      po_y[k - 2 * kP] = y;
     } else if (k & 1) {
       px2[k >> 1].y = x;
       py2[k >> 1].y = y;
@@ -151,6 +152,11 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   for (int i = 0; i < kP; ++i) {
     ax2[i] = make_float2(0.f, 0.f);
     ay2[i] = make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < kS; ++i) {
+    ao_x[i] = 0.f;
+    ao_y[i] = 0.f;
   }
   // bounding box of the unit's samples (uniform across the warp)
 #pragma unroll
@@ -177,13 +183,16 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
 #pragma unroll
     for (int i = 0; i < kP; ++i) packed_pair(t, Kc, px2[i], py2[i], ax2[i], ay2[i]);
   };
-  auto far_odd = [&](const float4* t, auto Kc) {  // the odd sample
+  auto far_scalar = [&](const float4* t, auto Kc) {  // the scalar samples
     constexpr int K = decltype(Kc)::value;
-    const float dx = po_x + t[0].x, dy = po_y + t[0].z;
-    const float u = rsqrt_ftz(fmaf(dx, dx, dy * dy));
-    const float gg = tnfw_series_k<K>(u, u * u, t);
-    ao_x = fmaf(gg, dx, ao_x);
-    ao_y = fmaf(gg, dy, ao_y);
+#pragma unroll
+    for (int i = 0; i < kS; ++i) {
+      const float dx = po_x[i] + t[0].x, dy = po_y[i] + t[0].z;
+      const float u = rsqrt_ftz(fmaf(dx, dx, dy * dy));
+      const float gg = tnfw_series_k<K>(u, u * u, t);
+      ao_x[i] = fmaf(gg, dx, ao_x[i]);
+      ao_y[i] = fmaf(gg, dy, ao_y[i]);
+    }
   };
   auto load_far = [&](int q, float4* t) {
     t[0] = area.sub[q][0];
@@ -201,25 +210,28 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       load_far(qq.x, ta);
       load_far(qq.y, tb);
       far_samples(ta, Kc);
-      far_odd(ta, Kc);
+      far_scalar(ta, Kc);
       far_samples(tb, Kc);
-      far_odd(tb, Kc);
+      far_scalar(tb, Kc);
     }
     if (q < e) {
       float4 ta[5];
       load_far(area.list[q], ta);
       far_samples(ta, Kc);
-      far_odd(ta, Kc);
+      far_scalar(ta, Kc);
     }
   };
   // sample k's coordinates (k static) and its accumulators
   auto sample_at = [&](int k, float& x, float& y) {
-    if (k == 2 * kP) { x = po_x; y = po_y; }
+    if (k >= 2 * kP) { x = po_x[k - 2 * kP]; y = po_y[k - 2 * kP]; }
     else if (k & 1) { x = px2[k >> 1].y; y = py2[k >> 1].y; }
     else { x = px2[k >> 1].x; y = py2[k >> 1].x; }
   };
   auto accumulate_at = [&](int k, float g, float dx, float dy) {
-    if (k == 2 * kP) { ao_x = fmaf(g, dx, ao_x); ao_y = fmaf(g, dy, ao_y); }
+    if (k >= 2 * kP) {
+      ao_x[k - 2 * kP] = fmaf(g, dx, ao_x[k - 2 * kP]);
+      ao_y[k - 2 * kP] = fmaf(g, dy, ao_y[k - 2 * kP]);
+    }
     else if (k & 1) { ax2[k >> 1].y = fmaf(g, dx, ax2[k >> 1].y); ay2[k >> 1].y = fmaf(g, dy, ay2[k >> 1].y); }
     else { ax2[k >> 1].x = fmaf(g, dx, ax2[k >> 1].x); ay2[k >> 1].x = fmaf(g, dy, ay2[k >> 1].x); }
   };
@@ -286,13 +298,16 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
       ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
     }
-    const float dx = po_x + t[0].x, dy = po_y + t[0].z;
-    const float r2 = fmaf(dx, dx, dy * dy);
-    const float u = rsqrt_ftz(r2), u2 = u * u;
-    const float gg = pick(r2, tnfw_series_u(u, u2, t), tnfw_mid_u(u, u2, t, m));
-    inner |= (r2 < r_in2 ? 1u : 0u) << (2 * kP);
-    ao_x = fmaf(gg, dx, ao_x);
-    ao_y = fmaf(gg, dy, ao_y);
+#pragma unroll
+    for (int i = 0; i < kS; ++i) {
+      const float dx = po_x[i] + t[0].x, dy = po_y[i] + t[0].z;
+      const float r2 = fmaf(dx, dx, dy * dy);
+      const float u = rsqrt_ftz(r2), u2 = u * u;
+      const float gg = pick(r2, tnfw_series_u(u, u2, t), tnfw_mid_u(u, u2, t, m));
+      inner |= (r2 < r_in2 ? 1u : 0u) << (2 * kP + i);
+      ao_x[i] = fmaf(gg, dx, ao_x[i]);
+      ao_y[i] = fmaf(gg, dy, ao_y[i]);
+    }
     if (__any_sync(0xffffffffu, inner != 0u)) near_inner(t, inner);
   };
   // While staging, each lane tests its subhalo against the unit's bounding box: subhalos some
@@ -368,7 +383,8 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     area.part[2 * i][lane] = make_float2(ax2[i].x, ay2[i].x);
     area.part[2 * i + 1][lane] = make_float2(ax2[i].y, ay2[i].y);
   }
-  area.part[2 * kP][lane] = make_float2(ao_x, ao_y);
+#pragma unroll
+  for (int i = 0; i < kS; ++i) area.part[2 * kP + i][lane] = make_float2(ao_x[i], ao_y[i]);
 }
 
 // Finalise a unit from its kTraceWarps slice partials (part(slice, k, lane) in slice order):
