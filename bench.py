@@ -392,6 +392,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
         extras["fitting"] = fitting_extra(sim, W, dev)
         extras["serving"] = serving_extra(lenssim, W, args.serve_rates, args.serve_seconds)
         extras["per_config"] = per_config_extra(sim, lenssim, W, dev, args.cpu_budget_s)
+        extras["far_field"] = far_field_extra(sim, lenssim, W, dev)  # last: it re-tunes the variant
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -715,6 +716,72 @@ def fft_conv_extra(sim, W, dev, n_img: int = 64):
     return res
 
 
+def far_field_extra(sim, lenssim, W, dev, reps: int = 20):
+    """The optional far-field interpolation of the subhalo sum on the benchmark image (200^2,
+    s = 3, 10,000 TNFW, 21x21 PSF, seed 1000): per kappa, the fraction of (unit, subhalo) pairs
+    it interpolates, the whole-image error against the FP64 oracle's exact sum, and the
+    device-resident images/s (trace + PSF, CUDA events, the launch variant autotuned for that
+    kappa).  kappa = 0 is the exact sum the headline measures."""
+    import ctypes
+    import torch
+    import oracle
+    oracle.build()
+    system = W.substructure_system(1000)
+    ref = oracle.image(system)
+    floor = _rel_linf(oracle.image(system, fp32=True), ref)
+    # interpolated fraction: per unit (8x4 pixels at s = 3), subhalos at box distance >= kappa h
+    # that the near-field test does not mark (box distance >= 7 max(tau, 1) Rs)
+    cx, cy, Rs, _, rt = system.subhalos.astype(np.float64)
+    tm = np.maximum(rt / Rs, 1.0)
+    g = system.grid
+    dp, nx, s = float(g.dpix), g.nx, g.s
+    def coord(j, b):
+        return (j - 0.5 * (nx - 1) + (b + 0.5) / s - 0.5) * dp
+    dists, halfw = [], []
+    for by in range(g.ny // 4):
+        y0, y1 = coord(by * 4, 0), coord(by * 4 + 3, s - 1)
+        for bx in range(nx // 8):
+            x0, x1 = coord(bx * 8, 0), coord(bx * 8 + 7, s - 1)
+            ddx = np.maximum(np.maximum(x0 - cx, cx - x1), 0.0)
+            ddy = np.maximum(np.maximum(y0 - cy, cy - y1), 0.0)
+            dists.append(np.hypot(ddx, ddy))
+            halfw.append(0.5 * max(x1 - x0, y1 - y0))
+    dists = np.array(dists)
+    halfw = np.array(halfw)[:, None]
+    marked = dists < 7.0 * tm * Rs
+    L = lenssim.lib()
+    st = torch.cuda.current_stream()
+    out = torch.empty((g.ny, g.nx), device=dev)
+    ptrs = (ctypes.c_void_p * 1)(out.data_ptr())
+    keep = []
+    c = sim.system_struct(system, keep, subhalos=torch.from_numpy(system.subhalos).to(dev))
+    res = {}
+    for kappa in (0.0, 3.0, 4.0, 6.0):
+        sim.set_far_field(kappa)
+        tune = sim.autotune(system, use_cache=False)
+        for _ in range(3):
+            L.lens_sim_image(sim.h, ctypes.byref(c), 1, ptrs, int(st.cuda_stream))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            rc = L.lens_sim_image(sim.h, ctypes.byref(c), 1, ptrs, int(st.cuda_stream))
+            if rc:
+                raise lenssim.LensSimError(rc, sim.last_error())
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        frac = float(((dists >= kappa * halfw) & ~marked).mean()) if kappa > 0 else 0.0
+        res[f"{kappa:g}"] = {"images_per_s": 1e3 / ms, "ms_per_image": ms, "variant": tune["name"],
+                             "trace_ms_by_variant": tune["ms"], "interpolated_pair_fraction": frac,
+                             "rel_linf_vs_oracle": _rel_linf(out.cpu().numpy(), ref)}
+    sim.set_far_field(0.0)
+    return {"kappa": res, "oracle_floor": floor, "tolerance": max(1e-5, 2 * floor),
+            "stated_bound_per_subhalo": {"3": 1.2e-6, "4": 1.4e-7, "6": 6e-9},
+            "workload": "200x200 at 0.04\", s = 3, EPL + shear, 10,000 TNFW, Sersic, 21x21 Moffat (seed 1000); "
+                        f"{reps} device-resident calls per kappa after 3 warm-up calls"}
+
+
 def subhalo_scaling_extra(sim, W, dev):
     """Trace-kernel throughput against the subhalo count on the benchmark grid (200x200, s = 3):
     the pair sum should stay at a flat pairs/s once the subhalos fill the GPU."""
@@ -958,7 +1025,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, gradient and serving lines")
     ap.add_argument("--variant", type=int, default=-1, help="fixed trace launch variant instead of autotuning")
     ap.add_argument("--extra-only", default="", choices=["", "differentiation", "batched", "batched_small_systems",
-                                                          "fitting", "scaling", "serving", "per_config"],
+                                                          "fitting", "scaling", "far_field", "serving", "per_config"],
                     help="profiling mode: only this one extra measurement")
     ap.add_argument("--fft-only", type=int, default=0, metavar="N_IMG",
                     help="profiling mode: only the FFT-versus-direct PSF measurement (N_IMG images per call)")
@@ -987,6 +1054,7 @@ def main():
               "batched_small_systems": lambda: batched_extra(sim, lenssim, W, dev, args.batch_systems, small=True),
               "fitting": lambda: fitting_extra(sim, W, dev),
               "scaling": lambda: subhalo_scaling_extra(sim, W, dev),
+              "far_field": lambda: far_field_extra(sim, lenssim, W, dev),
               "serving": lambda: serving_extra(lenssim, W, args.serve_rates, args.serve_seconds),
               "per_config": lambda: per_config_extra(sim, lenssim, W, dev, args.cpu_budget_s)}[args.extra_only]
         print(json.dumps({args.extra_only: fn()}), flush=True)

@@ -188,6 +188,25 @@ int lens_sim_autotune(lens_sim* sim, const lens_system* sample, int reps, int* b
                       float* ms_per_variant, int n_ms, void* stream);
 int lens_sim_set_variant(lens_sim* sim, int variant);
 
+/* Far-field interpolation of the subhalo sum (optional; off by default; CHANGES RESULTS within
+ * the bound below).  The paper's method sums every subhalo at every traced point ("Statement of
+ * need": ray tracing through tens of thousands of substructures); this option approximates the
+ * far part of that sum.  With kappa > 0, lens_sim_image and lens_sim_autotune sum a subhalo that
+ * is at least kappa * h from a work unit's box of traced points (h: the larger half-width of the
+ * box; the subhalos the kernel's near-field test marks are never approximated) at the box's
+ * 8 x 8 Chebyshev nodes instead of at the unit's 288 points, and interpolate the unit's summed
+ * node values to its points with the tensor Lagrange basis: the local-expansion step of a
+ * black-box fast multipole method (Fong and Darve 2009).  Error bound, per approximated
+ * subhalo, as the largest error of its deflection over the box relative to its largest value
+ * there (FP64 analysis over tau in [0.5, 20], Rs in [0.002, 0.1], all directions, box aspect
+ * 1:1 .. 4:1): kappa = 3: 1.2e-6, 4: 1.4e-7, 6: 6e-9; the error of a traced point's total
+ * deflection is below that fraction of the sum of the approximated subhalos' magnitudes, plus
+ * FP32 rounding of the interpolation (Lebesgue constant of the 8 x 8 grid below 6).
+ * kappa = 0 restores the exact sum; 0 < kappa < 3 or a non-finite kappa is LENS_ERR_INVALID_ARG.
+ * Every launch variant still gives bitwise-identical images.  The batched launch, the server,
+ * the likelihood and the no-alloc entry point always use the exact sum. */
+int lens_sim_set_far_field(lens_sim* sim, float kappa);
+
 /* Schedule of the batched launch (lens_sim_image with n_sys > 1; the batched configuration of
  * the paper's workloads): `form` is the persistent trace kernel (0: CTAs of 4 warps summing a
  * unit's 8 subhalo slices in two passes; 1: CTAs of 8 warps; 2: clusters of 2 CTAs x 4 warps),

@@ -48,7 +48,7 @@ struct DevSystem {
                                              // (nullptr without the profile)
   DevProfile defl[LENS_MAX_DEFLECTORS];
   int n_sub;
-  int pad_;
+  float far_kappa;  // > 0: far-field interpolation of the subhalo sum from kappa box half-widths
   const float4* sub;
   float* out;
 };

@@ -599,6 +599,7 @@ int lens_sim_image(lens_sim* s, const lens_system* systems, int n_sys, float* co
     const bool dev_out = is_device_ptr(out_images[i]);
     float* final_dst = dev_out ? out_images[i] : (float*)s->stage.p;
     d.out = (y.psf_id >= 0) ? (float*)s->img.p : final_dst;
+    d.far_kappa = s->far_kappa;
     cudaError_t e = launch_trace_variant(d, s->trace_variant, st);
     if (e != cudaSuccess) return cuda_fail(s, e, "trace kernel launch");
     if (y.psf_id >= 0 && (rc = psf_apply(s, (float*)s->img.p, final_dst, 1, d.ny, d.nx, y.psf_id, st, false)))
@@ -672,6 +673,14 @@ int lens_sim_set_variant(lens_sim* s, int variant) {
   return LENS_OK;
 }
 
+int lens_sim_set_far_field(lens_sim* s, float kappa) {
+  if (!s) return LENS_ERR_INVALID_ARG;
+  if (!std::isfinite(kappa) || kappa < 0.f || (kappa > 0.f && kappa < 3.f))
+    return fail(s, LENS_ERR_INVALID_ARG, "far-field kappa must be 0 or >= 3 (got %g)", (double)kappa);
+  s->far_kappa = kappa;
+  return LENS_OK;
+}
+
 int lens_sim_autotune(lens_sim* s, const lens_system* sample, int reps, int* best_variant, float* ms_per_variant,
                       int n_ms, void* stream) {
   if (!s) return LENS_ERR_INVALID_ARG;
@@ -691,6 +700,7 @@ int lens_sim_autotune(lens_sim* s, const lens_system* sample, int reps, int* bes
   if ((rc = upload_ell_table(s, *sample, d, st))) return rc;
   if ((rc = prepare_subhalos(s, *sample, (float4*)s->tab.p, (float*)s->raw_sub.p, &d.sub, &d.n_sub, st))) return rc;
   d.out = (float*)s->img.p;
+  d.far_kappa = s->far_kappa;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

@@ -120,6 +120,7 @@ struct lens_sim {
   int max_batch = 4096;
   int sm_count = 0;
   int trace_variant = 0;  // launch variant of the single-system trace kernel
+  float far_kappa = 0.f;  // far-field interpolation of the subhalo sum (0: exact)
   int batch_form = 0;     // persistent trace kernel of the batched launch (kBatchForms)
   int batch_order = 0;    // unit queue: 0 systems by per-unit cost (largest first), 1 as given
   int conv_method = 0;    // LENS_CONV_AUTO / _DIRECT / _FFT

@@ -56,12 +56,43 @@ int unit_count(int nx, int ny, int s) {
 // A warp stages 32 subhalos at a time, record q in lane q's slot, and lists them by class -- 6-,
 // 4-, 3-term far-field series, then the marked near-field subhalos -- in subhalo order within
 // the class, so each class is a counted loop over consecutive list entries (whose loads the
-// compiler can issue ahead) rather than a scan of a ballot mask.  The first two classes start
-// on even list positions (one pad each at most), so a pair of entries loads as one int2.
-constexpr int kStageList = 34;
+// compiler can issue ahead) rather than a scan of a ballot mask.  Every class but the last
+// (marked) one starts on an even list position (one pad each at most), so a pair of entries
+// loads as one int2.  With the far-field interpolation, far subhalos form three more classes
+// (summed at the Chebyshev nodes) between the sample classes and the marked ones.
+constexpr int kStageList = 38;
 constexpr int kFarRec = 4;                 // t0, t2, t3, t4: centre and series coefficients
 constexpr int kNearRec = 2 + kMidStride;   // t1, t6 and the annulus block
 static_assert(kUnitPts > 2 * kPackedPairs, "a lane runs kPackedPairs sample pairs and at least one scalar sample");
+
+// Far-field interpolation (optional, changes results): a subhalo at least kappa times the box's
+// larger half-width from the unit's sample box is summed at the 8 x 8 Chebyshev nodes of the box
+// (first kind, x_i = cos(pi (i + 1/2) / 8) scaled to the box) rather than at its 288 samples,
+// and the unit's summed node values are interpolated to the samples with the tensor Lagrange
+// basis -- the local-expansion step of a black-box fast multipole method (Fong and Darve 2009).
+// Node n = 8 i + j sits at (x_i, y_j); lane l holds nodes 2l and 2l + 1 as one packed pair.
+constexpr int kFarNodes1 = 8;
+constexpr int kFarNodes = kFarNodes1 * kFarNodes1;
+static_assert(kFarNodes == 2 * 32, "a lane evaluates two nodes");
+__constant__ float c_cheb8[kFarNodes1] = {9.807852804e-01f, 8.314696123e-01f, 5.555702330e-01f, 1.950903220e-01f,
+                                          -1.950903220e-01f, -5.555702330e-01f, -8.314696123e-01f, -9.807852804e-01f};
+// 1 / prod_{k != i} (x_i - x_k): the Lagrange basis is L_i(t) = w_i prod_{k != i} (t - x_k)
+__constant__ float c_cheb8_w[kFarNodes1] = {3.121445152e+00f, -8.889123728e+00f, 1.330351380e+01f, -1.569256449e+01f,
+                                            1.569256449e+01f, -1.330351380e+01f, 8.889123728e+00f, -3.121445152e+00f};
+
+__device__ __forceinline__ void cheb8_lagrange(float t, float* L) {
+  float d[kFarNodes1], pre[kFarNodes1], suf[kFarNodes1];
+#pragma unroll
+  for (int k = 0; k < kFarNodes1; ++k) d[k] = t - c_cheb8[k];
+  pre[0] = 1.f;
+#pragma unroll
+  for (int k = 1; k < kFarNodes1; ++k) pre[k] = pre[k - 1] * d[k - 1];
+  suf[kFarNodes1 - 1] = 1.f;
+#pragma unroll
+  for (int k = kFarNodes1 - 2; k >= 0; --k) suf[k] = suf[k + 1] * d[k + 1];
+#pragma unroll
+  for (int k = 0; k < kFarNodes1; ++k) L[k] = c_cheb8_w[k] * (pre[k] * suf[k]);
+}
 
 template <int NW>
 struct TraceSmem {
@@ -73,11 +104,13 @@ struct TraceSmem {
       float4 marked[32][kNearRec];
       int list[kStageList];
       float4 box;  // the unit's bounding box (kept here rather than in registers)
-      float queue[kUnitPts * 32];  // closed-form arguments, then values, of one marked subhalo
+      float queue[kUnitPts * 32];  // closed-form arguments, then values, of one marked subhalo;
+                                   // at the end, the slice's far-field node sums (float2 x 64)
     };
     float2 part[kUnitPts][32];
   } wa[NW];
   float I[kUnitPts * 32];
+  float2 nodes[kFarNodes];  // the unit's far-field node sums (interpolation only)
 };
 
 struct UnitGeom {
@@ -111,7 +144,7 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
 // per issue slot), the rest as scalars; the two kinds run on different FP32 pipes.  The
 // packed operations are element-wise the same IEEE operations as the scalar ones, so every
 // sample's deflection is the same whichever kind it is.
-template <int NWC>
+template <int NWC, bool FAR = false>
 __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGeom& g, int slice0,
                                               TraceSmem<NWC>& sm, int area0 = 0) {
   constexpr int kP = kPackedPairs;
@@ -168,6 +201,19 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   }
   if (lane == 0) area.box = make_float4(xmin, xmax, ymin, ymax);
   __syncwarp();
+  // far-field interpolation: the lane's two nodes and their sums
+  float2 pn_x = make_float2(0.f, 0.f), pn_y = pn_x, an_x = pn_x, an_y = pn_x;
+  float far_d2 = 3.0e38f;
+  if constexpr (FAR) {
+    const float hx = 0.5f * (xmax - xmin), hy = 0.5f * (ymax - ymin);
+    const float cxb = 0.5f * (xmin + xmax), cyb = 0.5f * (ymin + ymax);
+    const float hf = sys.far_kappa * fmaxf(hx, hy);
+    far_d2 = hf * hf;
+    const int ni = lane >> 2, nj = 2 * (lane & 3);
+    const float xn = fmaf(hx, c_cheb8[ni], cxb);
+    pn_x = make_float2(xn, xn);
+    pn_y = make_float2(fmaf(hy, c_cheb8[nj], cyb), fmaf(hy, c_cheb8[nj + 1], cyb));
+  }
   // far-field series truncated after d_K for the record t of one subhalo: a packed sample pair
   auto packed_pair = [&](const float4* t, auto Kc, float2 px, float2 py, float2& ax, float2& ay) {
     constexpr int K = decltype(Kc)::value;
@@ -276,6 +322,25 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     }
     __syncwarp();  // the queue is free for the next subhalo
   };
+  // far-field interpolation: a class of far subhalos at list positions [b, e), b even, summed
+  // at the lane's two nodes
+  auto node_class = [&](int b, int e, auto Kc) {
+    int q = b;
+#pragma unroll 1
+    for (; q + 1 < e; q += 2) {
+      float4 ta[5], tb[5];
+      const int2 qq = *reinterpret_cast<const int2*>(&area.list[q]);
+      load_far(qq.x, ta);
+      load_far(qq.y, tb);
+      packed_pair(ta, Kc, pn_x, pn_y, an_x, an_y);
+      packed_pair(tb, Kc, pn_x, pn_y, an_x, an_y);
+    }
+    if (q < e) {
+      float4 ta[5];
+      load_far(area.list[q], ta);
+      packed_pair(ta, Kc, pn_x, pn_y, an_x, an_y);
+    }
+  };
   // subhalos the bounding-box test marked: series and annulus polynomial for every sample
   // (packed, branch-free), each sample then keeps the form of its distance; samples inside
   // r_in add nothing here and take the closed form through the queue
@@ -319,7 +384,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   for (int base = lo; base < hi; base += 32) {
     const int idx = base + lane;
     const bool alive = idx < hi;
-    bool near = false;
+    bool near = false, interp = false;
     int tier = 0;  // 0: 6-term series, 1: 4-term, 2: 3-term
     if (alive) {
       float4 st[kSubStride];
@@ -336,6 +401,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       const float d2 = fmaf(ddx, ddx, ddy * ddy);
       near = d2 < st[1].x;
       tier = d2 >= st[5].y ? 2 : (d2 >= st[5].x ? 1 : 0);
+      if constexpr (FAR) interp = !near && d2 >= far_d2;  // marked subhalos always run at the samples
       if (near) {
         area.marked[lane][0] = st[1];
         area.marked[lane][1] = st[6];
@@ -343,23 +409,43 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
         for (int c = 0; c < kMidStride; ++c) area.marked[lane][2 + c] = __ldg(mid_tab + (size_t)kMidStride * idx + c);
       }
     }
+    const bool direct = alive && !near && !interp;
     const unsigned mn = __ballot_sync(0xffffffffu, alive && near);
-    const unsigned m3 = __ballot_sync(0xffffffffu, alive && !near && tier == 2);
-    const unsigned m4 = __ballot_sync(0xffffffffu, alive && !near && tier == 1);
-    const unsigned m6 = __ballot_sync(0xffffffffu, alive && !near && tier == 0);
+    const unsigned m3 = __ballot_sync(0xffffffffu, direct && tier == 2);
+    const unsigned m4 = __ballot_sync(0xffffffffu, direct && tier == 1);
+    const unsigned m6 = __ballot_sync(0xffffffffu, direct && tier == 0);
     const int n6 = __popc(m6), n4 = __popc(m4), n3 = __popc(m3), nn = __popc(mn);
-    const int b4 = (n6 + 1) & ~1, b3 = b4 + ((n4 + 1) & ~1), bn = b3 + n3;
+    const int b4 = (n6 + 1) & ~1, b3 = b4 + ((n4 + 1) & ~1);
+    int bn = b3 + n3;
+    unsigned f3 = 0u, f4 = 0u, f6 = 0u;
+    int nf6 = 0, nf4 = 0, nf3 = 0, bf6 = bn, bf4 = bn, bf3 = bn;
+    if constexpr (FAR) {
+      f3 = __ballot_sync(0xffffffffu, interp && tier == 2);
+      f4 = __ballot_sync(0xffffffffu, interp && tier == 1);
+      f6 = __ballot_sync(0xffffffffu, interp && tier == 0);
+      nf6 = __popc(f6); nf4 = __popc(f4); nf3 = __popc(f3);
+      bf6 = b3 + ((n3 + 1) & ~1);
+      bf4 = bf6 + ((nf6 + 1) & ~1);
+      bf3 = bf4 + ((nf4 + 1) & ~1);
+      bn = bf3 + nf3;
+    }
     if (alive) {
       const unsigned below = (1u << lane) - 1u;
-      const int pos = near ? bn + __popc(mn & below)
-                           : (tier == 2 ? b3 + __popc(m3 & below)
-                                        : (tier == 1 ? b4 + __popc(m4 & below) : __popc(m6 & below)));
+      int pos;
+      if (near) pos = bn + __popc(mn & below);
+      else if (interp) pos = tier == 2 ? bf3 + __popc(f3 & below) : (tier == 1 ? bf4 + __popc(f4 & below) : bf6 + __popc(f6 & below));
+      else pos = tier == 2 ? b3 + __popc(m3 & below) : (tier == 1 ? b4 + __popc(m4 & below) : __popc(m6 & below));
       area.list[pos] = lane;
     }
     __syncwarp();
     far_class(0, n6, std::integral_constant<int, kFarTerms>{});
     far_class(b4, b4 + n4, std::integral_constant<int, 4>{});
     far_class(b3, b3 + n3, std::integral_constant<int, 3>{});
+    if constexpr (FAR) {
+      node_class(bf6, bf6 + nf6, std::integral_constant<int, kFarTerms>{});
+      node_class(bf4, bf4 + nf4, std::integral_constant<int, 4>{});
+      node_class(bf3, bf3 + nf3, std::integral_constant<int, 3>{});
+    }
 #pragma unroll 1
     for (int i = bn; i < bn + nn; ++i) {
       const int q = area.list[i];
@@ -385,13 +471,45 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   }
 #pragma unroll
   for (int i = 0; i < kS; ++i) area.part[2 * kP + i][lane] = make_float2(ao_x[i], ao_y[i]);
+  if constexpr (FAR) {  // the slice's node sums, for the unit's interpolation
+    float2* nv = reinterpret_cast<float2*>(area.queue);
+    nv[2 * lane] = make_float2(an_x.x, an_y.x);
+    nv[2 * lane + 1] = make_float2(an_x.y, an_y.y);
+  }
+}
+
+// Far-field interpolation: the unit's node sums from its kTraceWarps slices' (node(slice, n), in
+// slice order) into `nodes`.  Executed by `nthr` threads, ends with a CTA barrier.
+template <class NodeFn>
+__device__ __forceinline__ void unit_sum_nodes(float2* nodes, int nthr, NodeFn node) {
+  for (int n = threadIdx.x; n < kFarNodes; n += nthr) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int sl = 0; sl < kTraceWarps; ++sl) {
+      const float2 v = node(sl, n);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    nodes[n] = acc;
+  }
+  __syncthreads();
 }
 
 // Finalise a unit from its kTraceWarps slice partials (part(slice, k, lane) in slice order):
-// main deflectors, lens equation, source, then the bin-down.  Executed by `nthr` threads.
-template <class PartFn>
+// main deflectors, lens equation, source, then the bin-down.  Executed by `nthr` threads.  With
+// FAR, each sample adds the interpolant of the node sums (`nodes`, over the box `box`).
+template <bool FAR = false, class PartFn>
 __device__ __forceinline__ void unit_finalize(const DevSystem& sys, const UnitGeom& g, float* I, int nthr,
-                                              PartFn part) {
+                                              PartFn part, const float2* nodes = nullptr,
+                                              float4 box = make_float4(0.f, 0.f, 0.f, 0.f)) {
+  float cxb = 0.f, cyb = 0.f, ihx = 0.f, ihy = 0.f;
+  if constexpr (FAR) {
+    const float hx = 0.5f * (box.y - box.x), hy = 0.5f * (box.w - box.z);
+    cxb = 0.5f * (box.x + box.y);
+    cyb = 0.5f * (box.z + box.w);
+    ihx = hx > 0.f ? 1.f / hx : 0.f;  // a box one sample wide: every sample at t = 0
+    ihy = hy > 0.f ? 1.f / hy : 0.f;
+  }
   for (int idx = threadIdx.x; idx < 32 * kUnitPts; idx += nthr) {
     const int k = idx >> 5, l = idx & 31;
     const int q = l * kUnitPts + k;
@@ -405,6 +523,26 @@ __device__ __forceinline__ void unit_finalize(const DevSystem& sys, const UnitGe
     }
     float x, y;
     sample_xy(sys, g, q, x, y);
+    if constexpr (FAR) {
+      float lx[kFarNodes1], ly[kFarNodes1];
+      cheb8_lagrange((x - cxb) * ihx, lx);
+      cheb8_lagrange((y - cyb) * ihy, ly);
+      float fx = 0.f, fy = 0.f;
+#pragma unroll
+      for (int i = 0; i < kFarNodes1; ++i) {
+        float rx = 0.f, ry = 0.f;
+#pragma unroll
+        for (int j = 0; j < kFarNodes1; ++j) {
+          const float2 v = nodes[kFarNodes1 * i + j];
+          rx = fmaf(ly[j], v.x, rx);
+          ry = fmaf(ly[j], v.y, ry);
+        }
+        fx = fmaf(lx[i], rx, fx);
+        fy = fmaf(lx[i], ry, fy);
+      }
+      sx += fx;
+      sy += fy;
+    }
     for (int d = 0; d < sys.n_defl; ++d) {
       float dax, day;
       alpha_profile(sys.defl[d], sys.ell_c, sys.ell_K, x, y, dax, day);
@@ -428,21 +566,30 @@ __device__ __forceinline__ void unit_bin_down(const DevSystem& sys, const UnitGe
   }
 }
 
+// The slices' node sums as written by unit_partials<FAR = true>
+template <int NW>
+__device__ __forceinline__ float2 slice_node(const TraceSmem<NW>& sm, int w, int n) {
+  return reinterpret_cast<const float2*>(sm.wa[w].queue)[n];
+}
+
 // One unit of one system by one CTA of kTraceWarps warps; ends with a CTA barrier.
+template <bool FAR = false>
 __device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceSmem<kTraceWarps>& sm) {
   const UnitGeom g = unit_geom(sys, blk);
-  unit_partials<kTraceWarps>(sys, g, 0, sm);
+  unit_partials<kTraceWarps, FAR>(sys, g, 0, sm);
   __syncthreads();
-  unit_finalize(sys, g, sm.I, 32 * kTraceWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; });
+  if constexpr (FAR) unit_sum_nodes(sm.nodes, 32 * kTraceWarps, [&](int sl, int n) { return slice_node(sm, sl, n); });
+  unit_finalize<FAR>(sys, g, sm.I, 32 * kTraceWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; },
+                     sm.nodes, sm.wa[0].box);
   __syncthreads();
   unit_bin_down(sys, g, sm.I, 32 * kTraceWarps);
   __syncthreads();
 }
 
-template <int MINB>
+template <int MINB, bool FAR = false>
 __global__ void __launch_bounds__(32 * kTraceWarps, MINB) trace_image_kernel(const __grid_constant__ DevSystem sys) {
   __shared__ TraceSmem<kTraceWarps> sm;
-  trace_unit(sys, blockIdx.x, sm);
+  trace_unit<FAR>(sys, blockIdx.x, sm);
 }
 
 // Subhalo deflection field of a grid (the likelihood's fixed field): the units, slices and
@@ -477,20 +624,25 @@ __global__ void __launch_bounds__(32 * kTraceWarps, 2) subhalo_field_kernel(cons
 // slices w and w + 4) into the same per-slice areas, then reduces them in slice order like the
 // one-CTA form, so its images are bitwise the same; the smaller CTA fits three per SM.
 constexpr int kHalfWarps = kTraceWarps / 2;
+template <bool FAR = false>
 __device__ __forceinline__ void trace_unit_2pass(const DevSystem& sys, int blk, TraceSmem<kTraceWarps>& sm) {
   const UnitGeom g = unit_geom(sys, blk);
 #pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) unit_partials<kTraceWarps>(sys, g, pass * kHalfWarps, sm, pass * kHalfWarps);
+  for (int pass = 0; pass < 2; ++pass)
+    unit_partials<kTraceWarps, FAR>(sys, g, pass * kHalfWarps, sm, pass * kHalfWarps);
   __syncthreads();
-  unit_finalize(sys, g, sm.I, 32 * kHalfWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; });
+  if constexpr (FAR) unit_sum_nodes(sm.nodes, 32 * kHalfWarps, [&](int sl, int n) { return slice_node(sm, sl, n); });
+  unit_finalize<FAR>(sys, g, sm.I, 32 * kHalfWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; },
+                     sm.nodes, sm.wa[0].box);
   __syncthreads();
   unit_bin_down(sys, g, sm.I, 32 * kHalfWarps);
   __syncthreads();
 }
 
+template <bool FAR = false>
 __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_image_2pass_kernel(const __grid_constant__ DevSystem sys) {
   __shared__ TraceSmem<kTraceWarps> sm;
-  trace_unit_2pass(sys, blockIdx.x, sm);
+  trace_unit_2pass<FAR>(sys, blockIdx.x, sm);
 }
 
 // Cluster form: CL CTAs of kTraceWarps/CL warps share one unit (register budget for 16 warps
@@ -498,7 +650,7 @@ __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_image_2pass_kernel(c
 // [r*NWC, (r+1)*NWC) of the same split; the leader reads every CTA's partials through
 // distributed shared memory in slice order, so the image is bitwise that of the one-CTA form,
 // while the finer CTAs balance the tail of the grid across the SMs.
-template <int CL>
+template <int CL, bool FAR = false>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(32 * (kTraceWarps / CL), 4 * CL / 2)
 trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
   constexpr int NWC = kTraceWarps / CL;
@@ -506,14 +658,17 @@ trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const UnitGeom g = unit_geom(sys, blockIdx.x / CL);
-  unit_partials<NWC>(sys, g, rank * NWC, sm);
+  unit_partials<NWC, FAR>(sys, g, rank * NWC, sm);
   cluster.sync();
   if (rank == 0) {
     const TraceSmem<NWC>* peers[CL];
 #pragma unroll
     for (int r = 0; r < CL; ++r) peers[r] = cluster.map_shared_rank(&sm, r);
-    unit_finalize(sys, g, sm.I, 32 * NWC,
-                  [&](int sl, int k, int l) { return peers[sl / NWC]->wa[sl % NWC].part[k][l]; });
+    if constexpr (FAR)
+      unit_sum_nodes(sm.nodes, 32 * NWC, [&](int sl, int n) { return slice_node(*peers[sl / NWC], sl % NWC, n); });
+    unit_finalize<FAR>(sys, g, sm.I, 32 * NWC,
+                       [&](int sl, int k, int l) { return peers[sl / NWC]->wa[sl % NWC].part[k][l]; },
+                       sm.nodes, sm.wa[0].box);
     __syncthreads();
     unit_bin_down(sys, g, sm.I, 32 * NWC);
   }
@@ -618,15 +773,21 @@ const char* trace_variant_name(int v) {
   }
 }
 
+template <bool FAR>
+static void launch_trace_form(const DevSystem& sys, int variant, int units, cudaStream_t st) {
+  switch (variant) {
+    case 1: trace_image_2pass_kernel<FAR><<<units, 32 * kHalfWarps, 0, st>>>(sys); break;
+    case 2: trace_cluster_kernel<2, FAR><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
+    case 3: trace_cluster_kernel<4, FAR><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
+    case 4: trace_cluster_kernel<8, FAR><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
+    default: trace_image_kernel<2, FAR><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
+  }
+}
+
 cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t st) {
   const int units = unit_count(sys.nx, sys.ny, sys.s);
-  switch (variant) {
-    case 1: trace_image_2pass_kernel<<<units, 32 * kHalfWarps, 0, st>>>(sys); break;
-    case 2: trace_cluster_kernel<2><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
-    case 3: trace_cluster_kernel<4><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
-    case 4: trace_cluster_kernel<8><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
-    default: trace_image_kernel<2><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
-  }
+  if (sys.far_kappa > 0.f) launch_trace_form<true>(sys, variant, units, st);
+  else launch_trace_form<false>(sys, variant, units, st);
   return cudaGetLastError();
 }
 

@@ -38,7 +38,8 @@ _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build",
 
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
             "lens_sim_register_subhalos", "lens_sim_image", "lens_sim_deflection", "lens_sim_convolve",
-            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_set_batch_schedule", "lens_sim_autotune_batch",
+            "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_set_far_field", "lens_sim_set_batch_schedule",
+            "lens_sim_autotune_batch",
             "lens_sim_set_conv_method", "lens_sim_grad",
             "lens_sim_linear_amp",
             "lens_sim_image_noalloc", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
@@ -124,6 +125,7 @@ def lib():
             L.lens_sim_autotune.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(ip),
                                             ctypes.POINTER(fp), ip, vp]
             L.lens_sim_set_variant.argtypes = [vp, ip]
+            L.lens_sim_set_far_field.argtypes = [vp, ctypes.c_float]
             L.lens_sim_set_batch_schedule.argtypes = [vp, ip, ip]
             L.lens_sim_autotune_batch.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(vp), ip,
                                                   ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(fp), vp]
@@ -279,6 +281,14 @@ class Simulator:
     def set_variant(self, variant: int) -> None:
         self._check(self._L.lens_sim_set_variant(self.h, int(variant)))
 
+    def set_far_field(self, kappa: float) -> None:
+        """Far-field interpolation of the subhalo sum for image calls (0: the exact sum, the
+        default; >= 3: subhalos kappa box half-widths from a work unit are summed at 8 x 8
+        Chebyshev nodes and interpolated -- changes results within the bound the C header
+        states)."""
+        self._check(self._L.lens_sim_set_far_field(self.h, float(kappa)))
+        self.far_kappa = float(kappa)
+
     def set_conv_method(self, method: str) -> None:
         """PSF method: "auto" (FFT for k >= 33 when it fits), "direct" or "fft"."""
         self._check(self._L.lens_sim_set_conv_method(self.h, CONV_METHODS[method]))
@@ -292,6 +302,8 @@ class Simulator:
         g = system.grid
         nsub = system.n_sub
         bucket = f"{g.nx}x{g.ny}/s{g.s}/sub{1 << max(nsub, 1).bit_length()}"
+        if getattr(self, "far_kappa", 0.0) > 0.0:
+            bucket += f"/far{self.far_kappa:g}"
         key = f"{torch.cuda.get_device_name(self.device)}|{bucket}"
         cache = {}
         if use_cache and os.path.exists(_TUNE_CACHE):

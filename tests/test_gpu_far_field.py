@@ -1,0 +1,110 @@
+"""GPU tests of the optional far-field interpolation of the subhalo sum (lens_sim_set_far_field).
+
+The option changes results: subhalos kappa box half-widths or more from a work unit are summed
+at the unit's 8 x 8 Chebyshev nodes and interpolated to its traced points.  At kappa >= 3 the
+stated per-subhalo error (1.2e-6 of its deflection, pinned on the CPU in
+test_far_field_bound.py) keeps whole images within the exact path's tolerance of the FP64
+oracle, which is what these tests check, together with the properties the exact path has:
+every launch variant bitwise identical, and kappa = 0 restoring the exact sum bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_01547_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sim():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_01547_gb300 import lenssim
+    s = lenssim.Simulator(device=0)
+    yield s
+    s.close()
+
+
+def rel_linf(got, ref):
+    return float(np.abs(np.asarray(got, np.float64) - ref).max() / np.abs(ref).max())
+
+
+def image_tol(system, ref):
+    floor = rel_linf(oracle.image(system, fp32=True), ref)
+    return max(1e-5, 2.0 * floor), floor
+
+
+def gpu_image(sim, system, kappa=0.0, variant=None, **kw):
+    sim.set_far_field(kappa)
+    if variant is not None:
+        sim.set_variant(variant)
+    try:
+        out = sim.image(system, **kw)[0]
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    finally:
+        sim.set_far_field(0.0)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_far_field_whole_images_match_oracle(sim, seed):
+    # the benchmark workload (200^2, s = 3, 10,000 subhalos, 21x21 PSF): ~97 % of the
+    # (unit, subhalo) pairs are interpolated at kappa = 4, ~98 % at kappa = 3
+    system = W.substructure_system(seed)
+    ref = oracle.image(system)
+    tol, floor = image_tol(system, ref)
+    exact = gpu_image(sim, system)
+    for kappa in (3.0, 4.0):
+        got = gpu_image(sim, system, kappa)
+        err = rel_linf(got, ref)
+        assert err <= tol, (kappa, err, floor)
+        # the option did replace most of the sum: the images differ from the exact ones, by
+        # far less than the tolerance
+        d = rel_linf(got, exact.astype(np.float64))
+        assert 0.0 < d <= 0.5 * tol, (kappa, d)
+
+
+def test_far_field_variants_are_bitwise_identical(sim):
+    from paper_2606_01547_gb300 import lenssim
+    system = W.substructure_system(5, n_sub=3000, nx=96, s=3, k=9)
+    imgs = [gpu_image(sim, system, 4.0, variant=v) for v in range(len(lenssim.TRACE_VARIANTS))]
+    sim.set_variant(0)
+    for v, im in enumerate(imgs[1:], 1):
+        assert np.array_equal(im, imgs[0]), lenssim.TRACE_VARIANTS[v]
+
+
+def test_far_field_off_restores_the_exact_sum(sim):
+    system = W.substructure_system(6, n_sub=2000, nx=64, s=2, k=7)
+    before = gpu_image(sim, system)
+    approx = gpu_image(sim, system, 3.0)
+    after = gpu_image(sim, system)
+    assert np.array_equal(before, after)
+    assert not np.array_equal(before, approx)
+
+
+@pytest.mark.parametrize("kappa", [1.0, 2.99, -1.0, math.nan, math.inf])
+def test_far_field_rejects_bad_kappa(sim, kappa):
+    from paper_2606_01547_gb300 import lenssim
+    with pytest.raises(lenssim.LensSimError) as e:
+        sim.set_far_field(kappa)
+    assert e.value.code == lenssim.LENS_ERR_INVALID_ARG
+    sim.set_far_field(0.0)
+
+
+@pytest.mark.parametrize("nx,ny,s,nsub,k", [(1, 1, 1, 200, 1), (1, 37, 2, 150, 3), (37, 1, 3, 90, 1),
+                                            (13, 7, 6, 333, 5), (41, 23, 8, 64, 3), (30, 30, 1, 0, 5)])
+def test_far_field_edge_grids_match_oracle(sim, nx, ny, s, nsub, k):
+    # boxes one sample wide in x, in y or in both (every node at the same point), the largest
+    # supersampling factors, ragged subhalo counts, and no subhalos at all
+    base = W.substructure_system(70 + s, n_sub=nsub, nx=8, s=s, k=k)
+    system = W.LensSystem(W.Grid(nx, ny, s, base.grid.dpix), base.deflectors, base.subhalos, base.source, base.psf)
+    ref = oracle.image(system)
+    tol, floor = image_tol(system, ref)
+    err = rel_linf(gpu_image(sim, system, 3.0), ref)
+    assert err <= tol, (err, floor)
+    if nsub == 0:
+        assert np.array_equal(gpu_image(sim, system, 3.0), gpu_image(sim, system))
