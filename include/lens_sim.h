@@ -203,8 +203,11 @@ int lens_sim_set_variant(lens_sim* sim, int variant);
  * deflection is below that fraction of the sum of the approximated subhalos' magnitudes, plus
  * FP32 rounding of the interpolation (Lebesgue constant of the 8 x 8 grid below 6).
  * kappa = 0 restores the exact sum; 0 < kappa < 3 or a non-finite kappa is LENS_ERR_INVALID_ARG.
- * Every launch variant still gives bitwise-identical images.  The batched launch, the server,
- * the likelihood and the no-alloc entry point always use the exact sum. */
+ * It applies to every lens_sim_image call of the handle (single systems and the batched launch
+ * of n_sys > 1 alike, each system's image the same either way) and to both autotuners.  Every
+ * launch variant and batch schedule still gives bitwise-identical images.  Ray shooting
+ * (lens_sim_deflection), the likelihood and its adjoint, the server and the no-alloc entry
+ * point always use the exact sum. */
 int lens_sim_set_far_field(lens_sim* sim, float kappa);
 
 /* Schedule of the batched launch (lens_sim_image with n_sys > 1; the batched configuration of

@@ -53,7 +53,8 @@ int capture_batch_graph(lens_sim* s, int kmax) {
   if (e != cudaSuccess) return cuda_fail(s, e, "begin capture");
   prep_batch_meta_kernel<<<s->sm_count * 4, 256, 0, s->cap_stream>>>(meta);
   cudaError_t e1 = cudaGetLastError();
-  cudaError_t e2 = launch_trace_batch_meta(meta, s->batch_form, trace_batch_grid(s->sm_count, s->batch_form),
+  const bool far = s->far_kappa > 0.f;
+  cudaError_t e2 = launch_trace_batch_meta(meta, s->batch_form, trace_batch_grid(s->sm_count, s->batch_form), far,
                                            s->cap_stream);
   cudaError_t e3 = launch_conv_batch_meta(meta, kmax, conv_batch_grid(s->sm_count, kmax), s->cap_stream);
   e = cudaStreamEndCapture(s->cap_stream, &graph);
@@ -71,6 +72,7 @@ int capture_batch_graph(lens_sim* s, int kmax) {
   s->graph_meta = s->batch_meta.p;
   s->graph_kmax = kmax;
   s->graph_form = s->batch_form;
+  s->graph_far = far;
   return LENS_OK;
 }
 
@@ -198,6 +200,7 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
     const lens_system& y = systems[i];
     DevSystem& d = hsys[r];
     fill_dev_system(y, d);
+    d.far_kappa = s->far_kappa;
     if (count_deflectors(y, LENS_MULTIPOLE_ELL) > 0) {
       d.ell_K = ell_table(y, (float*)(hb + o_ell));
       d.ell_c = (const float*)(db + o_ell);
@@ -240,7 +243,8 @@ int run_image_batch(lens_sim* s, const lens_system* systems, int n, float* const
   if (e != cudaSuccess) return cuda_fail(s, e, "record staging event");
 
   // ---- launch the captured graph (re-captured if the workspace moved or a PSF grew)
-  if (!s->graph_exec || s->graph_meta != s->batch_meta.p || s->graph_kmax < kmax || s->graph_form != s->batch_form) {
+  if (!s->graph_exec || s->graph_meta != s->batch_meta.p || s->graph_kmax < kmax || s->graph_form != s->batch_form ||
+      s->graph_far != (s->far_kappa > 0.f)) {
     if ((rc = capture_batch_graph(s, std::max(kmax, s->graph_kmax)))) return rc;
   }
   e = cudaGraphLaunch(s->graph_exec, st);

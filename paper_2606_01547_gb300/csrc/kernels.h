@@ -59,7 +59,7 @@ const char* trace_variant_name(int v);
 constexpr int kBatchForms = 3;
 const char* batch_form_name(int form);
 int trace_batch_grid(int sm_count, int form);
-cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int form, int grid, cudaStream_t st);
+cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int form, int grid, bool far, cudaStream_t st);
 
 // Summed subhalo deflection at every sample of the grid (main deflectors excluded), in the
 // order ((row * nx + column) * s + sub-row) * s + sub-column; the same sum as the image kernels.

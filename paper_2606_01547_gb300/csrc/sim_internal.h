@@ -164,4 +164,5 @@ struct lens_sim {
   void* graph_meta = nullptr;
   int graph_kmax = 0;
   int graph_form = -1;
+  bool graph_far = false;  // the captured graph runs the far-field interpolation
 };

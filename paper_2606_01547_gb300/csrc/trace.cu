@@ -692,6 +692,7 @@ __device__ __forceinline__ int batch_system_of(const int* __restrict__ unit_pref
   return lo;
 }
 
+template <bool FAR>
 __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_batch_kernel(BatchMeta* __restrict__ meta) {
   __shared__ TraceSmem<kTraceWarps> sm;
   __shared__ int s_ticket;
@@ -706,10 +707,11 @@ __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_batch_kernel(BatchMe
     __syncthreads();
     if (u >= total) return;
     const int i = batch_system_of(unit_prefix, n_sys, u);
-    trace_unit_2pass(systems[i], u - unit_prefix[i], sm);
+    trace_unit_2pass<FAR>(systems[i], u - unit_prefix[i], sm);
   }
 }
 
+template <bool FAR>
 __global__ void __launch_bounds__(32 * kTraceWarps, 2) trace_batch8_kernel(BatchMeta* __restrict__ meta) {
   __shared__ TraceSmem<kTraceWarps> sm;
   __shared__ int s_ticket;
@@ -724,10 +726,11 @@ __global__ void __launch_bounds__(32 * kTraceWarps, 2) trace_batch8_kernel(Batch
     __syncthreads();
     if (u >= total) return;
     const int i = batch_system_of(unit_prefix, n_sys, u);
-    trace_unit(systems[i], u - unit_prefix[i], sm);
+    trace_unit<FAR>(systems[i], u - unit_prefix[i], sm);
   }
 }
 
+template <bool FAR>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * kHalfWarps, 4)
 trace_batch_cluster_kernel(BatchMeta* __restrict__ meta) {
   constexpr int NWC = kHalfWarps;
@@ -749,12 +752,15 @@ trace_batch_cluster_kernel(BatchMeta* __restrict__ meta) {
     const int i = batch_system_of(unit_prefix, n_sys, u);
     const DevSystem& sys = systems[i];
     const UnitGeom g = unit_geom(sys, u - unit_prefix[i]);
-    unit_partials<NWC>(sys, g, rank * NWC, sm);
+    unit_partials<NWC, FAR>(sys, g, rank * NWC, sm);
     cluster.sync();
     if (rank == 0) {
       const TraceSmem<NWC>* peers[2] = {cluster.map_shared_rank(&sm, 0), cluster.map_shared_rank(&sm, 1)};
-      unit_finalize(sys, g, sm.I, 32 * NWC,
-                    [&](int sl, int k, int l) { return peers[sl / NWC]->wa[sl % NWC].part[k][l]; });
+      if constexpr (FAR)
+        unit_sum_nodes(sm.nodes, 32 * NWC, [&](int sl, int n) { return slice_node(*peers[sl / NWC], sl % NWC, n); });
+      unit_finalize<FAR>(sys, g, sm.I, 32 * NWC,
+                         [&](int sl, int k, int l) { return peers[sl / NWC]->wa[sl % NWC].part[k][l]; },
+                         sm.nodes, sm.wa[0].box);
       __syncthreads();
       unit_bin_down(sys, g, sm.I, 32 * NWC);
     }
@@ -812,9 +818,11 @@ int trace_batch_grid(int sm_count, int form) {
   if (!per_sm[form]) {
     int v = 0;
     cudaError_t e = cudaSuccess;
-    if (form == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch_kernel, 32 * kHalfWarps, 0);
-    if (form == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch8_kernel, 32 * kTraceWarps, 0);
-    if (form == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch_cluster_kernel, 32 * kHalfWarps, 0);
+    // the FAR instantiations have the same launch bounds and shared memory
+    if (form == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch_kernel<false>, 32 * kHalfWarps, 0);
+    if (form == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch8_kernel<false>, 32 * kTraceWarps, 0);
+    if (form == 2)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, trace_batch_cluster_kernel<false>, 32 * kHalfWarps, 0);
     if (e != cudaSuccess || v < 1) {
       cudaGetLastError();
       v = form == 1 ? 1 : 2;
@@ -825,13 +833,19 @@ int trace_batch_grid(int sm_count, int form) {
   return sm_count * per_sm[form];
 }
 
-cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int form, int grid, cudaStream_t st) {
-  BatchMeta* m = const_cast<BatchMeta*>(meta);
+template <bool FAR>
+static void launch_batch_form(BatchMeta* m, int form, int grid, cudaStream_t st) {
   switch (form) {
-    case 1: trace_batch8_kernel<<<grid, 32 * kTraceWarps, 0, st>>>(m); break;
-    case 2: trace_batch_cluster_kernel<<<grid, 32 * kHalfWarps, 0, st>>>(m); break;
-    default: trace_batch_kernel<<<grid, 32 * kHalfWarps, 0, st>>>(m); break;
+    case 1: trace_batch8_kernel<FAR><<<grid, 32 * kTraceWarps, 0, st>>>(m); break;
+    case 2: trace_batch_cluster_kernel<FAR><<<grid, 32 * kHalfWarps, 0, st>>>(m); break;
+    default: trace_batch_kernel<FAR><<<grid, 32 * kHalfWarps, 0, st>>>(m); break;
   }
+}
+
+cudaError_t launch_trace_batch_meta(const BatchMeta* meta, int form, int grid, bool far, cudaStream_t st) {
+  BatchMeta* m = const_cast<BatchMeta*>(meta);
+  if (far) launch_batch_form<true>(m, form, grid, st);
+  else launch_batch_form<false>(m, form, grid, st);
   return cudaGetLastError();
 }
 

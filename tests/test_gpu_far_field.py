@@ -108,3 +108,30 @@ def test_far_field_edge_grids_match_oracle(sim, nx, ny, s, nsub, k):
     assert err <= tol, (err, floor)
     if nsub == 0:
         assert np.array_equal(gpu_image(sim, system, 3.0), gpu_image(sim, system))
+
+
+def test_far_field_batched_launch_equals_single_calls(sim):
+    # the batched launch (n_sys > 1) runs the same FAR units: each system's image is bitwise its
+    # single-system image, for every batch schedule; and the mode reaches the batch graph
+    # (re-captured when the setting changes)
+    from paper_2606_01547_gb300 import lenssim
+    systems = [W.substructure_system(80 + i, n_sub=n, nx=nx, s=s, k=k)
+               for i, (n, nx, s, k) in enumerate([(1500, 48, 3, 7), (400, 30, 2, 5), (0, 20, 1, 3), (2500, 64, 1, 9)])]
+    singles = [gpu_image(sim, y, 3.0) for y in systems]
+    exact_batch = [o.cpu().numpy() for o in sim.image(systems)]
+    try:
+        for form in range(len(lenssim.BATCH_FORMS)):
+            for order in range(len(lenssim.BATCH_ORDERS)):
+                sim.set_batch_schedule(form, order)
+                sim.set_far_field(3.0)
+                outs = sim.image(systems)
+                torch.cuda.synchronize()
+                sim.set_far_field(0.0)
+                for y, o, ref in zip(systems, outs, singles):
+                    assert np.array_equal(o.cpu().numpy(), ref), (lenssim.BATCH_FORMS[form], y.grid.nx)
+    finally:
+        sim.set_batch_schedule(0, 0)
+        sim.set_far_field(0.0)
+    after = [o.cpu().numpy() for o in sim.image(systems)]
+    assert all(np.array_equal(a, b) for a, b in zip(after, exact_batch))
+    assert not np.array_equal(exact_batch[0], singles[0])
