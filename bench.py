@@ -910,17 +910,20 @@ def fitting_extra(sim, W, dev):
 
 
 def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_sets: int = 2,
-                  warmup_requests: int = 6000):
+                  warmup_requests: int = 6000, settle_s: float = 3.0):
     """Serving: open-loop Poisson arrivals at each rate for `seconds`, drawn from a pool of
     `pool_size` pre-generated requests of the serving mix (70 % image / 30 % likelihood +
     gradient, grids 64..256, subhalos 0..20,000, PSF 5..31) that is cycled.  One server serves
     every rate; its PSFs are registered up front, as a deployment would, and an untimed warm-up
     (the whole pool submitted back to back) lets its slots size their workspaces and capture
-    their batch graphs before the first measured rate, whose statistics are then reset (a
-    warm-up of half the pool left the first rate to meet the other half's largest requests, and
-    a workspace growth inside it held the client up by 85 ms).  Each pool entry has `out_sets` sets of output buffers used in turn, so a
-    buffer set is reused only pool_size * out_sets arrivals later, after its previous request
-    finished (a reuse that had to wait for it is counted in `blocked_reuses`); a submit refused
+    their batch graphs (a warm-up of half the pool left the first rate to meet the other half's
+    largest requests, and a workspace growth inside it held the client up by 85 ms); an
+    unmeasured open-loop window of `settle_s` at the first rate follows (the first window after
+    the warm-up saw a one-time 58 ms overshoot of the client's own sleep, in no later window),
+    and each rate's statistics are reset before it starts.  Each pool entry has `out_sets` sets
+    of output buffers used in turn, so a buffer set is reused only pool_size * out_sets arrivals
+    later, after its previous request finished (a reuse that had to wait for it is counted in
+    `blocked_reuses`); a submit refused
     with LENS_ERR_BUSY (more than max_inflight = 4096 requests admitted) counts as rejected.
     p50/p99 are the server's own submit-to-result latencies of the admitted requests.  The image
     requests of the pool are then run one by one through lens_sim_image with a synchronisation
@@ -965,6 +968,18 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
     for t in warm:
         srv.wait(t, 600000)
     t_warm = time.perf_counter() - t0
+    if settle_s > 0 and rates:
+        rng = np.random.default_rng(12345)
+        arr = np.cumsum(rng.exponential(1.0 / rates[0], int(rates[0] * settle_s * 1.2) + 16))
+        ts0 = time.perf_counter()
+        settle = []
+        for i, ta in enumerate(arr[arr < settle_s]):
+            delay = ta - (time.perf_counter() - ts0)
+            if delay > 0:
+                time.sleep(delay)
+            settle.append(submit(srv, i % len(pool), 0))
+        for t in settle:
+            srv.wait(t, 600000)
     out = []
     for rate in rates:
         srv.reset_stats()
@@ -1031,6 +1046,7 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
     plain = len(imgs) / (time.perf_counter() - t1)
     sim.close()
     return {"rates": out, "pool": pool_size, "warmup_requests": n_warm, "warmup_seconds": t_warm,
+            "settle_seconds": settle_s,
             "plain_images_per_s": plain, "plain_images": len(imgs),
             "mix": "70% image / 30% likelihood+gradient, grids 64..256 (even), s = 1, subhalos log-uniform "
                    "0..20000, PSF 5..31"}
