@@ -137,14 +137,24 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
   y = grid_coord(sys.y0, i, sys.ny, a, g.s, sys.dpix);
 }
 
+// Sample layout of a lane at s = 3, where its 9 samples are its pixel's 3 x 3 sub-grid (sample
+// k = 3a + b, row a, column b): packed pairs {(0,0),(0,1)}, {(1,0),(1,1)}, {(2,0),(2,1)},
+// {(0,2),(1,2)} and the scalar sample (2,2).  The first three pairs share their columns, so one
+// dx per column serves them, and the scalar sample's dx and dy are halves of pairs 3 and 2.
+__host__ __device__ constexpr int s3_pair_of(int k) { return k == 8 ? -1 : (k % 3 == 2 ? 3 : k / 3); }
+__host__ __device__ constexpr int s3_half_of(int k) { return k % 3 == 2 ? k / 3 : k % 3; }
+__host__ __device__ constexpr int s3_k_of(int i, int e) { return i < 3 ? 3 * i + e : 2 + 3 * e; }
+
 // Partial subhalo deflections of one unit: warp w of this CTA sums slice (slice0 + w) of the
 // kTraceWarps-way split of the subhalo list and writes its 288 partials to wa[area0 + w].part.
 //
 // A lane's first 2 kPackedPairs samples run as packed pairs (FP32x2 instructions, two samples
 // per issue slot), the rest as scalars; the two kinds run on different FP32 pipes.  The
 // packed operations are element-wise the same IEEE operations as the scalar ones, so every
-// sample's deflection is the same whichever kind it is.
-template <int NWC, bool FAR = false>
+// sample's deflection is the same whichever kind it is.  With S3 (s = 3 only) the samples take the
+// pixel layout above: each sample's arithmetic is unchanged, only shared terms are computed once,
+// so the partials are bitwise those of the generic layout.
+template <int NWC, bool FAR = false, bool S3 = false>
 __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGeom& g, int slice0,
                                               TraceSmem<NWC>& sm, int area0 = 0) {
   constexpr int kP = kPackedPairs;
@@ -160,7 +170,12 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
 
   float2 px2[kP], py2[kP], ax2[kP], ay2[kP];
   constexpr int kS = kUnitPts - 2 * kP;  // scalar samples
+  static_assert(!S3 || (kP == 4 && kS == 1), "the s = 3 layout pairs a pixel's 3 x 3 samples");
   float po_x[kS], po_y[kS], ao_x[kS], ao_y[kS];  // the scalar samples and their sums
+  // sample k's place: packed pair pair_of(k) (-1: scalar k - 2 kP), half half_of(k); and back
+  auto pair_of = [](int k) { return S3 ? s3_pair_of(k) : (k < 2 * kP ? k >> 1 : -1); };
+  auto half_of = [](int k) { return S3 ? s3_half_of(k) : (k & 1); };
+  auto k_of = [](int i, int e) { return S3 ? s3_k_of(i, e) : 2 * i + e; };
   float xmin = 3.0e38f, xmax = -3.0e38f, ymin = 3.0e38f, ymax = -3.0e38f;
 #pragma unroll
   for (int k = 0; k < kUnitPts; ++k) {
@@ -170,15 +185,16 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     sample_xy(sys, g, q, x, y);
     xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
     ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
-    if (k >= 2 * kP) {
+    const int pr = pair_of(k);
+    if (pr < 0) {
       po_x[k - 2 * kP] = x;
       po_y[k - 2 * kP] = y;
-    } else if (k & 1) {
-      px2[k >> 1].y = x;
-      py2[k >> 1].y = y;
+    } else if (half_of(k)) {
+      px2[pr].y = x;
+      py2[pr].y = y;
     } else {
-      px2[k >> 1].x = x;
-      py2[k >> 1].x = y;
+      px2[pr].x = x;
+      py2[pr].x = y;
     }
   }
 #pragma unroll
@@ -225,19 +241,57 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     ax = __ffma2_rn(gg, dx, ax);
     ay = __ffma2_rn(gg, dy, ay);
   };
-  auto far_samples = [&](const float4* t, auto Kc) {
+  // offsets of the lane's samples from record t's centre: packed pairs' dx, dy, dy^2, and the
+  // scalar samples' (dx = x - cx, dy = y - cy, each computed once per distinct value)
+  auto deltas = [&](const float4* t, float2* dx, float2* dy, float2* dy2, float* sdx, float* sdy, float* sdy2) {
+    const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
+    if constexpr (S3) {
+      const float2 dxa = __fadd2_rn(px2[0], ncx);  // columns 0, 1 (pairs 0-2 hold the same x)
+      const float2 dxc = __fadd2_rn(px2[3], ncx);  // column 2, duplicated
+      dx[0] = dxa; dx[1] = dxa; dx[2] = dxa; dx[3] = dxc;
 #pragma unroll
-    for (int i = 0; i < kP; ++i) packed_pair(t, Kc, px2[i], py2[i], ax2[i], ay2[i]);
+      for (int i = 0; i < kP; ++i) {
+        dy[i] = __fadd2_rn(py2[i], ncy);
+        dy2[i] = __fmul2_rn(dy[i], dy[i]);
+      }
+      sdx[0] = dxc.x;     // sample (2, 2): column 2
+      sdy[0] = dy[2].x;   // row 2
+      sdy2[0] = dy2[2].x;
+    } else {
+#pragma unroll
+      for (int i = 0; i < kP; ++i) {
+        dx[i] = __fadd2_rn(px2[i], ncx);
+        dy[i] = __fadd2_rn(py2[i], ncy);
+        dy2[i] = __fmul2_rn(dy[i], dy[i]);
+      }
+#pragma unroll
+      for (int j = 0; j < kS; ++j) {
+        sdx[j] = po_x[j] + t[0].x;
+        sdy[j] = po_y[j] + t[0].z;
+        sdy2[j] = sdy[j] * sdy[j];
+      }
+    }
   };
-  auto far_scalar = [&](const float4* t, auto Kc) {  // the scalar samples
+  // far-field series truncated after d_K for record t, every sample of the lane
+  auto far_all = [&](const float4* t, auto Kc) {
     constexpr int K = decltype(Kc)::value;
+    float2 dx[kP], dy[kP], dy2[kP];
+    float sdx[kS], sdy[kS], sdy2[kS];
+    deltas(t, dx, dy, dy2, sdx, sdy, sdy2);
 #pragma unroll
-    for (int i = 0; i < kS; ++i) {
-      const float dx = po_x[i] + t[0].x, dy = po_y[i] + t[0].z;
-      const float u = rsqrt_ftz(fmaf(dx, dx, dy * dy));
+    for (int i = 0; i < kP; ++i) {
+      const float2 r2 = __ffma2_rn(dx[i], dx[i], dy2[i]);
+      const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
+      const float2 gg = tnfw_series2_k<K>(u, __fmul2_rn(u, u), t);
+      ax2[i] = __ffma2_rn(gg, dx[i], ax2[i]);
+      ay2[i] = __ffma2_rn(gg, dy[i], ay2[i]);
+    }
+#pragma unroll
+    for (int j = 0; j < kS; ++j) {
+      const float u = rsqrt_ftz(fmaf(sdx[j], sdx[j], sdy2[j]));
       const float gg = tnfw_series_k<K>(u, u * u, t);
-      ao_x[i] = fmaf(gg, dx, ao_x[i]);
-      ao_y[i] = fmaf(gg, dy, ao_y[i]);
+      ao_x[j] = fmaf(gg, sdx[j], ao_x[j]);
+      ao_y[j] = fmaf(gg, sdy[j], ao_y[j]);
     }
   };
   auto load_far = [&](int q, float4* t) {
@@ -255,31 +309,36 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       const int2 qq = *reinterpret_cast<const int2*>(&area.list[q]);
       load_far(qq.x, ta);
       load_far(qq.y, tb);
-      far_samples(ta, Kc);
-      far_scalar(ta, Kc);
-      far_samples(tb, Kc);
-      far_scalar(tb, Kc);
+      far_all(ta, Kc);
+      far_all(tb, Kc);
     }
     if (q < e) {
       float4 ta[5];
       load_far(area.list[q], ta);
-      far_samples(ta, Kc);
-      far_scalar(ta, Kc);
+      far_all(ta, Kc);
     }
   };
   // sample k's coordinates (k static) and its accumulators
   auto sample_at = [&](int k, float& x, float& y) {
-    if (k >= 2 * kP) { x = po_x[k - 2 * kP]; y = po_y[k - 2 * kP]; }
-    else if (k & 1) { x = px2[k >> 1].y; y = py2[k >> 1].y; }
-    else { x = px2[k >> 1].x; y = py2[k >> 1].x; }
+    if constexpr (S3) {  // column b from pair 0 or 3, row a from pairs 0-2 (only those stay live)
+      const int a = k / 3, b = k % 3;
+      x = b == 2 ? px2[3].x : (b == 0 ? px2[0].x : px2[0].y);
+      y = py2[a].x;
+      return;
+    }
+    const int pr = pair_of(k);
+    if (pr < 0) { x = po_x[k - 2 * kP]; y = po_y[k - 2 * kP]; }
+    else if (half_of(k)) { x = px2[pr].y; y = py2[pr].y; }
+    else { x = px2[pr].x; y = py2[pr].x; }
   };
   auto accumulate_at = [&](int k, float g, float dx, float dy) {
-    if (k >= 2 * kP) {
+    const int pr = pair_of(k);
+    if (pr < 0) {
       ao_x[k - 2 * kP] = fmaf(g, dx, ao_x[k - 2 * kP]);
       ao_y[k - 2 * kP] = fmaf(g, dy, ao_y[k - 2 * kP]);
     }
-    else if (k & 1) { ax2[k >> 1].y = fmaf(g, dx, ax2[k >> 1].y); ay2[k >> 1].y = fmaf(g, dy, ay2[k >> 1].y); }
-    else { ax2[k >> 1].x = fmaf(g, dx, ax2[k >> 1].x); ay2[k >> 1].x = fmaf(g, dy, ay2[k >> 1].x); }
+    else if (half_of(k)) { ax2[pr].y = fmaf(g, dx, ax2[pr].y); ay2[pr].y = fmaf(g, dy, ay2[pr].y); }
+    else { ax2[pr].x = fmaf(g, dx, ax2[pr].x); ay2[pr].x = fmaf(g, dy, ay2[pr].x); }
   };
   // The closed forms of a marked subhalo's samples inside r_in (bit k of `inner`), spread over
   // the whole warp: the samples of a few lanes' pixels would otherwise run them one sample
@@ -345,33 +404,33 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   // (packed, branch-free), each sample then keeps the form of its distance; samples inside
   // r_in add nothing here and take the closed form through the queue
   auto near_pairs = [&](const float4* t, const float4* m) {
-    const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
     const float r_far2 = t[1].x, r_in2 = t[6].z;
     auto pick = [&](float r2, float gs, float gm) { return r2 >= r_far2 ? gs : (r2 >= r_in2 ? gm : 0.f); };
     unsigned inner = 0u;
+    float2 dx[kP], dy[kP], dy2[kP];
+    float sdx[kS], sdy[kS], sdy2[kS];
+    deltas(t, dx, dy, dy2, sdx, sdy, sdy2);
 #pragma unroll
     for (int i = 0; i < kP; ++i) {
-      const float2 dx = __fadd2_rn(px2[i], ncx), dy = __fadd2_rn(py2[i], ncy);
-      const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+      const float2 r2 = __ffma2_rn(dx[i], dx[i], dy2[i]);
       const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
       const float2 u2 = __fmul2_rn(u, u);
       const float2 gs = tnfw_series2_u(u, u2, t);
       const float2 gm = tnfw_mid2_u(u, u2, t, m);
       const float2 gg = make_float2(pick(r2.x, gs.x, gm.x), pick(r2.y, gs.y, gm.y));
-      inner |= (r2.x < r_in2 ? 1u : 0u) << (2 * i);
-      inner |= (r2.y < r_in2 ? 1u : 0u) << (2 * i + 1);
-      ax2[i] = __ffma2_rn(gg, dx, ax2[i]);
-      ay2[i] = __ffma2_rn(gg, dy, ay2[i]);
+      inner |= (r2.x < r_in2 ? 1u : 0u) << k_of(i, 0);
+      inner |= (r2.y < r_in2 ? 1u : 0u) << k_of(i, 1);
+      ax2[i] = __ffma2_rn(gg, dx[i], ax2[i]);
+      ay2[i] = __ffma2_rn(gg, dy[i], ay2[i]);
     }
 #pragma unroll
-    for (int i = 0; i < kS; ++i) {
-      const float dx = po_x[i] + t[0].x, dy = po_y[i] + t[0].z;
-      const float r2 = fmaf(dx, dx, dy * dy);
+    for (int j = 0; j < kS; ++j) {
+      const float r2 = fmaf(sdx[j], sdx[j], sdy2[j]);
       const float u = rsqrt_ftz(r2), u2 = u * u;
       const float gg = pick(r2, tnfw_series_u(u, u2, t), tnfw_mid_u(u, u2, t, m));
-      inner |= (r2 < r_in2 ? 1u : 0u) << (2 * kP + i);
-      ao_x[i] = fmaf(gg, dx, ao_x[i]);
-      ao_y[i] = fmaf(gg, dy, ao_y[i]);
+      inner |= (r2 < r_in2 ? 1u : 0u) << (2 * kP + j);
+      ao_x[j] = fmaf(gg, sdx[j], ao_x[j]);
+      ao_y[j] = fmaf(gg, sdy[j], ao_y[j]);
     }
     if (__any_sync(0xffffffffu, inner != 0u)) near_inner(t, inner);
   };
@@ -466,8 +525,8 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   // the warp's staged records are dead from here on: its partials take their place
 #pragma unroll
   for (int i = 0; i < kP; ++i) {
-    area.part[2 * i][lane] = make_float2(ax2[i].x, ay2[i].x);
-    area.part[2 * i + 1][lane] = make_float2(ax2[i].y, ay2[i].y);
+    area.part[k_of(i, 0)][lane] = make_float2(ax2[i].x, ay2[i].x);
+    area.part[k_of(i, 1)][lane] = make_float2(ax2[i].y, ay2[i].y);
   }
 #pragma unroll
   for (int i = 0; i < kS; ++i) area.part[2 * kP + i][lane] = make_float2(ao_x[i], ao_y[i]);
@@ -573,10 +632,10 @@ __device__ __forceinline__ float2 slice_node(const TraceSmem<NW>& sm, int w, int
 }
 
 // One unit of one system by one CTA of kTraceWarps warps; ends with a CTA barrier.
-template <bool FAR = false>
+template <bool FAR = false, bool S3 = false>
 __device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceSmem<kTraceWarps>& sm) {
   const UnitGeom g = unit_geom(sys, blk);
-  unit_partials<kTraceWarps, FAR>(sys, g, 0, sm);
+  unit_partials<kTraceWarps, FAR, S3>(sys, g, 0, sm);
   __syncthreads();
   if constexpr (FAR) unit_sum_nodes(sm.nodes, 32 * kTraceWarps, [&](int sl, int n) { return slice_node(sm, sl, n); });
   unit_finalize<FAR>(sys, g, sm.I, 32 * kTraceWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; },
@@ -586,10 +645,10 @@ __device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceS
   __syncthreads();
 }
 
-template <int MINB, bool FAR = false>
+template <int MINB, bool FAR = false, bool S3 = false>
 __global__ void __launch_bounds__(32 * kTraceWarps, MINB) trace_image_kernel(const __grid_constant__ DevSystem sys) {
   __shared__ TraceSmem<kTraceWarps> sm;
-  trace_unit<FAR>(sys, blockIdx.x, sm);
+  trace_unit<FAR, S3>(sys, blockIdx.x, sm);
 }
 
 // Subhalo deflection field of a grid (the likelihood's fixed field): the units, slices and
@@ -624,12 +683,12 @@ __global__ void __launch_bounds__(32 * kTraceWarps, 2) subhalo_field_kernel(cons
 // slices w and w + 4) into the same per-slice areas, then reduces them in slice order like the
 // one-CTA form, so its images are bitwise the same; the smaller CTA fits three per SM.
 constexpr int kHalfWarps = kTraceWarps / 2;
-template <bool FAR = false>
+template <bool FAR = false, bool S3 = false>
 __device__ __forceinline__ void trace_unit_2pass(const DevSystem& sys, int blk, TraceSmem<kTraceWarps>& sm) {
   const UnitGeom g = unit_geom(sys, blk);
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass)
-    unit_partials<kTraceWarps, FAR>(sys, g, pass * kHalfWarps, sm, pass * kHalfWarps);
+    unit_partials<kTraceWarps, FAR, S3>(sys, g, pass * kHalfWarps, sm, pass * kHalfWarps);
   __syncthreads();
   if constexpr (FAR) unit_sum_nodes(sm.nodes, 32 * kHalfWarps, [&](int sl, int n) { return slice_node(sm, sl, n); });
   unit_finalize<FAR>(sys, g, sm.I, 32 * kHalfWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; },
@@ -639,10 +698,10 @@ __device__ __forceinline__ void trace_unit_2pass(const DevSystem& sys, int blk, 
   __syncthreads();
 }
 
-template <bool FAR = false>
+template <bool FAR = false, bool S3 = false>
 __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_image_2pass_kernel(const __grid_constant__ DevSystem sys) {
   __shared__ TraceSmem<kTraceWarps> sm;
-  trace_unit_2pass<FAR>(sys, blockIdx.x, sm);
+  trace_unit_2pass<FAR, S3>(sys, blockIdx.x, sm);
 }
 
 // Cluster form: CL CTAs of kTraceWarps/CL warps share one unit (register budget for 16 warps
@@ -650,7 +709,7 @@ __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_image_2pass_kernel(c
 // [r*NWC, (r+1)*NWC) of the same split; the leader reads every CTA's partials through
 // distributed shared memory in slice order, so the image is bitwise that of the one-CTA form,
 // while the finer CTAs balance the tail of the grid across the SMs.
-template <int CL, bool FAR = false>
+template <int CL, bool FAR = false, bool S3 = false>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(32 * (kTraceWarps / CL), 4 * CL / 2)
 trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
   constexpr int NWC = kTraceWarps / CL;
@@ -658,7 +717,7 @@ trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const UnitGeom g = unit_geom(sys, blockIdx.x / CL);
-  unit_partials<NWC, FAR>(sys, g, rank * NWC, sm);
+  unit_partials<NWC, FAR, S3>(sys, g, rank * NWC, sm);
   cluster.sync();
   if (rank == 0) {
     const TraceSmem<NWC>* peers[CL];
@@ -779,21 +838,29 @@ const char* trace_variant_name(int v) {
   }
 }
 
-template <bool FAR>
+template <bool FAR, bool S3>
 static void launch_trace_form(const DevSystem& sys, int variant, int units, cudaStream_t st) {
   switch (variant) {
-    case 1: trace_image_2pass_kernel<FAR><<<units, 32 * kHalfWarps, 0, st>>>(sys); break;
-    case 2: trace_cluster_kernel<2, FAR><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
-    case 3: trace_cluster_kernel<4, FAR><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
-    case 4: trace_cluster_kernel<8, FAR><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
-    default: trace_image_kernel<2, FAR><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
+    case 1: trace_image_2pass_kernel<FAR, S3><<<units, 32 * kHalfWarps, 0, st>>>(sys); break;
+    case 2: trace_cluster_kernel<2, FAR, S3><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
+    case 3: trace_cluster_kernel<4, FAR, S3><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
+    case 4: trace_cluster_kernel<8, FAR, S3><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
+    default: trace_image_kernel<2, FAR, S3><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
   }
 }
 
+// Single-system launches at s = 3 take the pixel-layout instantiation (bitwise the same images;
+// the batched launch mixes supersampling factors and keeps the generic layout).
 cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t st) {
   const int units = unit_count(sys.nx, sys.ny, sys.s);
-  if (sys.far_kappa > 0.f) launch_trace_form<true>(sys, variant, units, st);
-  else launch_trace_form<false>(sys, variant, units, st);
+  const bool far = sys.far_kappa > 0.f, s3 = sys.s == 3;
+  if (far) {
+    if (s3) launch_trace_form<true, true>(sys, variant, units, st);
+    else launch_trace_form<true, false>(sys, variant, units, st);
+  } else {
+    if (s3) launch_trace_form<false, true>(sys, variant, units, st);
+    else launch_trace_form<false, false>(sys, variant, units, st);
+  }
   return cudaGetLastError();
 }
 
