@@ -49,7 +49,8 @@ N_SYSTEMS = 8            # distinct seeded systems cycled through the steps
 # 4 Rs are not counted).  One MUFU per pair in every form.
 FLOPS_BY_FORM = {"near": 46, "series6": 21, "series4": 17, "series3": 15}
 FLOPS_PER_PAIR = 21  # the 6-term series formula: the previous single-form ledger, reported beside
-KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh",
+KERNEL_SOURCES = ("paper_2606_01547_gb300/csrc/trace.cu", "paper_2606_01547_gb300/csrc/trace_unit.cuh",
+                  "paper_2606_01547_gb300/csrc/trace_far.cu", "paper_2606_01547_gb300/csrc/lens_device.cuh",
                   "paper_2606_01547_gb300/csrc/kernels.h")
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "trace_kernel_substructure_200x200_traffic.txt")
 
