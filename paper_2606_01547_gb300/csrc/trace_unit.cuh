@@ -123,12 +123,13 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
 }
 
 // Sample layout of a lane at s = 3, where its 9 samples are its pixel's 3 x 3 sub-grid (sample
-// k = 3a + b, row a, column b): packed pairs {(0,0),(0,1)}, {(1,0),(1,1)}, {(2,0),(2,1)},
-// {(0,2),(1,2)} and the scalar sample (2,2).  The first three pairs share their columns, so one
-// dx per column serves them, and the scalar sample's dx and dy are halves of pairs 3 and 2.
-__host__ __device__ constexpr int s3_pair_of(int k) { return k == 8 ? -1 : (k % 3 == 2 ? 3 : k / 3); }
-__host__ __device__ constexpr int s3_half_of(int k) { return k % 3 == 2 ? k / 3 : k % 3; }
-__host__ __device__ constexpr int s3_k_of(int i, int e) { return i < 3 ? 3 * i + e : 2 + 3 * e; }
+// k = 3a + b, row a, column b): packed pairs {(0,b),(1,b)} for the columns b = 0, 1, 2, then
+// {(2,0),(2,1)}, and the scalar sample (2,2).  The three column pairs share their rows, so one
+// (dy, dy^2) pair serves them, each pair's dx is one column's, and the scalar sample's dx and
+// dy are halves of the column-2 and row-2 values.
+__host__ __device__ constexpr int s3_pair_of(int k) { return k / 3 < 2 ? k % 3 : (k % 3 < 2 ? 3 : -1); }
+__host__ __device__ constexpr int s3_half_of(int k) { return k / 3 < 2 ? k / 3 : k % 3; }
+__host__ __device__ constexpr int s3_k_of(int i, int e) { return i < 3 ? 3 * e + i : 6 + e; }
 
 // Partial subhalo deflections of one unit: warp w of this CTA sums slice (slice0 + w) of the
 // kTraceWarps-way split of the subhalo list and writes its 288 partials to wa[area0 + w].part.
@@ -231,17 +232,16 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   auto deltas = [&](const float4* t, float2* dx, float2* dy, float2* dy2, float* sdx, float* sdy, float* sdy2) {
     const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
     if constexpr (S3) {
-      const float2 dxa = __fadd2_rn(px2[0], ncx);  // columns 0, 1 (pairs 0-2 hold the same x)
-      const float2 dxc = __fadd2_rn(px2[3], ncx);  // column 2, duplicated
-      dx[0] = dxa; dx[1] = dxa; dx[2] = dxa; dx[3] = dxc;
 #pragma unroll
-      for (int i = 0; i < kP; ++i) {
-        dy[i] = __fadd2_rn(py2[i], ncy);
-        dy2[i] = __fmul2_rn(dy[i], dy[i]);
-      }
-      sdx[0] = dxc.x;     // sample (2, 2): column 2
-      sdy[0] = dy[2].x;   // row 2
-      sdy2[0] = dy2[2].x;
+      for (int i = 0; i < kP; ++i) dx[i] = __fadd2_rn(px2[i], ncx);  // columns 0, 1, 2 duplicated; (0, 1)
+      const float2 dya = __fadd2_rn(py2[0], ncy);  // rows 0, 1 (the column pairs hold the same y)
+      const float2 dyc = __fadd2_rn(py2[3], ncy);  // row 2, duplicated
+      const float2 dy2a = __fmul2_rn(dya, dya), dy2c = __fmul2_rn(dyc, dyc);
+      dy[0] = dya; dy[1] = dya; dy[2] = dya; dy[3] = dyc;
+      dy2[0] = dy2a; dy2[1] = dy2a; dy2[2] = dy2a; dy2[3] = dy2c;
+      sdx[0] = dx[2].x;   // sample (2, 2): column 2
+      sdy[0] = dyc.x;     // row 2
+      sdy2[0] = dy2c.x;
     } else {
 #pragma unroll
       for (int i = 0; i < kP; ++i) {
@@ -305,10 +305,10 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   };
   // sample k's coordinates (k static) and its accumulators
   auto sample_at = [&](int k, float& x, float& y) {
-    if constexpr (S3) {  // column b from pair 0 or 3, row a from pairs 0-2 (only those stay live)
+    if constexpr (S3) {  // column b from the column pairs, row a from pair 0 or 3 (those stay live)
       const int a = k / 3, b = k % 3;
-      x = b == 2 ? px2[3].x : (b == 0 ? px2[0].x : px2[0].y);
-      y = py2[a].x;
+      x = px2[b].x;
+      y = a == 2 ? py2[3].x : (a == 0 ? py2[0].x : py2[0].y);
       return;
     }
     const int pr = pair_of(k);
