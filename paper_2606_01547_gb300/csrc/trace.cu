@@ -69,7 +69,7 @@ const char* trace_variant_name(int v) {
 }
 
 // Single-system launches at s = 3 take the pixel-layout instantiation (bitwise the same images;
-// the batched launch mixes supersampling factors and keeps the generic layout).
+// the batched launch's persistent kernels choose the layout per unit from its system's s).
 cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t st) {
   const int units = unit_count(sys.nx, sys.ny, sys.s);
   const bool far = sys.far_kappa > 0.f, s3 = sys.s == 3;

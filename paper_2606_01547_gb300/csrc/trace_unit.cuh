@@ -724,7 +724,9 @@ __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_batch_kernel(BatchMe
     __syncthreads();
     if (u >= total) return;
     const int i = batch_system_of(unit_prefix, n_sys, u);
-    trace_unit_2pass<FAR>(systems[i], u - unit_prefix[i], sm);
+    const DevSystem& sys = systems[i];
+    if (sys.s == 3) trace_unit_2pass<FAR, true>(sys, u - unit_prefix[i], sm);
+    else trace_unit_2pass<FAR, false>(sys, u - unit_prefix[i], sm);
   }
 }
 
@@ -743,7 +745,9 @@ __global__ void __launch_bounds__(32 * kTraceWarps, 2) trace_batch8_kernel(Batch
     __syncthreads();
     if (u >= total) return;
     const int i = batch_system_of(unit_prefix, n_sys, u);
-    trace_unit<FAR>(systems[i], u - unit_prefix[i], sm);
+    const DevSystem& sys = systems[i];
+    if (sys.s == 3) trace_unit<FAR, true>(sys, u - unit_prefix[i], sm);
+    else trace_unit<FAR, false>(sys, u - unit_prefix[i], sm);
   }
 }
 
@@ -769,7 +773,8 @@ trace_batch_cluster_kernel(BatchMeta* __restrict__ meta) {
     const int i = batch_system_of(unit_prefix, n_sys, u);
     const DevSystem& sys = systems[i];
     const UnitGeom g = unit_geom(sys, u - unit_prefix[i]);
-    unit_partials<NWC, FAR>(sys, g, rank * NWC, sm);
+    if (sys.s == 3) unit_partials<NWC, FAR, true>(sys, g, rank * NWC, sm);
+    else unit_partials<NWC, FAR, false>(sys, g, rank * NWC, sm);
     cluster.sync();
     if (rank == 0) {
       const TraceSmem<NWC>* peers[2] = {cluster.map_shared_rank(&sm, 0), cluster.map_shared_rank(&sm, 1)};
