@@ -204,7 +204,8 @@ int lens_sim_set_variant(lens_sim* sim, int variant);
  * FP32 rounding of the interpolation (Lebesgue constant of the 8 x 8 grid below 6).
  * kappa = 0 restores the exact sum; 0 < kappa < 3 or a non-finite kappa is LENS_ERR_INVALID_ARG.
  * It applies to every lens_sim_image call of the handle (single systems and the batched launch
- * of n_sys > 1 alike, each system's image the same either way) and to both autotuners.  Every
+ * of n_sys > 1 alike, each system's image the same either way under the same convolution, see
+ * lens_sim_set_conv_method) and to both autotuners.  Every
  * launch variant and batch schedule still gives bitwise-identical images.  Ray shooting
  * (lens_sim_deflection), the likelihood and its adjoint, the server and the no-alloc entry
  * point always use the exact sum. */
@@ -227,13 +228,15 @@ int lens_sim_autotune_batch(lens_sim* sim, const lens_system* systems, int n_sys
 
 /* PSF method of lens_sim_image (single system) and lens_sim_convolve.  LENS_CONV_DIRECT: tiled
  * direct convolution.  LENS_CONV_FFT: FFT convolution (the paper's method for large kernels):
- * radix-2 transforms on a grid padded to powers of two >= (n + (k-1)/2) in each direction,
- * at most 1024; larger images return LENS_ERR_UNSUPPORTED.  The kernel's spectrum is computed
- * once per (psf_id, padded size) and kept by the handle.  LENS_CONV_AUTO (the default): FFT
- * when k >= LENS_CONV_FFT_MIN_K and the padded size fits, else direct.  Both compute the same
- * convolution; they differ by FP32 rounding only (the FFT's is of order eps log2(M) of the
- * output scale, below 1e-5 relative L-inf).  The batched and
- * likelihood paths always use the direct form. */
+ * the kernel's central 7 x 7 core convolved directly plus its wings (the rest) by four-step
+ * FFTs of real rows on a grid padded to powers of two >= (n + (k-1)/2) in each direction, at
+ * most 1024; larger images return LENS_ERR_UNSUPPORTED.  The wings' spectrum is computed once
+ * per (psf_id, padded size) and kept by the handle.  LENS_CONV_AUTO (the default): FFT when
+ * k >= LENS_CONV_FFT_MIN_K and the padded size fits, else direct.  Both compute the same
+ * convolution; they differ by FP32 rounding only (the FFT's, carried by the wings alone, is of
+ * order eps log2(M) of their contribution, below 1e-5 relative L-inf).  The batched and
+ * likelihood paths always use the direct form, so a batched image equals its single-system
+ * image bitwise when that call convolves directly (always for k < LENS_CONV_FFT_MIN_K). */
 #define LENS_CONV_AUTO 0
 #define LENS_CONV_DIRECT 1
 #define LENS_CONV_FFT 2

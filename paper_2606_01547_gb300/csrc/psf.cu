@@ -12,26 +12,10 @@ constexpr int kConvRows = 8;
 // From this kernel size on (above the TMA kernel's k <= 31) the direct sum is taken by rows.
 constexpr int kConvRowSumMinK = 33;
 
-__global__ void __launch_bounds__(kConvT * kConvRows)
-conv_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int nx,
-            const float* __restrict__ K, int k, int flip) {
-  extern __shared__ float smem[];
-  const int tw = kConvT + k - 1;
-  float* sK = smem;              // k*k (oriented so that out = sum sK[a][b] T[r+a][c+b])
-  float* sT = smem + k * k;      // tw*tw input tile with halo
-  const int c = (k - 1) / 2;
-  const size_t img = (size_t)blockIdx.z * ny * nx;
-  const int i0 = blockIdx.y * kConvT, j0 = blockIdx.x * kConvT;
-  const int tid = threadIdx.y * kConvT + threadIdx.x;
-  const int nthr = kConvT * kConvRows;
-  for (int t = tid; t < k * k; t += nthr) sK[t] = flip ? K[k * k - 1 - t] : K[t];
-  for (int t = tid; t < tw * tw; t += nthr) {
-    const int r = t / tw, cc = t - r * tw;
-    const int gi = i0 - c + r, gj = j0 - c + cc;
-    sT[t] = (gi >= 0 && gi < ny && gj >= 0 && gj < nx) ? in[img + (size_t)gi * nx + gj] : 0.f;
-  }
-  __syncthreads();
-  float acc[kConvT / kConvRows];
+// The tile sum of one thread's kConvT / kConvRows outputs, shared by the single-image and the
+// batched kernels so that both sum in the same order (bitwise equal outputs).
+__device__ __forceinline__ void conv_tile_sum(const float* sK, const float* sT, int tw, int k,
+                                              float (&acc)[kConvT / kConvRows]) {
 #pragma unroll
   for (int q = 0; q < kConvT / kConvRows; ++q) acc[q] = 0.f;
   if (k < kConvRowSumMinK) {
@@ -66,6 +50,29 @@ conv_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int n
       for (int q = 0; q < kConvT / kConvRows; ++q) acc[q] += row[q];
     }
   }
+}
+
+__global__ void __launch_bounds__(kConvT * kConvRows)
+conv_kernel(const float* __restrict__ in, float* __restrict__ out, int ny, int nx,
+            const float* __restrict__ K, int k, int flip) {
+  extern __shared__ float smem[];
+  const int tw = kConvT + k - 1;
+  float* sK = smem;              // k*k (oriented so that out = sum sK[a][b] T[r+a][c+b])
+  float* sT = smem + k * k;      // tw*tw input tile with halo
+  const int c = (k - 1) / 2;
+  const size_t img = (size_t)blockIdx.z * ny * nx;
+  const int i0 = blockIdx.y * kConvT, j0 = blockIdx.x * kConvT;
+  const int tid = threadIdx.y * kConvT + threadIdx.x;
+  const int nthr = kConvT * kConvRows;
+  for (int t = tid; t < k * k; t += nthr) sK[t] = flip ? K[k * k - 1 - t] : K[t];
+  for (int t = tid; t < tw * tw; t += nthr) {
+    const int r = t / tw, cc = t - r * tw;
+    const int gi = i0 - c + r, gj = j0 - c + cc;
+    sT[t] = (gi >= 0 && gi < ny && gj >= 0 && gj < nx) ? in[img + (size_t)gi * nx + gj] : 0.f;
+  }
+  __syncthreads();
+  float acc[kConvT / kConvRows];
+  conv_tile_sum(sK, sT, tw, k, acc);
 #pragma unroll
   for (int q = 0; q < kConvT / kConvRows; ++q) {
     const int gi = i0 + threadIdx.y + q * kConvRows, gj = j0 + threadIdx.x;
@@ -136,15 +143,7 @@ conv_batch_kernel(BatchMeta* __restrict__ meta) {
     }
     __syncthreads();
     float acc[kConvT / kConvRows];
-#pragma unroll
-    for (int q = 0; q < kConvT / kConvRows; ++q) acc[q] = 0.f;
-    for (int a = 0; a < k; ++a)
-      for (int b = 0; b < k; ++b) {
-        const float kv = sK[a * k + b];
-#pragma unroll
-        for (int q = 0; q < kConvT / kConvRows; ++q)
-          acc[q] = fmaf(kv, sT[(threadIdx.y + q * kConvRows + a) * tw + threadIdx.x + b], acc[q]);
-      }
+    conv_tile_sum(sK, sT, tw, k, acc);
 #pragma unroll
     for (int q = 0; q < kConvT / kConvRows; ++q) {
       const int gi = i0 + threadIdx.y + q * kConvRows, gj = j0 + threadIdx.x;
