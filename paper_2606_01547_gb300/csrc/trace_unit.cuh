@@ -368,22 +368,41 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   };
   // far-field interpolation: a class of far subhalos at list positions [b, e), b even, summed
   // at the lane's two nodes
+  //
+  // A node pair is one subhalo's work against one packed pair of a sample subhalo's nine, so
+  // the node classes read each record in the compact form (-cx, -cy, d_0, d_2), (d_3 .. d_6)
+  // that staging left in the queue area (2 broadcast loads instead of 3-4) and evaluate the
+  // lane's two nodes, which share their x, as scalars on the light FMA pipe.
+  auto node_pair = [&](const float4* compact, int q, auto Kc) {
+    constexpr int K = decltype(Kc)::value;
+    const float4 c0 = compact[2 * q], c1 = compact[2 * q + 1];
+    const float d[7] = {c0.z, 0.f, c0.w, c1.x, c1.y, c1.z, c1.w};  // d_0, -, d_2 .. d_6
+    const float dx = pn_x.x + c0.x, dy0 = pn_y.x + c0.y, dy1 = pn_y.y + c0.y;
+    const float dx2 = dx * dx;
+    const float u0 = rsqrt_ftz(fmaf(dy0, dy0, dx2)), u1 = rsqrt_ftz(fmaf(dy1, dy1, dx2));
+    const float v0 = u0 * u0, v1 = u1 * u1;
+    float p0 = fmaf(d[K], u0, d[K - 1]), p1 = fmaf(d[K], u1, d[K - 1]);
+#pragma unroll
+    for (int k = K - 2; k >= 2; --k) {
+      p0 = fmaf(p0, u0, d[k]);
+      p1 = fmaf(p1, u1, d[k]);
+    }
+    const float g0 = fmaf(p0, v0, d[0]) * v0, g1 = fmaf(p1, v1, d[0]) * v1;
+    an_x.x = fmaf(g0, dx, an_x.x);
+    an_y.x = fmaf(g0, dy0, an_y.x);
+    an_x.y = fmaf(g1, dx, an_x.y);
+    an_y.y = fmaf(g1, dy1, an_y.y);
+  };
   auto node_class = [&](int b, int e, auto Kc) {
+    const float4* compact = reinterpret_cast<const float4*>(area.queue);
     int q = b;
 #pragma unroll 1
     for (; q + 1 < e; q += 2) {
-      float4 ta[5], tb[5];
       const int2 qq = *reinterpret_cast<const int2*>(&area.list[q]);
-      load_far(qq.x, ta);
-      load_far(qq.y, tb);
-      packed_pair(ta, Kc, pn_x, pn_y, an_x, an_y);
-      packed_pair(tb, Kc, pn_x, pn_y, an_x, an_y);
+      node_pair(compact, qq.x, Kc);
+      node_pair(compact, qq.y, Kc);
     }
-    if (q < e) {
-      float4 ta[5];
-      load_far(area.list[q], ta);
-      packed_pair(ta, Kc, pn_x, pn_y, an_x, an_y);
-    }
+    if (q < e) node_pair(compact, area.list[q], Kc);
   };
   // subhalos the bounding-box test marked: series and annulus polynomial for every sample
   // (packed, branch-free), each sample then keeps the form of its distance; samples inside
@@ -445,7 +464,14 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
       const float d2 = fmaf(ddx, ddx, ddy * ddy);
       near = d2 < st[1].x;
       tier = d2 >= st[5].y ? 2 : (d2 >= st[5].x ? 1 : 0);
-      if constexpr (FAR) interp = !near && d2 >= far_d2;  // marked subhalos always run at the samples
+      if constexpr (FAR) {
+        interp = !near && d2 >= far_d2;  // marked subhalos always run at the samples
+        if (interp) {  // the compact record of the node classes (queue area, free until the near field)
+          float4* compact = reinterpret_cast<float4*>(area.queue);
+          compact[2 * lane] = make_float4(st[0].x, st[0].z, st[2].x, st[2].z);
+          compact[2 * lane + 1] = make_float4(st[3].x, st[3].z, st[4].x, st[4].z);
+        }
+      }
       if (near) {
         area.marked[lane][0] = st[1];
         area.marked[lane][1] = st[6];
