@@ -36,11 +36,12 @@ __global__ void __launch_bounds__(32 * kTraceWarps, 2) subhalo_field_kernel(cons
                                                                             float2* __restrict__ out) {
   __shared__ TraceSmem<kTraceWarps> sm;
   const UnitGeom g = unit_geom(sys, blockIdx.x);
-  unit_partials<kTraceWarps>(sys, g, 0, sm);
+  if (block_layout(g.s)) unit_partials<kTraceWarps, false, true>(sys, g, 0, sm);
+  else unit_partials<kTraceWarps, false, false>(sys, g, 0, sm);
   __syncthreads();
   for (int idx = threadIdx.x; idx < 32 * kUnitPts; idx += 32 * kTraceWarps) {
     const int k = idx >> 5, l = idx & 31;
-    const int q = l * kUnitPts + k;
+    const int q = unit_sample_index(g, l, k);
     if (q >= g.nsamp) continue;
     const int p = q / g.s2, sub = q - p * g.s2;
     const int a = sub / g.s, b = sub - a * g.s;
@@ -68,13 +69,14 @@ const char* trace_variant_name(int v) {
   }
 }
 
-// Single-system launches at s = 3 take the pixel-layout instantiation (bitwise the same images;
-// the batched launch's persistent kernels choose the layout per unit from its system's s).
+// Every launch takes the block layout where the unit allows it (the finalisation maps samples by
+// block_layout(s), so the layout is a function of s alone; the batched launch's persistent
+// kernels choose it per unit).  Each sample's arithmetic is the same in both layouts.
 cudaError_t launch_trace_variant(const DevSystem& sys, int variant, cudaStream_t st) {
   const int units = unit_count(sys.nx, sys.ny, sys.s);
-  const bool far = sys.far_kappa > 0.f, s3 = sys.s == 3;
+  const bool far = sys.far_kappa > 0.f, blk = block_layout(sys.s);
   if (far) launch_trace_far(sys, variant, units, st);
-  else if (s3) launch_trace_form<false, true>(sys, variant, units, st);
+  else if (blk) launch_trace_form<false, true>(sys, variant, units, st);
   else launch_trace_form<false, false>(sys, variant, units, st);
   return cudaGetLastError();
 }

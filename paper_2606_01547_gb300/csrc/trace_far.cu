@@ -6,7 +6,7 @@
 namespace ls {
 
 void launch_trace_far(const DevSystem& sys, int variant, int units, cudaStream_t st) {
-  if (sys.s == 3) launch_trace_form<true, true>(sys, variant, units, st);
+  if (block_layout(sys.s)) launch_trace_form<true, true>(sys, variant, units, st);
   else launch_trace_form<true, false>(sys, variant, units, st);
 }
 

@@ -122,8 +122,21 @@ __device__ __forceinline__ void sample_xy(const DevSystem& sys, const UnitGeom& 
   y = grid_coord(sys.y0, i, sys.ny, a, g.s, sys.dpix);
 }
 
-// Sample layout of a lane at s = 3, where its 9 samples are its pixel's 3 x 3 sub-grid (sample
-// k = 3a + b, row a, column b): packed pairs {(0,b),(1,b)} for the columns b = 0, 1, 2, then
+// Block layout: at s = 1, 2, 3, 4 and 6 a unit is 24 x 12 samples, and lane l holds the 3 x 3
+// block of samples at sample columns 3 (l mod 8) + b and rows 3 (l div 8) + a (k = 3a + b; at
+// s = 3 the block is the lane's pixel, its 9 sub-samples).  unit_sample_index maps lane l's
+// sample k to the unit's sample index q (pixel q / s^2 of the unit's pixel block, sub-sample
+// q mod s^2) in either layout, so partials, finalisation and bin-down agree.
+__host__ __device__ constexpr bool block_layout(int s) { return s == 1 || s == 2 || s == 3 || s == 4 || s == 6; }
+
+__device__ __forceinline__ int unit_sample_index(const UnitGeom& g, int l, int k) {
+  if (!block_layout(g.s)) return l * kUnitPts + k;
+  const int sc = 3 * (l & 7) + k % 3, sr = 3 * (l >> 3) + k / 3;
+  const int pc = sc / g.s, pr = sr / g.s;
+  return (pr * g.bw + pc) * g.s2 + (sr - pr * g.s) * g.s + (sc - pc * g.s);
+}
+
+// In the block layout a lane's packed pairs are {(0,b),(1,b)} for the columns b = 0, 1, 2, then
 // {(2,0),(2,1)}, and the scalar sample (2,2).  The three column pairs share their rows, so one
 // (dy, dy^2) pair serves them, each pair's dx is one column's, and the scalar sample's dx and
 // dy are halves of the column-2 and row-2 values.
@@ -137,10 +150,10 @@ __host__ __device__ constexpr int s3_k_of(int i, int e) { return i < 3 ? 3 * e +
 // A lane's first 2 kPackedPairs samples run as packed pairs (FP32x2 instructions, two samples
 // per issue slot), the rest as scalars; the two kinds run on different FP32 pipes.  The
 // packed operations are element-wise the same IEEE operations as the scalar ones, so every
-// sample's deflection is the same whichever kind it is.  With S3 (s = 3 only) the samples take the
-// pixel layout above: each sample's arithmetic is unchanged, only shared terms are computed once,
-// so the partials are bitwise those of the generic layout.
-template <int NWC, bool FAR = false, bool S3 = false>
+// sample's deflection is the same whichever kind it is.  With BLK (block_layout(s) only) the
+// samples take the block layout above: each sample's arithmetic is unchanged, only shared terms
+// are computed once, so every sample's partial is bitwise that of the generic layout.
+template <int NWC, bool FAR = false, bool BLK = false>
 __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGeom& g, int slice0,
                                               TraceSmem<NWC>& sm, int area0 = 0) {
   constexpr int kP = kPackedPairs;
@@ -156,16 +169,16 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
 
   float2 px2[kP], py2[kP], ax2[kP], ay2[kP];
   constexpr int kS = kUnitPts - 2 * kP;  // scalar samples
-  static_assert(!S3 || (kP == 4 && kS == 1), "the s = 3 layout pairs a pixel's 3 x 3 samples");
+  static_assert(!BLK || (kP == 4 && kS == 1), "the block layout pairs a lane's 3 x 3 samples");
   float po_x[kS], po_y[kS], ao_x[kS], ao_y[kS];  // the scalar samples and their sums
   // sample k's place: packed pair pair_of(k) (-1: scalar k - 2 kP), half half_of(k); and back
-  auto pair_of = [](int k) { return S3 ? s3_pair_of(k) : (k < 2 * kP ? k >> 1 : -1); };
-  auto half_of = [](int k) { return S3 ? s3_half_of(k) : (k & 1); };
-  auto k_of = [](int i, int e) { return S3 ? s3_k_of(i, e) : 2 * i + e; };
+  auto pair_of = [](int k) { return BLK ? s3_pair_of(k) : (k < 2 * kP ? k >> 1 : -1); };
+  auto half_of = [](int k) { return BLK ? s3_half_of(k) : (k & 1); };
+  auto k_of = [](int i, int e) { return BLK ? s3_k_of(i, e) : 2 * i + e; };
   float xmin = 3.0e38f, xmax = -3.0e38f, ymin = 3.0e38f, ymax = -3.0e38f;
 #pragma unroll
   for (int k = 0; k < kUnitPts; ++k) {
-    int q = lane * kUnitPts + k;
+    int q = BLK ? unit_sample_index(g, lane, k) : lane * kUnitPts + k;
     if (q >= g.nsamp) q = 0;
     float x, y;
     sample_xy(sys, g, q, x, y);
@@ -231,7 +244,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   // scalar samples' (dx = x - cx, dy = y - cy, each computed once per distinct value)
   auto deltas = [&](const float4* t, float2* dx, float2* dy, float2* dy2, float* sdx, float* sdy, float* sdy2) {
     const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
-    if constexpr (S3) {
+    if constexpr (BLK) {
 #pragma unroll
       for (int i = 0; i < kP; ++i) dx[i] = __fadd2_rn(px2[i], ncx);  // columns 0, 1, 2 duplicated; (0, 1)
       const float2 dya = __fadd2_rn(py2[0], ncy);  // rows 0, 1 (the column pairs hold the same y)
@@ -305,7 +318,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   };
   // sample k's coordinates (k static) and its accumulators
   auto sample_at = [&](int k, float& x, float& y) {
-    if constexpr (S3) {  // column b from the column pairs, row a from pair 0 or 3 (those stay live)
+    if constexpr (BLK) {  // column b from the column pairs, row a from pair 0 or 3 (those stay live)
       const int a = k / 3, b = k % 3;
       x = px2[b].x;
       y = a == 2 ? py2[3].x : (a == 0 ? py2[0].x : py2[0].y);
@@ -582,7 +595,7 @@ __device__ __forceinline__ void unit_finalize(const DevSystem& sys, const UnitGe
   }
   for (int idx = threadIdx.x; idx < 32 * kUnitPts; idx += nthr) {
     const int k = idx >> 5, l = idx & 31;
-    const int q = l * kUnitPts + k;
+    const int q = unit_sample_index(g, l, k);
     if (q >= g.nsamp) continue;
     float sx = 0.f, sy = 0.f;
 #pragma unroll
@@ -643,10 +656,10 @@ __device__ __forceinline__ float2 slice_node(const TraceSmem<NW>& sm, int w, int
 }
 
 // One unit of one system by one CTA of kTraceWarps warps; ends with a CTA barrier.
-template <bool FAR = false, bool S3 = false>
+template <bool FAR = false, bool BLK = false>
 __device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceSmem<kTraceWarps>& sm) {
   const UnitGeom g = unit_geom(sys, blk);
-  unit_partials<kTraceWarps, FAR, S3>(sys, g, 0, sm);
+  unit_partials<kTraceWarps, FAR, BLK>(sys, g, 0, sm);
   __syncthreads();
   if constexpr (FAR) unit_sum_nodes(sm.nodes, 32 * kTraceWarps, [&](int sl, int n) { return slice_node(sm, sl, n); });
   unit_finalize<FAR>(sys, g, sm.I, 32 * kTraceWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; },
@@ -656,10 +669,10 @@ __device__ __forceinline__ void trace_unit(const DevSystem& sys, int blk, TraceS
   __syncthreads();
 }
 
-template <int MINB, bool FAR = false, bool S3 = false>
+template <int MINB, bool FAR = false, bool BLK = false>
 __global__ void __launch_bounds__(32 * kTraceWarps, MINB) trace_image_kernel(const __grid_constant__ DevSystem sys) {
   __shared__ TraceSmem<kTraceWarps> sm;
-  trace_unit<FAR, S3>(sys, blockIdx.x, sm);
+  trace_unit<FAR, BLK>(sys, blockIdx.x, sm);
 }
 
 
@@ -667,12 +680,12 @@ __global__ void __launch_bounds__(32 * kTraceWarps, MINB) trace_image_kernel(con
 // slices w and w + 4) into the same per-slice areas, then reduces them in slice order like the
 // one-CTA form, so its images are bitwise the same; the smaller CTA fits three per SM.
 constexpr int kHalfWarps = kTraceWarps / 2;
-template <bool FAR = false, bool S3 = false>
+template <bool FAR = false, bool BLK = false>
 __device__ __forceinline__ void trace_unit_2pass(const DevSystem& sys, int blk, TraceSmem<kTraceWarps>& sm) {
   const UnitGeom g = unit_geom(sys, blk);
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass)
-    unit_partials<kTraceWarps, FAR, S3>(sys, g, pass * kHalfWarps, sm, pass * kHalfWarps);
+    unit_partials<kTraceWarps, FAR, BLK>(sys, g, pass * kHalfWarps, sm, pass * kHalfWarps);
   __syncthreads();
   if constexpr (FAR) unit_sum_nodes(sm.nodes, 32 * kHalfWarps, [&](int sl, int n) { return slice_node(sm, sl, n); });
   unit_finalize<FAR>(sys, g, sm.I, 32 * kHalfWarps, [&](int sl, int k, int l) { return sm.wa[sl].part[k][l]; },
@@ -682,10 +695,10 @@ __device__ __forceinline__ void trace_unit_2pass(const DevSystem& sys, int blk, 
   __syncthreads();
 }
 
-template <bool FAR = false, bool S3 = false>
+template <bool FAR = false, bool BLK = false>
 __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_image_2pass_kernel(const __grid_constant__ DevSystem sys) {
   __shared__ TraceSmem<kTraceWarps> sm;
-  trace_unit_2pass<FAR, S3>(sys, blockIdx.x, sm);
+  trace_unit_2pass<FAR, BLK>(sys, blockIdx.x, sm);
 }
 
 // Cluster form: CL CTAs of kTraceWarps/CL warps share one unit (register budget for 16 warps
@@ -693,7 +706,7 @@ __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_image_2pass_kernel(c
 // [r*NWC, (r+1)*NWC) of the same split; the leader reads every CTA's partials through
 // distributed shared memory in slice order, so the image is bitwise that of the one-CTA form,
 // while the finer CTAs balance the tail of the grid across the SMs.
-template <int CL, bool FAR = false, bool S3 = false>
+template <int CL, bool FAR = false, bool BLK = false>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(32 * (kTraceWarps / CL), 4 * CL / 2)
 trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
   constexpr int NWC = kTraceWarps / CL;
@@ -701,7 +714,7 @@ trace_cluster_kernel(const __grid_constant__ DevSystem sys) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const UnitGeom g = unit_geom(sys, blockIdx.x / CL);
-  unit_partials<NWC, FAR, S3>(sys, g, rank * NWC, sm);
+  unit_partials<NWC, FAR, BLK>(sys, g, rank * NWC, sm);
   cluster.sync();
   if (rank == 0) {
     const TraceSmem<NWC>* peers[CL];
@@ -751,7 +764,7 @@ __global__ void __launch_bounds__(32 * kHalfWarps, 4) trace_batch_kernel(BatchMe
     if (u >= total) return;
     const int i = batch_system_of(unit_prefix, n_sys, u);
     const DevSystem& sys = systems[i];
-    if (sys.s == 3) trace_unit_2pass<FAR, true>(sys, u - unit_prefix[i], sm);
+    if (block_layout(sys.s)) trace_unit_2pass<FAR, true>(sys, u - unit_prefix[i], sm);
     else trace_unit_2pass<FAR, false>(sys, u - unit_prefix[i], sm);
   }
 }
@@ -772,7 +785,7 @@ __global__ void __launch_bounds__(32 * kTraceWarps, 2) trace_batch8_kernel(Batch
     if (u >= total) return;
     const int i = batch_system_of(unit_prefix, n_sys, u);
     const DevSystem& sys = systems[i];
-    if (sys.s == 3) trace_unit<FAR, true>(sys, u - unit_prefix[i], sm);
+    if (block_layout(sys.s)) trace_unit<FAR, true>(sys, u - unit_prefix[i], sm);
     else trace_unit<FAR, false>(sys, u - unit_prefix[i], sm);
   }
 }
@@ -799,7 +812,7 @@ trace_batch_cluster_kernel(BatchMeta* __restrict__ meta) {
     const int i = batch_system_of(unit_prefix, n_sys, u);
     const DevSystem& sys = systems[i];
     const UnitGeom g = unit_geom(sys, u - unit_prefix[i]);
-    if (sys.s == 3) unit_partials<NWC, FAR, true>(sys, g, rank * NWC, sm);
+    if (block_layout(sys.s)) unit_partials<NWC, FAR, true>(sys, g, rank * NWC, sm);
     else unit_partials<NWC, FAR, false>(sys, g, rank * NWC, sm);
     cluster.sync();
     if (rank == 0) {
@@ -817,14 +830,14 @@ trace_batch_cluster_kernel(BatchMeta* __restrict__ meta) {
 }
 
 // Launch of a single-system form (variant) and of a batched form, per instantiation.
-template <bool FAR, bool S3>
+template <bool FAR, bool BLK>
 inline void launch_trace_form(const DevSystem& sys, int variant, int units, cudaStream_t st) {
   switch (variant) {
-    case 1: trace_image_2pass_kernel<FAR, S3><<<units, 32 * kHalfWarps, 0, st>>>(sys); break;
-    case 2: trace_cluster_kernel<2, FAR, S3><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
-    case 3: trace_cluster_kernel<4, FAR, S3><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
-    case 4: trace_cluster_kernel<8, FAR, S3><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
-    default: trace_image_kernel<2, FAR, S3><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
+    case 1: trace_image_2pass_kernel<FAR, BLK><<<units, 32 * kHalfWarps, 0, st>>>(sys); break;
+    case 2: trace_cluster_kernel<2, FAR, BLK><<<units * 2, 32 * (kTraceWarps / 2), 0, st>>>(sys); break;
+    case 3: trace_cluster_kernel<4, FAR, BLK><<<units * 4, 32 * (kTraceWarps / 4), 0, st>>>(sys); break;
+    case 4: trace_cluster_kernel<8, FAR, BLK><<<units * 8, 32 * (kTraceWarps / 8), 0, st>>>(sys); break;
+    default: trace_image_kernel<2, FAR, BLK><<<units, 32 * kTraceWarps, 0, st>>>(sys); break;
   }
 }
 
