@@ -136,6 +136,17 @@ __device__ __forceinline__ int unit_sample_index(const UnitGeom& g, int l, int k
   return (pr * g.bw + pc) * g.s2 + (sr - pr * g.s) * g.s + (sc - pc * g.s);
 }
 
+// Coordinate of a block-layout sample column c (0 .. 23 of the unit) or row r (0 .. 11): the
+// sample_xy value of every sample in it, from one division by s.
+__device__ __forceinline__ float block_x(const DevSystem& sys, const UnitGeom& g, int c) {
+  const int pc = c / g.s;
+  return grid_coord(sys.x0, g.bx * g.bw + pc, sys.nx, c - pc * g.s, g.s, sys.dpix);
+}
+__device__ __forceinline__ float block_y(const DevSystem& sys, const UnitGeom& g, int r) {
+  const int pr = r / g.s;
+  return grid_coord(sys.y0, g.by * g.bh + pr, sys.ny, r - pr * g.s, g.s, sys.dpix);
+}
+
 // In the block layout a lane's packed pairs are {(0,b),(1,b)} for the columns b = 0, 1, 2, then
 // {(2,0),(2,1)}, and the scalar sample (2,2).  The three column pairs share their rows, so one
 // (dy, dy^2) pair serves them, each pair's dx is one column's, and the scalar sample's dx and
@@ -176,12 +187,25 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   auto half_of = [](int k) { return BLK ? s3_half_of(k) : (k & 1); };
   auto k_of = [](int i, int e) { return BLK ? s3_k_of(i, e) : 2 * i + e; };
   float xmin = 3.0e38f, xmax = -3.0e38f, ymin = 3.0e38f, ymax = -3.0e38f;
+  float bxs[3], bys[3];  // block layout: the lane's three sample columns and rows
+  if constexpr (BLK) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      bxs[e] = block_x(sys, g, 3 * (lane & 7) + e);
+      bys[e] = block_y(sys, g, 3 * (lane >> 3) + e);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < kUnitPts; ++k) {
-    int q = BLK ? unit_sample_index(g, lane, k) : lane * kUnitPts + k;
-    if (q >= g.nsamp) q = 0;
     float x, y;
-    sample_xy(sys, g, q, x, y);
+    if constexpr (BLK) {
+      x = bxs[k % 3];
+      y = bys[k / 3];
+    } else {
+      int q = lane * kUnitPts + k;
+      if (q >= g.nsamp) q = 0;
+      sample_xy(sys, g, q, x, y);
+    }
     xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
     ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
     const int pr = pair_of(k);
@@ -595,8 +619,19 @@ __device__ __forceinline__ void unit_finalize(const DevSystem& sys, const UnitGe
   }
   for (int idx = threadIdx.x; idx < 32 * kUnitPts; idx += nthr) {
     const int k = idx >> 5, l = idx & 31;
-    const int q = unit_sample_index(g, l, k);
-    if (q >= g.nsamp) continue;
+    int q;
+    float x, y;
+    if (block_layout(g.s)) {  // the sample's index and coordinates from its column and row
+      const int sc = 3 * (l & 7) + k % 3, sr = 3 * (l >> 3) + k / 3;
+      const int pc = sc / g.s, pr = sr / g.s;
+      q = (pr * g.bw + pc) * g.s2 + (sr - pr * g.s) * g.s + (sc - pc * g.s);
+      x = grid_coord(sys.x0, g.bx * g.bw + pc, sys.nx, sc - pc * g.s, g.s, sys.dpix);
+      y = grid_coord(sys.y0, g.by * g.bh + pr, sys.ny, sr - pr * g.s, g.s, sys.dpix);
+    } else {
+      q = l * kUnitPts + k;
+      if (q >= g.nsamp) continue;
+      sample_xy(sys, g, q, x, y);
+    }
     float sx = 0.f, sy = 0.f;
 #pragma unroll
     for (int sl = 0; sl < kTraceWarps; ++sl) {
@@ -604,8 +639,6 @@ __device__ __forceinline__ void unit_finalize(const DevSystem& sys, const UnitGe
       sx += v.x;
       sy += v.y;
     }
-    float x, y;
-    sample_xy(sys, g, q, x, y);
     if constexpr (FAR) {
       float lx[kFarNodes1], ly[kFarNodes1];
       cheb8_lagrange((x - cxb) * ihx, lx);
