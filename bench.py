@@ -919,7 +919,7 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
     (the whole pool submitted back to back) lets its slots size their workspaces and capture
     their batch graphs (a warm-up of half the pool left the first rate to meet the other half's
     largest requests, and a workspace growth inside it held the client up by 85 ms); an
-    unmeasured open-loop window of `settle_s` at the first rate follows (the first window after
+    unmeasured open-loop window of `settle_s` at the first rate (at most 3,000 req/s) follows (the first window after
     the warm-up saw a one-time 58 ms overshoot of the client's own sleep, in no later window),
     and each rate's statistics are reset before it starts.  Each pool entry has `out_sets` sets
     of output buffers used in turn, so a buffer set is reused only pool_size * out_sets arrivals
@@ -970,16 +970,24 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
         srv.wait(t, 600000)
     t_warm = time.perf_counter() - t0
     if settle_s > 0 and rates:
+        settle_rate = min(rates[0], 3000.0)
         rng = np.random.default_rng(12345)
-        arr = np.cumsum(rng.exponential(1.0 / rates[0], int(rates[0] * settle_s * 1.2) + 16))
+        arr = np.cumsum(rng.exponential(1.0 / settle_rate, int(settle_rate * settle_s * 1.2) + 16))
         ts0 = time.perf_counter()
-        settle = []
+        settle = {}
         for i, ta in enumerate(arr[arr < settle_s]):
             delay = ta - (time.perf_counter() - ts0)
             if delay > 0:
                 time.sleep(delay)
-            settle.append(submit(srv, i % len(pool), 0))
-        for t in settle:
+            j = i % len(pool)
+            if j in settle:  # an entry's buffers are reused only after its previous request
+                srv.wait(settle.pop(j), 600000)
+            try:
+                settle[j] = submit(srv, j, 0)
+            except lenssim.LensSimError as e:
+                if e.code != lenssim.LENS_ERR_BUSY:
+                    raise
+        for t in settle.values():
             srv.wait(t, 600000)
     out = []
     for rate in rates:
@@ -989,7 +997,7 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
         arrivals = arrivals[arrivals < seconds]
         codes = collections.Counter()
         pending = {}
-        rejected = blocked = 0
+        rejected = blocked = img_ok = 0
         late = 0.0
         gc.collect()
         gc.disable()  # no collector pauses inside the arrival schedule
@@ -1010,6 +1018,7 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
                     blocked += 1
                     rc = srv.wait(prev, 600000)
                 codes[rc] += 1
+                img_ok += int(rc == 0 and pool[j].kind == 0)
             try:
                 pending[(j, c)] = submit(srv, j, c)
             except lenssim.LensSimError as e:
@@ -1017,8 +1026,10 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
                     raise
                 rejected += 1
         t_submit = time.perf_counter() - t0
-        for t in pending.values():
-            codes[srv.wait(t, 600000)] += 1
+        for (jj, _), t in pending.items():
+            rc = srv.wait(t, 600000)
+            codes[rc] += 1
+            img_ok += int(rc == 0 and pool[jj].kind == 0)
         t_all = time.perf_counter() - t0
         gc.enable()
         st = srv.stats()
@@ -1027,6 +1038,8 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
                "blocked_reuses": blocked, "admitted": int(sum(codes.values())), "completed_ok": codes.get(0, 0),
                "failed": {str(k): v for k, v in codes.items() if k != 0},
                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "served_req_per_s": st["requests_per_s"],
+               "images_completed": img_ok,
+               "served_images_per_s": st["requests_per_s"] * img_ok / max(1, codes.get(0, 0)),
                "completed_per_wall_s": codes.get(0, 0) / t_all}
         if rec["failed"]:
             rec["last_error"] = srv.last_error()
@@ -1079,7 +1092,7 @@ def main():
     ap.add_argument("--psf-only", type=int, default=0, metavar="N_IMG",
                     help="only the standalone PSF measurement on N_IMG 256^2 images (profiling runs)")
     ap.add_argument("--batch-systems", type=int, default=4096)
-    ap.add_argument("--serve-rates", type=float, nargs="*", default=[1000.0, 3000.0, 10000.0, 20000.0])
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[100.0, 1000.0, 3000.0, 10000.0, 20000.0, 30000.0])
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     args = ap.parse_args()
     if args.warmup < 3:
