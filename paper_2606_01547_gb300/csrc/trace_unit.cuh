@@ -89,8 +89,10 @@ struct TraceSmem {
       float4 marked[32][kNearRec];
       int list[kStageList];
       float4 box;  // the unit's bounding box (kept here rather than in registers)
-      float queue[kUnitPts * 32];  // closed-form arguments, then values, of one marked subhalo;
-                                   // at the end, the slice's far-field node sums (float2 x 64)
+      // per stage: the far-field node classes' compact records (float4 x 2 per lane), then the
+      // closed-form arguments and values of one marked subhalo at a time; at the end, the
+      // slice's far-field node sums (float2 x 64)
+      alignas(16) float queue[kUnitPts * 32];
     };
     float2 part[kUnitPts][32];
   } wa[NW];
@@ -253,17 +255,6 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     pn_x = make_float2(xn, xn);
     pn_y = make_float2(fmaf(hy, c_cheb8[nj], cyb), fmaf(hy, c_cheb8[nj + 1], cyb));
   }
-  // far-field series truncated after d_K for the record t of one subhalo: a packed sample pair
-  auto packed_pair = [&](const float4* t, auto Kc, float2 px, float2 py, float2& ax, float2& ay) {
-    constexpr int K = decltype(Kc)::value;
-    const float2 dx = __fadd2_rn(px, make_float2(t[0].x, t[0].y));
-    const float2 dy = __fadd2_rn(py, make_float2(t[0].z, t[0].w));
-    const float2 r2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-    const float2 u = make_float2(rsqrt_ftz(r2.x), rsqrt_ftz(r2.y));
-    const float2 gg = tnfw_series2_k<K>(u, __fmul2_rn(u, u), t);
-    ax = __ffma2_rn(gg, dx, ax);
-    ay = __ffma2_rn(gg, dy, ay);
-  };
   // offsets of the lane's samples from record t's centre: packed pairs' dx, dy, dy^2, and the
   // scalar samples' (dx = x - cx, dy = y - cy, each computed once per distinct value)
   auto deltas = [&](const float4* t, float2* dx, float2* dy, float2* dy2, float* sdx, float* sdy, float* sdy2) {
