@@ -296,7 +296,7 @@ int lens_sim_linear_amp(lens_sim* sim, const lens_system* sys, const float* data
  *    threads) race on the array: serialise them on one stream. */
 #define LENS_NOALLOC_MAX_SUBHALOS 20000
 #define LENS_NOALLOC_MAX_PIXELS (512 * 512)
-#define LENS_NOALLOC_SCRATCH_BYTES (LENS_NOALLOC_MAX_SUBHALOS * 176 + LENS_NOALLOC_MAX_PIXELS * 4 + 642 * 4)
+#define LENS_NOALLOC_SCRATCH_BYTES (LENS_NOALLOC_MAX_SUBHALOS * 224 + LENS_NOALLOC_MAX_PIXELS * 4 + 642 * 4)
 int lens_sim_image_noalloc(const lens_system* sys, const float* psf, int k, float* out_image, void* stream);
 
 /* ---------------------------------------------------------------- serving

@@ -310,13 +310,18 @@ constexpr float kFarRadius3 = 40.f;  // 3-term series (c_0, c_2, c_3) from here
 constexpr int kSubStride = 8;   // float4 per subhalo record (staged through shared memory)
 constexpr int kMidTerms = 12;   // coefficients of the annulus polynomial
 constexpr int kMidStride = 3;   // float4 per subhalo in the annulus block
-constexpr int kTableStride = kSubStride + kMidStride;  // float4 per subhalo in a whole table
+constexpr int kFarStride = 3;   // float4 per subhalo in the compact far-field block
+constexpr int kTableStride = kSubStride + kMidStride + kFarStride;  // float4 per subhalo in a whole table
 // Largest tau whose annulus 4 <= x < 7 max(tau, 1) the 12-term polynomial covers to 1e-7
 // (relative, in FP64 arithmetic); beyond it the annulus takes the closed form.
 constexpr float kMidTauMax = 8.5f;
 
-// A subhalo table of n subhalos is n records of kSubStride float4 followed by n annulus blocks of
-// kMidStride float4.  The record (128 B) is laid out for packed FP32x2 arithmetic (two samples
+// A subhalo table of n subhalos is n records of kSubStride float4, then n annulus blocks of
+// kMidStride float4, then n compact far-field blocks of kFarStride float4,
+//   f0 = (-cx, -cy, r_far^2, r_4^2),  f1 = (r_3^2, d_0, d_2, d_3),  f2 = (d_4, d_5, d_6, 0),
+// the same numbers as the record's, once each: all that the bounding-box test and the far-field
+// series read, in 48 B instead of 128 B (the image kernels stage the table once per unit and
+// slice).  The record (128 B) is laid out for packed FP32x2 arithmetic (two samples
 // per instruction): centres negated and every series coefficient stored as a duplicated pair,
 //   t0 = (-cx, -cx, -cy, -cy),           t1 = (r_far^2 = 49 max(tau,1)^2 Rs^2, 1/Rs^2, tau, A),
 //   t2 = (d_0, d_0, d_2, d_2),  t3 = (d_3, d_3, d_4, d_4),  t4 = (d_5, d_5, d_6, d_6),
@@ -590,6 +595,11 @@ static __device__ __noinline__ void tnfw_write_table(float cx, float cy, float R
   float4* om = tab + (size_t)kSubStride * n + (size_t)kMidStride * j;
 #pragma unroll
   for (int c = 0; c < kMidStride; ++c) om[c] = m[c];
+  static_assert(kFarTerms == 6, "the compact block holds d_0, d_2 .. d_6");
+  float4* of = tab + (size_t)(kSubStride + kMidStride) * n + (size_t)kFarStride * j;
+  of[0] = make_float4(t[0].x, t[0].z, t[1].x, t[5].x);
+  of[1] = make_float4(t[5].y, t[2].x, t[2].z, t[3].x);
+  of[2] = make_float4(t[3].z, t[4].x, t[4].z, 0.f);
 }
 
 __device__ __forceinline__ void alpha_nfw(float x, float y, float Rs, float alphaRs, float cx, float cy,

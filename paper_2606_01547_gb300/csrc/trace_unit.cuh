@@ -176,8 +176,9 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   const int slice = slice0 + w;
   const int lo = (int)(((long long)n * slice) / kTraceWarps);
   const int hi = (int)(((long long)n * (slice + 1)) / kTraceWarps);
-  const float4* __restrict__ tab = sys.sub;
+  const float4* __restrict__ rec_tab = sys.sub;
   const float4* __restrict__ mid_tab = sys.sub + (size_t)kSubStride * n;
+  const float4* __restrict__ far_tab = sys.sub + (size_t)(kSubStride + kMidStride) * n;
   auto& area = sm.wa[area0 + w];
 
   float2 px2[kP], py2[kP], ax2[kP], ay2[kP];
@@ -478,31 +479,33 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     bool near = false, interp = false;
     int tier = 0;  // 0: 6-term series, 1: 4-term, 2: 3-term
     if (alive) {
-      float4 st[kSubStride];
-#pragma unroll
-      for (int c = 0; c < kSubStride; ++c) st[c] = __ldg(tab + (size_t)kSubStride * idx + c);
-      area.sub[lane][0] = st[0];
-#pragma unroll
-      for (int c = 1; c < kFarRec; ++c) area.sub[lane][c] = st[1 + c];
-      // st[0] holds the negated centre
+      // the compact block, written out as the record's duplicated pairs
+      const float4 f0 = __ldg(far_tab + (size_t)kFarStride * idx);
+      const float4 f1 = __ldg(far_tab + (size_t)kFarStride * idx + 1);
+      const float4 f2 = __ldg(far_tab + (size_t)kFarStride * idx + 2);
+      area.sub[lane][0] = make_float4(f0.x, f0.x, f0.y, f0.y);
+      area.sub[lane][1] = make_float4(f1.y, f1.y, f1.z, f1.z);
+      area.sub[lane][2] = make_float4(f1.w, f1.w, f2.x, f2.x);
+      area.sub[lane][3] = make_float4(f2.y, f2.y, f2.z, f2.z);
+      // f0.xy hold the negated centre
       const float4 bx = area.box;
       const float xmin = bx.x, xmax = bx.y, ymin = bx.z, ymax = bx.w;
-      const float ddx = fmaxf(fmaxf(xmin + st[0].x, -st[0].x - xmax), 0.f);
-      const float ddy = fmaxf(fmaxf(ymin + st[0].z, -st[0].z - ymax), 0.f);
+      const float ddx = fmaxf(fmaxf(xmin + f0.x, -f0.x - xmax), 0.f);
+      const float ddy = fmaxf(fmaxf(ymin + f0.y, -f0.y - ymax), 0.f);
       const float d2 = fmaf(ddx, ddx, ddy * ddy);
-      near = d2 < st[1].x;
-      tier = d2 >= st[5].y ? 2 : (d2 >= st[5].x ? 1 : 0);
+      near = d2 < f0.z;
+      tier = d2 >= f1.x ? 2 : (d2 >= f0.w ? 1 : 0);
       if constexpr (FAR) {
         interp = !near && d2 >= far_d2;  // marked subhalos always run at the samples
         if (interp) {  // the compact record of the node classes (queue area, free until the near field)
           float4* compact = reinterpret_cast<float4*>(area.queue);
-          compact[2 * lane] = make_float4(st[0].x, st[0].z, st[2].x, st[2].z);
-          compact[2 * lane + 1] = make_float4(st[3].x, st[3].z, st[4].x, st[4].z);
+          compact[2 * lane] = make_float4(f0.x, f0.y, f1.y, f1.z);
+          compact[2 * lane + 1] = make_float4(f1.w, f2.x, f2.y, f2.z);
         }
       }
       if (near) {
-        area.marked[lane][0] = st[1];
-        area.marked[lane][1] = st[6];
+        area.marked[lane][0] = __ldg(rec_tab + (size_t)kSubStride * idx + 1);
+        area.marked[lane][1] = __ldg(rec_tab + (size_t)kSubStride * idx + 6);
 #pragma unroll
         for (int c = 0; c < kMidStride; ++c) area.marked[lane][2 + c] = __ldg(mid_tab + (size_t)kMidStride * idx + c);
       }
