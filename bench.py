@@ -345,6 +345,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
     clocks["soak"] = dict(clk_soak.summary(), steps=soak_steps, seconds=args.clock_soak_s)
     max_mhz = clocks["sm_max_mhz"] or 2070.0
     peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    # measured pipe rates per SM and SM clock (after the timed region): the derived FP32 peak's
+    # 128 lanes checked, and the MUFU rate the reciprocal square root of every pair draws on
+    rates = sim.pipe_rates()
     census = pair_census(systems[0], args.far_field)
     achieved = census["flops"] / avg_trace_s / 1e12
     traffic = None
@@ -365,9 +368,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int) -> None:
                 "frac_21_flop_ledger": (pairs * FLOPS_PER_PAIR / avg_trace_s / 1e12 / peak_tflops
                                         if args.far_field <= 0 else None),
                 "trace_ms": avg_trace_s * 1e3,
-                # SFU: one MUFU.RSQ per evaluated pair against 16 MUFU results per clock per SM
-                "sfu": {"mufu_per_s": census["pairs"] / avg_trace_s, "peak_per_s": sms * 16 * max_mhz * 1e6,
-                        "frac": census["pairs"] / avg_trace_s / (sms * 16 * max_mhz * 1e6)}}
+                "pipe_rates_per_sm_clock": rates,
+                "frac_of_measured_fp32": achieved / (sms * rates["fp32_lane_ops_ffma2"] * 2 * max_mhz * 1e6 / 1e12),
+                # SFU: one MUFU.RSQ per evaluated pair against the measured rsqrt rate
+                "sfu": {"mufu_per_s": census["pairs"] / avg_trace_s,
+                        "peak_per_s": sms * rates["mufu_rsqrt"] * max_mhz * 1e6,
+                        "peak_basis": f"{sms} SMs x {rates['mufu_rsqrt']:.2f} rsqrt.approx results per clock "
+                                      f"(measured, lens_sim_pipe_rates) x {max_mhz:.0f} MHz",
+                        "frac": census["pairs"] / avg_trace_s / (sms * rates["mufu_rsqrt"] * max_mhz * 1e6)}}
     if args.far_field > 0:
         roofline["evaluated_pairs"] = census["pairs"]
         roofline["interpolated_pair_fraction"] = census["interpolated_pairs"] / pairs

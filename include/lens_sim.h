@@ -299,6 +299,23 @@ int lens_sim_linear_amp(lens_sim* sim, const lens_system* sys, const float* data
 #define LENS_NOALLOC_SCRATCH_BYTES (LENS_NOALLOC_MAX_SUBHALOS * 224 + LENS_NOALLOC_MAX_PIXELS * 4 + 642 * 4)
 int lens_sim_image_noalloc(const lens_system* sys, const float* psf, int k, float* out_image, void* stream);
 
+/* ---------------------------------------------------------------- measurement
+ * lens_sim_pipe_rates measures the handle's GPU pipes that bound its ALU-bound kernels (the
+ * subhalo sum: FP32 FMAs and one MUFU reciprocal square root per pair), the denominators of
+ * their rooflines.  Each rate comes from a short launch of independent dependency chains of
+ * one instruction kind (32 warps per SM), timed by every block with the SM clock, so it is
+ * per SM and per SM clock, independent of the clock the GPU ran at: the median over SMs of the
+ * lane operations of an SM's blocks over the longest of their times.  rates[0]: FP32 lane
+ * operations (an FMA counted once) with packed FFMA2 chains; rates[1]: the same with scalar
+ * FFMA chains; rates[2 .. 5]: MUFU results with rsqrt.approx.ftz, ex2.approx.ftz,
+ * lg2.approx.ftz and rcp.approx.ftz chains.  The first min(n_rates, LENS_PIPE_RATES) entries
+ * are written (later ones set to 0).  It synchronises its own stream, takes a few
+ * milliseconds and a scratch of about 4 KB per SM (within the memory budget), and is not
+ * meant for a timed region.  rates NULL or n_rates < 1: LENS_ERR_INVALID_ARG; a failed CUDA
+ * call: LENS_ERR_CUDA. */
+#define LENS_PIPE_RATES 6
+int lens_sim_pipe_rates(lens_sim* sim, double* rates, int n_rates);
+
 /* ---------------------------------------------------------------- serving
  * A server owns its own lens_sim state, streams and a worker thread that admits requests
  * by a device-memory budget, batches what is waiting, and overlaps batches on the device.

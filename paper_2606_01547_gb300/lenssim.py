@@ -34,6 +34,8 @@ CONV_FFT_MIN_K = 33   # LENS_CONV_FFT_MIN_K: auto takes the FFT from this kernel
 TRACE_VARIANTS = ("cta8", "cta4x2pass", "cluster2x4", "cluster4x2", "cluster8x1")
 BATCH_FORMS = ("cta4x2pass", "cta8", "cluster2x4")   # LENS_BATCH_FORMS persistent trace kernels
 BATCH_ORDERS = ("cost_desc", "given")
+# LENS_PIPE_RATES entries of lens_sim_pipe_rates, in order (per SM and SM clock)
+PIPE_RATES = ("fp32_lane_ops_ffma2", "fp32_lane_ops_ffma", "mufu_rsqrt", "mufu_ex2", "mufu_lg2", "mufu_rcp")
 _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_sim_register_psf",
@@ -41,7 +43,7 @@ EXPORTED = ("lens_sim_create", "lens_sim_destroy", "lens_sim_last_error", "lens_
             "lens_sim_autotune", "lens_sim_set_variant", "lens_sim_set_far_field", "lens_sim_set_batch_schedule",
             "lens_sim_autotune_batch",
             "lens_sim_set_conv_method", "lens_sim_grad",
-            "lens_sim_linear_amp",
+            "lens_sim_linear_amp", "lens_sim_pipe_rates",
             "lens_sim_image_noalloc", "lens_serve_create", "lens_serve_sim", "lens_serve_submit", "lens_serve_wait",
             "lens_serve_poll", "lens_serve_cancel", "lens_serve_pause", "lens_serve_stats", "lens_serve_last_error",
             "lens_serve_reset_stats", "lens_serve_destroy")
@@ -130,6 +132,7 @@ def lib():
             L.lens_sim_autotune_batch.argtypes = [vp, ctypes.POINTER(LensSystemC), ip, ctypes.POINTER(vp), ip,
                                                   ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(fp), vp]
             L.lens_sim_set_conv_method.argtypes = [vp, ctypes.c_int]
+            L.lens_sim_pipe_rates.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ip]
             L.lens_sim_image_noalloc.argtypes = [ctypes.POINTER(LensSystemC), vp, ip, vp, vp]
             L.lens_sim_linear_amp.argtypes = [vp, ctypes.POINTER(LensSystemC), vp, fp, fp, vp, ip, vp, vp, vp]
             L.lens_serve_create.argtypes = [ctypes.POINTER(SimConfig), ip, ctypes.POINTER(vp)]
@@ -280,6 +283,13 @@ class Simulator:
     # ------------------------------------------------------------------ tuning
     def set_variant(self, variant: int) -> None:
         self._check(self._L.lens_sim_set_variant(self.h, int(variant)))
+
+    def pipe_rates(self) -> dict:
+        """Measured FP32 and MUFU rates of this GPU per SM and SM clock (lens_sim_pipe_rates):
+        the denominators of the ALU-bound kernels' rooflines."""
+        out = (ctypes.c_double * len(PIPE_RATES))()
+        self._check(self._L.lens_sim_pipe_rates(self.h, out, len(PIPE_RATES)))
+        return {k: float(v) for k, v in zip(PIPE_RATES, out)}
 
     def set_far_field(self, kappa: float) -> None:
         """Far-field interpolation of the subhalo sum for image calls (0: the exact sum, the

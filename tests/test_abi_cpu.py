@@ -78,6 +78,7 @@ def test_binding_constants_match_the_header():
     assert _define(text, "LENS_TRACE_VARIANTS") == len(lenssim.TRACE_VARIANTS)
     assert int(re.search(r"kBatchForms\s*=\s*(\d+)", kern).group(1)) == len(lenssim.BATCH_FORMS)
     assert _define(text, "LENS_BATCH_FORMS") == len(lenssim.BATCH_FORMS)
+    assert _define(text, "LENS_PIPE_RATES") == len(lenssim.PIPE_RATES)
     # every profile the library takes has a parameter layout in the input generators
     for name in list(lenssim.LENS_TYPES) + list(lenssim.LIGHT_TYPES):
         assert name in workloads.N_PARAMS, name
