@@ -675,8 +675,8 @@ def per_config_extra(sim, lenssim, W, dev, cpu_budget_s: float = 10.0):
 
 
 def measured_hbm_gbs():
-    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json), else the
-    recipe's fallback figure."""
+    """HBM copy bandwidth measured on GB300s (MEASURED_PEAKS.json), else a fallback figure
+    from an earlier GB300 measurement."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"

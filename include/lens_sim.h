@@ -45,7 +45,7 @@ typedef enum {
   LENS_ERR_CUDA = -3,         /* a CUDA runtime call failed; see lens_sim_last_error */
   LENS_ERR_TIMEOUT = -4,      /* a bounded wait ran out */
   LENS_ERR_BUSY = -5,         /* admission refused (server) or result still pending (poll) */
-  LENS_ERR_UNSUPPORTED = -6,  /* valid request outside what this build implements */
+  LENS_ERR_UNSUPPORTED = -6,  /* valid request outside what this library implements */
   LENS_ERR_CANCELLED = -7     /* the request was cancelled before it ran */
 } lens_status;
 
