@@ -181,6 +181,8 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   const float4* __restrict__ far_tab = sys.sub + (size_t)(kSubStride + kMidStride) * n;
   auto& area = sm.wa[area0 + w];
 
+  // generic layout: the packed pairs' and scalar samples' coordinates (px2, py2, po_*); block
+  // layout: the lane's three columns and rows (bxs, bys); both: the sums (ax2, ay2, ao_*)
   float2 px2[kP], py2[kP], ax2[kP], ay2[kP];
   constexpr int kS = kUnitPts - 2 * kP;  // scalar samples
   static_assert(!BLK || (kP == 4 && kS == 1), "the block layout pairs a lane's 3 x 3 samples");
@@ -211,6 +213,7 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     }
     xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
     ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
+    if constexpr (BLK) continue;
     const int pr = pair_of(k);
     if (pr < 0) {
       po_x[k - 2 * kP] = x;
@@ -257,21 +260,29 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     pn_y = make_float2(fmaf(hy, c_cheb8[nj], cyb), fmaf(hy, c_cheb8[nj + 1], cyb));
   }
   // offsets of the lane's samples from record t's centre: packed pairs' dx, dy, dy^2, and the
-  // scalar samples' (dx = x - cx, dy = y - cy, each computed once per distinct value)
+  // scalar samples' (dx = x - cx, dy = y - cy).  In the block layout the 3 columns' dx and the
+  // 3 rows' dy and dy^2 are computed once each as scalars and then paired: an FP32x2 operation
+  // on a duplicated pair spends two lane operations of the FP32 pipe on one value (9 scalar
+  // operations per subhalo instead of 8 FP32x2 ones, i.e. 16 lane operations; the same IEEE
+  // results)
   auto deltas = [&](const float4* t, float2* dx, float2* dy, float2* dy2, float* sdx, float* sdy, float* sdy2) {
-    const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
     if constexpr (BLK) {
-#pragma unroll
-      for (int i = 0; i < kP; ++i) dx[i] = __fadd2_rn(px2[i], ncx);  // columns 0, 1, 2 duplicated; (0, 1)
-      const float2 dya = __fadd2_rn(py2[0], ncy);  // rows 0, 1 (the column pairs hold the same y)
-      const float2 dyc = __fadd2_rn(py2[3], ncy);  // row 2, duplicated
-      const float2 dy2a = __fmul2_rn(dya, dya), dy2c = __fmul2_rn(dyc, dyc);
+      const float ex0 = bxs[0] + t[0].x, ex1 = bxs[1] + t[0].x, ex2 = bxs[2] + t[0].x;
+      const float ey0 = bys[0] + t[0].z, ey1 = bys[1] + t[0].z, ey2 = bys[2] + t[0].z;
+      const float qy0 = ey0 * ey0, qy1 = ey1 * ey1, qy2 = ey2 * ey2;
+      dx[0] = make_float2(ex0, ex0);
+      dx[1] = make_float2(ex1, ex1);
+      dx[2] = make_float2(ex2, ex2);
+      dx[3] = make_float2(ex0, ex1);
+      const float2 dya = make_float2(ey0, ey1), dyc = make_float2(ey2, ey2);
+      const float2 dy2a = make_float2(qy0, qy1), dy2c = make_float2(qy2, qy2);
       dy[0] = dya; dy[1] = dya; dy[2] = dya; dy[3] = dyc;
       dy2[0] = dy2a; dy2[1] = dy2a; dy2[2] = dy2a; dy2[3] = dy2c;
-      sdx[0] = dx[2].x;   // sample (2, 2): column 2
-      sdy[0] = dyc.x;     // row 2
-      sdy2[0] = dy2c.x;
+      sdx[0] = ex2;   // sample (2, 2): column 2
+      sdy[0] = ey2;   // row 2
+      sdy2[0] = qy2;
     } else {
+      const float2 ncx = make_float2(t[0].x, t[0].y), ncy = make_float2(t[0].z, t[0].w);
 #pragma unroll
       for (int i = 0; i < kP; ++i) {
         dx[i] = __fadd2_rn(px2[i], ncx);
@@ -334,10 +345,9 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
   };
   // sample k's coordinates (k static) and its accumulators
   auto sample_at = [&](int k, float& x, float& y) {
-    if constexpr (BLK) {  // column b from the column pairs, row a from pair 0 or 3 (those stay live)
-      const int a = k / 3, b = k % 3;
-      x = px2[b].x;
-      y = a == 2 ? py2[3].x : (a == 0 ? py2[0].x : py2[0].y);
+    if constexpr (BLK) {  // the lane's column b and row a
+      x = bxs[k % 3];
+      y = bys[k / 3];
       return;
     }
     const int pr = pair_of(k);
