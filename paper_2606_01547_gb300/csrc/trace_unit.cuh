@@ -324,10 +324,27 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
 #pragma unroll
     for (int c = 1; c < kFarRec; ++c) t[1 + c] = area.sub[q][c];
   };
-  // a class of far subhalos at list positions [b, e), b even: two per basic block, so the
-  // scheduler overlaps one's reciprocal square roots and loads with the other's polynomial
+  // a class of far subhalos at list positions [b, e), b even: two per basic block (four for the
+  // shortest series, the most common class), so the scheduler overlaps one's reciprocal square
+  // roots and loads with another's polynomial; the subhalos are summed in list order either way
   auto far_class = [&](int b, int e, auto Kc) {
     int q = b;
+    if constexpr (decltype(Kc)::value == 3) {
+#pragma unroll 1
+      for (; q + 3 < e; q += 4) {
+        float4 ta[5], tb[5], tc[5], td[5];
+        const int2 qa = *reinterpret_cast<const int2*>(&area.list[q]);
+        const int2 qb = *reinterpret_cast<const int2*>(&area.list[q + 2]);
+        load_far(qa.x, ta);
+        load_far(qa.y, tb);
+        load_far(qb.x, tc);
+        load_far(qb.y, td);
+        far_all(ta, Kc);
+        far_all(tb, Kc);
+        far_all(tc, Kc);
+        far_all(td, Kc);
+      }
+    }
 #pragma unroll 1
     for (; q + 1 < e; q += 2) {
       float4 ta[5], tb[5];
