@@ -1014,7 +1014,13 @@ def serving_extra(lenssim, W, rates, seconds: float, pool_size: int = 6000, out_
         for i, ta in enumerate(arrivals):
             delay = ta - (time.perf_counter() - t0)
             if delay > 0:
-                time.sleep(delay)
+                # time.sleep overshoots short delays (timer slack, ~50-80 us): at 20,000 req/s
+                # (50 us between arrivals) it let the client fall up to 51 ms behind its schedule
+                # and then submit in a burst; the last 0.3 ms are spun instead
+                if delay > 3e-4:
+                    time.sleep(delay - 3e-4)
+                while time.perf_counter() - t0 < ta:
+                    pass
             else:
                 late = max(late, -delay)
             j = i % len(pool)

@@ -325,11 +325,12 @@ __device__ __forceinline__ void unit_partials(const DevSystem& sys, const UnitGe
     for (int c = 1; c < kFarRec; ++c) t[1 + c] = area.sub[q][c];
   };
   // a class of far subhalos at list positions [b, e), b even: two per basic block (four for the
-  // shortest series, the most common class), so the scheduler overlaps one's reciprocal square
-  // roots and loads with another's polynomial; the subhalos are summed in list order either way
+  // shortest series, the most common class, in the exact kernels; the far-field ones measured
+  // slower with it), so the scheduler overlaps one's reciprocal square roots and loads with
+  // another's polynomial; the subhalos are summed in list order either way
   auto far_class = [&](int b, int e, auto Kc) {
     int q = b;
-    if constexpr (decltype(Kc)::value == 3) {
+    if constexpr (decltype(Kc)::value == 3 && !FAR) {
 #pragma unroll 1
       for (; q + 3 < e; q += 4) {
         float4 ta[5], tb[5], tc[5], td[5];
