@@ -22,6 +22,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -106,10 +107,19 @@ def pair_census(system, kappa: float = 0.0) -> dict:
     return out
 
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments, trailing blanks and empty lines."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_hash() -> str:
+    """Hash of the trace kernel's sources as code (comments and blank lines left out), so that a
+    profile capture stays matched to the kernel across comment edits but not code changes."""
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, p)).read()).encode())
     return h.hexdigest()[:16]
 
 

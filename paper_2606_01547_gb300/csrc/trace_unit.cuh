@@ -151,8 +151,9 @@ __device__ __forceinline__ float block_y(const DevSystem& sys, const UnitGeom& g
 
 // In the block layout a lane's packed pairs are {(0,b),(1,b)} for the columns b = 0, 1, 2, then
 // {(2,0),(2,1)}, and the scalar sample (2,2).  The three column pairs share their rows, so one
-// (dy, dy^2) pair serves them, each pair's dx is one column's, and the scalar sample's dx and
-// dy are halves of the column-2 and row-2 values.
+// (dy, dy^2) pair serves them, and each pair's dx is one column's: per subhalo the 3 column
+// offsets and the 3 row offsets and squares are computed once, and the scalar sample takes
+// column 2's and row 2's.
 __host__ __device__ constexpr int s3_pair_of(int k) { return k / 3 < 2 ? k % 3 : (k % 3 < 2 ? 3 : -1); }
 __host__ __device__ constexpr int s3_half_of(int k) { return k / 3 < 2 ? k / 3 : k % 3; }
 __host__ __device__ constexpr int s3_k_of(int i, int e) { return i < 3 ? 3 * e + i : 6 + e; }
@@ -161,9 +162,10 @@ __host__ __device__ constexpr int s3_k_of(int i, int e) { return i < 3 ? 3 * e +
 // kTraceWarps-way split of the subhalo list and writes its 288 partials to wa[area0 + w].part.
 //
 // A lane's first 2 kPackedPairs samples run as packed pairs (FP32x2 instructions, two samples
-// per issue slot), the rest as scalars; the two kinds run on different FP32 pipes.  The
-// packed operations are element-wise the same IEEE operations as the scalar ones, so every
-// sample's deflection is the same whichever kind it is.  With BLK (block_layout(s) only) the
+// per issue slot, on the heavy FMA pipe), the rest as scalars; both kinds draw on the same
+// FP32 capacity, so the packing saves issue slots, not lane operations.  The packed operations
+// are element-wise the same IEEE operations as the scalar ones, so every sample's deflection
+// is the same whichever kind it is.  With BLK (block_layout(s) only) the
 // samples take the block layout above: each sample's arithmetic is unchanged, only shared terms
 // are computed once, so every sample's partial is bitwise that of the generic layout.
 template <int NWC, bool FAR = false, bool BLK = false>

@@ -86,3 +86,17 @@ def test_pair_census_on_the_benchmark_image_and_the_far_field():
     assert 0 < c6["interpolated_pairs"] <= c3["interpolated_pairs"] < system.pairs()
     assert c3["pairs"] < c6["pairs"] < c0["pairs"]
     assert c3["flops"] < c0["flops"]
+
+
+def test_kernel_hash_ignores_comments_but_not_code():
+    # the stored profile traffic is matched to the trace kernel by this hash: a comment edit keeps
+    # the capture valid, any change of code invalidates it
+    sys.path.insert(0, ROOT)
+    import bench
+    src = "// header\n__device__ float f(float x) {  /* a\n block */\n  return x * 2.f;  // twice\n}\n\n"
+    same = "__device__ float f(float x) {\n  return x * 2.f;   // doubled\n}\n"
+    other = "__device__ float f(float x) {\n  return x * 3.f;\n}\n"
+    assert bench._code_only(src) == bench._code_only(same)
+    assert bench._code_only(src) != bench._code_only(other)
+    assert "//" not in bench._code_only(src) and "/*" not in bench._code_only(src)
+    assert len(bench.kernel_hash()) == 16
