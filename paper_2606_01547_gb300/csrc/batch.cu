@@ -5,7 +5,8 @@
 // to the device with one cudaMemcpyAsync, and replays a CUDA graph of three persistent kernels
 // (subhalo constants, trace units, PSF tiles).  The kernels read every count and pointer from
 // the device header, so one captured graph serves every batch; it is re-captured only when the
-// workspace moves or the largest PSF grows.
+// workspace moves, the largest PSF grows, or the persistent trace form or the far-field on/off
+// setting changes (the far-field kappa itself travels in each system's descriptor).
 #include <algorithm>
 #include <cstring>
 #include <numeric>
